@@ -1,0 +1,444 @@
+"""Benchmark: H phi for every support function + sparse H_ab / S_ab, on synthetic
+locreg workloads shaped like the paper's (arXiv 1401.7441), on one or more GPUs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--precision fp32|fp64] [--impl ours|reference]
+
+One step = lsw_apply_hamiltonian (every support function) + lsw_build_matrices (the
+whole CSR pattern) on inputs resident in HBM.  The L2 is flushed (a 512 MB write)
+before every timed step; each step is bracketed by CUDA events on the library's
+stream.  value = support functions per second (whole job; N > 1 runs N independent
+replicas, one per rank, no collective: "replicas only", weak scaling).
+
+Extra keys: e2e (the same metric through lsw_step_host with pinned host buffers:
+phi host->device, H and S device->host inside the timed region), roofline (the
+dominant kernel, from the library's per-launch device trace over the timed steps),
+cpu_baseline (the oracle on a bounded sample, host cores), clocks (nvidia-smi sampled
+during the timed steps), gpu_launches (kernels enqueued per timed step x steps).
+
+--impl reference runs the oracle (the plain FP64 CPU implementation written from the
+paper) on a bounded sample of the same workload: it is the only reference there is.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1401_7441_gb300 import inputs as I  # noqa: E402
+
+METRIC = "H-phi support functions/s incl. sparse H,S build"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# CUDA-core peaks derived from the SM count and the maximum SM clock (no measured
+# figure exists for them): FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 is the
+# nominal GB300 figure.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default="atoms64")
+    p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--batch", type=int, default=0)
+    p.add_argument("--tile", type=int, default=0)
+    return p.parse_args()
+
+
+def workload(name):
+    if name in I.WORKLOADS:
+        return I.WORKLOADS[name]()
+    if name.startswith("atoms10k_n"):
+        return I.scaled("atoms10k", int(name.split("_n")[1]))
+    if name.startswith("atoms64_n"):
+        return I.scaled("atoms64", int(name.split("_n")[1]))
+    raise SystemExit("unknown workload " + name)
+
+
+def keys_to_g(keys):
+    if len(keys) == 0:
+        return np.zeros(0, np.int64)
+    lens = keys[:, 1] - keys[:, 0] + 1
+    starts = np.repeat(keys[:, 0] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+    return starts + np.arange(int(lens.sum()), dtype=np.int64)
+
+
+# ---------------------------------------------------------------- oracle (CPU) leg
+
+def oracle_sample(wl, budget_s=20.0, max_fn=None):
+    """Time the oracle on a bounded sample: H phi of the first functions, then the S/H
+    entries between them.  Returns (functions/s, cores, description)."""
+    from oracle import geometry as G
+    from oracle import hamiltonian as Hm
+    from oracle import matrices as Mx
+    desc = G.SystemDesc(tuple(wl.N), wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff,
+                        wl.pair_mode, wl.lprime_margin, wl.fine_mode)
+    nsf = int(np.sum(wl.nsf))
+    sf_atom = np.repeat(np.arange(len(wl.nsf)), wl.nsf)
+    t0 = time.perf_counter()
+    geo = G.build(desc, atoms=sorted(set(sf_atom[:min(nsf, 64)].tolist())), pattern=False)
+    V = None
+    done = []
+    tf = time.perf_counter()
+    hphi, phi = {}, {}
+    for f in range(nsf if max_fn is None else min(nsf, max_fn)):
+        a = int(sf_atom[f])
+        if geo.L[a] is None:
+            break
+        L = geo.L[a]
+        phi[f] = I.phi_values(wl, f, a, L.coarse.g, L.fine.g)
+        lo = [2 * int(L.lo[d]) - 14 for d in range(3)]
+        shape = [2 * int(L.hi[d] - L.lo[d] + 1) + 29 for d in range(3)]
+        Vb = I.potential_block(wl, lo, shape)
+        hphi[f] = Hm.apply_hamiltonian(geo, f, phi[f], Vb, lo)[0]
+        done.append(f)
+        if time.perf_counter() - tf > budget_s:
+            break
+    for a in done:
+        for b in done:
+            Mx.overlap_entry(geo, a, b, phi[a], phi[b])
+            Mx.hamiltonian_entry(geo, a, b, phi[a], hphi[b])
+    dt = time.perf_counter() - tf
+    cores = 1
+    try:
+        import threadpoolctl  # noqa: F401
+    except Exception:
+        pass
+    sample = ("oracle (numpy FP64, 1 thread of %d host cores) on the first %d of %d support functions: "
+              "H phi each, then S and H entries among them; %.1f s" % (os.cpu_count() or 1, len(done), nsf, dt))
+    _ = t0
+    return len(done) / dt, cores, sample
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    prec = args.precision or wl.precision
+    # the whole --steps/--warmup run must end within a few minutes: bound each step
+    per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = oracle_sample(wl, budget_s=per_step)
+        if i >= args.warmup:
+            vals.append(v)
+    val = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "support_functions/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "precision_of_ours": prec},
+            "cpu_baseline": {"value": val, "unit": "support_functions/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "support_functions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, dev_index):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [ln.split(",") for ln in open(self.path) if ln.strip()]
+        except Exception:
+            return out
+        rows = [[x.strip() for x in r] for r in rows if r and r[0].strip() == str(dev_index)]
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        out["sm_mhz"] = statistics.median(sm) if sm else None
+        out["sm_max_mhz"] = max(mx) if mx else None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+def kernel_work(S, wl, prec):
+    """Algorithmic FLOPs of each kernel kind for one full step (exact in-range tap
+    counts of the separable filters), and compulsory bytes."""
+    es = 8 if prec == "fp64" else 4
+    fl = {"fwd_xy": 0.0, "z_stage": 0.0, "bwd_xy": 0.0, "kinetic": 0.0}
+
+    def up_taps(nout, nin):
+        # sum over outputs o of #{q: 0<=q<nin, 0<=o-2q<=30}
+        o = np.arange(nout)[:, None]
+        q = np.arange(nin)[None, :]
+        return int(np.sum((o - 2 * q >= 0) & (o - 2 * q <= 30)))
+
+    def down_taps(nout, off, nin):
+        b = np.arange(nout)[:, None] + off
+        o = np.arange(nin)[None, :]
+        return int(np.sum((o - 2 * b >= 0) & (o - 2 * b <= 30)))
+
+    cache = {}
+    for f in range(S.n_sf):
+        a = int(S.sf_atom[f])
+        if a not in cache:
+            kc = S.keys(a, 0, 0)
+            kp = S.keys(a, 1, 0)
+            def box(k):
+                g0, g1 = k[:, 0], k[:, 1]
+                N = wl.N
+                x0, x1 = g0 % N[0], g1 % N[0]
+                y = (g0 // N[0]) % N[1]
+                z = g0 // (N[0] * N[1])
+                lo = np.array([x0.min(), y.min(), z.min()])
+                hi = np.array([x1.max(), y.max(), z.max()])
+                return lo, hi - lo + 1
+            lo, n = box(kc)
+            lop, npp = box(kp)
+            X, Y, Z = (2 * n + 29)
+            d = lop - lo
+            fx = 4 * n[1] * n[2] * 2 * up_taps(X, n[0])                      # 4 type pairs, 2 inputs
+            fy = 2 * n[2] * X * 2 * up_taps(Y, n[1])
+            fz = X * Y * 2 * up_taps(Z, n[2])
+            bz = X * Y * 2 * down_taps(npp[2], d[2], Z)
+            by = npp[2] * 2 * X * 2 * down_taps(npp[1], d[1], Y)
+            bx = npp[2] * 4 * npp[1] * down_taps(npp[0], d[0], X) * 2
+            # kinetic: 8 output types x 3 axes x 2 input types x in-range taps, per L' point
+            kin = 0
+            for ax in range(3):
+                o = np.arange(npp[ax])[:, None] + d[ax]
+                l = np.arange(-14, 15)[None, :]
+                taps = int(np.sum((o + l >= 0) & (o + l < n[ax])))
+                others = [k for k in range(3) if k != ax]
+                inside = 1
+                for e in others:
+                    ob = np.arange(npp[e]) + d[e]
+                    inside *= int(np.sum((ob >= 0) & (ob < n[e])))
+                kin += 8 * 2 * taps * inside
+            cache[a] = (2.0 * (fx + fy), 2.0 * (fz + bz), 2.0 * (by + bx), 2.0 * kin)
+        c = cache[a]
+        fl["fwd_xy"] += c[0]
+        fl["z_stage"] += c[1]
+        fl["bwd_xy"] += c[2]
+        fl["kinetic"] += c[3]
+    comp_bytes = es * (S.total_L + S.total_Lp) + 16.0 * len(S.col)
+    return fl, comp_bytes
+
+
+def gpu_main(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1401_7441_gb300 import build as B
+    from paper_1401_7441_gb300 import lsw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    wl = workload(args.workload)
+    prec = args.precision or wl.precision
+    P = lsw.LSW_FP64 if prec == "fp64" else lsw.LSW_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t_setup = time.perf_counter()
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   wl.lprime_margin, 0, P, device=local, stream=stream.cuda_stream)
+    if args.batch:
+        lsw.lsw_set_option(S.sys, "batch", args.batch)
+    if args.tile:
+        lsw.lsw_set_option(S.sys, "tile", args.tile)
+    # inputs on the device: phi from the counter generator, V sampled on the fine grid
+    phi = torch.zeros(S.total_L, dtype=dt, device="cuda")
+    first = 0
+    atom_g = {}
+    for f in range(S.n_sf):
+        a = int(S.sf_atom[f])
+        if a not in atom_g:
+            atom_g = {a: (torch.as_tensor(keys_to_g(S.keys(a, 0, 0)), device="cuda"),
+                          torch.as_tensor(keys_to_g(S.keys(a, 0, 1)), device="cuda"))}
+        gc, gf = atom_g[a]
+        v = I.phi_values(wl, f, a, gc, gf, xp=torch, device="cuda")
+        phi[S.off_L[f]:S.off_L[f] + v.numel()] = v.to(dt)
+    _ = first
+    V = I.potential(wl, xp=torch, device="cuda").to(dt)
+    lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
+    hphi = torch.zeros(S.total_Lp, dtype=dt, device="cuda")
+    ek = torch.zeros(S.n_sf, dtype=torch.float64, device="cuda")
+    ep = torch.zeros(S.n_sf, dtype=torch.float64, device="cuda")
+    nnz = len(S.col)
+    Hm = torch.zeros(max(1, nnz), dtype=torch.float64, device="cuda")
+    Sm = torch.zeros(max(1, nnz), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
+    def step():
+        lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
+        lsw.lsw_build_matrices(S.sys, phi, hphi, Hm, Sm)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    lsw.lsw_profile(S.sys, 1)
+    step()                      # capture the traced graphs outside the timed region
+    lsw.lsw_profile_read(S.sys)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    prof = {}
+    clk_path = os.path.join(tempfile.gettempdir(), "lsw_clocks_%d.csv" % os.getpid())
+    with ClockSampler(clk_path) as clk:
+        time.sleep(0.3)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+            torch.cuda.synchronize()
+            for k, (ms, n) in lsw.lsw_profile_read(S.sys).items():
+                a, b = prof.get(k, (0.0, 0))
+                prof[k] = (a + ms, b + n)
+    step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    lsw.lsw_profile(S.sys, 0)
+    clocks = clk.summary(local)
+    value = world * S.n_sf * args.steps / (total_ms / 1000.0)
+
+    # end to end through host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        phi_h = phi.cpu().pin_memory()
+        hphi_h = torch.empty(S.total_Lp, dtype=dt).pin_memory()
+        H_h = torch.empty(max(1, nnz), dtype=torch.float64).pin_memory()
+        S_h = torch.empty(max(1, nnz), dtype=torch.float64).pin_memory()
+        lsw.lsw_step_host(S.sys, phi_h, None, H_h, S_h)
+        k2 = max(1, min(args.steps, 3))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            lsw.lsw_step_host(S.sys, phi_h, None, H_h, S_h)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * S.n_sf * k2 / el, "unit": "support_functions/s",
+               "h2d_bytes_per_step": int(phi_h.numel() * phi_h.element_size()),
+               "d2h_bytes_per_step": int(2 * nnz * 8)}
+        _ = hphi_h
+
+    # roofline of the dominant kernel
+    flops, comp_bytes = kernel_work(S, wl, prec)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0]) if kinds else None
+    roof = None
+    if dom is not None:
+        ms_tot, n_launch = kinds[dom]
+        per_launch_ms = ms_tot / n_launch
+        if dom in flops:
+            launches_per_step = n_launch / args.steps
+            work_per_launch = flops[dom] / launches_per_step
+            peak = (FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS)
+            ach = work_per_launch / (per_launch_ms / 1000.0) / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_source": "derived: %s CUDA-core FMA rate (see DESIGN.md)" % prec}
+        else:
+            roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
+                    "frac": None, "traffic": None}
+    kshare = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()} if kinds else {}
+    launches_per_step = int(sum(v[1] for v in kinds.values()) / args.steps) if kinds else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample = oracle_sample(wl, budget_s=20.0)
+        cpu = {"value": v, "unit": "support_functions/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "support_functions/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "atoms": len(wl.pos), "support_functions": S.n_sf,
+                           "pattern_nnz": nnz, "grid": list(wl.N), "h_bohr": wl.h,
+                           "precision": prec, "l2": "flushed (512 MB write) before every timed step",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
+                "kernel_share": kshare,
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+                "compulsory_gb_per_step": comp_bytes / 1e9,
+                "setup_s": t_setup, "step_ms": step_ms}
+        print(json.dumps(line))
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    return gpu_main(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * lsw.h -- C ABI of the GB300 (sm_103a) library for the localized Hamiltonian
+ * application and the sparse H_ab / S_ab build of Daubechies-wavelet linear-scaling
+ * DFT (arXiv 1401.7441).
+ *
+ * Problem statement (Sec. III, Eq. loccon; Sec. III.B; Sec. II.A): support functions
+ * phi_alpha, each stored on its localization region L(alpha) (a sphere of radius
+ * R_cut around its atom on a two-resolution Daubechies-16 grid, Sec. II.B), and a
+ * local potential V(r) on the real-space grid of spacing h/2.  Compute
+ *     H phi_alpha = L'(alpha) H L(alpha) phi_alpha,   H = -1/2 nabla^2 + V,
+ * with L' of radius R_cut + 8 grid points (Sec. III.B), and the sparse matrices
+ *     S_ab = <phi_a|phi_b>,  H_ab = <phi_a|H phi_b>
+ * on the pattern of pairs whose atoms lie within a cutoff (Sec. II.A; Sec. IV.A
+ * "Suitability of the methods": sparse matrices in compressed form).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an lsw_status.  On failure nothing was enqueued, and
+ *   lsw_last_error() returns a message for the calling thread.
+ * - Grid: coarse point (i1, i2, i3), 0 <= i_d < N_d, sits at (i1 h, i2 h, i3 h);
+ *   fine real-space point j sits at j h / 2.  Global index g = i1 + N1 (i2 + N2 i3).
+ * - Membership (locregs, fine spheres, pattern) is inclusive, d^2 <= R^2, with d^2
+ *   computed in IEEE FP64 as ((x-X)^2 + (y-Y)^2) + (z-Z)^2 without fused operations.
+ * - The fine region is the union of every atom's fine sphere (LSW_FINE_UNION, Sec.
+ *   II.B) or, per locreg, its own atom's sphere (LSW_FINE_OWN).
+ * - Compressed layout of one support function on a region: the scaling coefficients
+ *   s at the region's coarse points in key order, then seven planes d^1..d^7 at its
+ *   fine points in key order; wavelet type l = bx + 2 by + 4 bz (b_d = 1: wavelet
+ *   along dimension d).  Functions are numbered atom by atom; function f starts at
+ *   element off[f] (multiples of 64 elements).
+ * - Ownership: the caller owns every pointer it passes (device buffers may come
+ *   from any allocator, e.g. PyTorch).  Host arrays returned by the library stay
+ *   valid until the owning object is destroyed.  The library owns its keys, plans
+ *   and device workspace (lsw_workspace_bytes).
+ * - Asynchrony: device work is enqueued on the context's stream; calls return after
+ *   enqueueing.  Only lsw_sync and lsw_step_host wait for the device.
+ * - Device-side checks never trap: they set a status word that lsw_sync reports.
+ */
+#ifndef LSW_H
+#define LSW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSW_OK = 0,
+    LSW_ERR_ARG = 1,          /* invalid argument (detected before any launch)   */
+    LSW_ERR_OOM = 2,          /* device or host allocation failed                */
+    LSW_ERR_CUDA = 3,         /* a CUDA runtime call failed                      */
+    LSW_ERR_TIMEOUT = 4,      /* lsw_sync: the device did not finish in time     */
+    LSW_ERR_STATE = 5,        /* wrong call order (e.g. no potential set)        */
+    LSW_ERR_UNSUPPORTED = 6   /* valid but outside what this build handles       */
+} lsw_status;
+
+#define LSW_HOST_ONLY (-1)
+
+typedef enum { LSW_FP64 = 0, LSW_FP32 = 1 } lsw_precision;
+typedef enum { LSW_REGION_L = 0, LSW_REGION_LP = 1 } lsw_region;
+typedef enum { LSW_PART_COARSE = 0, LSW_PART_FINE = 1 } lsw_part;
+typedef enum { LSW_FINE_UNION = 0, LSW_FINE_OWN = 1 } lsw_fine_mode;
+typedef enum { LSW_PAIR_CUTOFF = 0, LSW_PAIR_SUM_OF_RADII = 1 } lsw_pair_mode;
+
+/* Filter tables exported for cross-checks (lsw_filter_table, `which`). */
+typedef enum {
+    LSW_FILTER_H = 0,        /* low-pass h_j, j = -7..8 (least-asymmetric D16)       */
+    LSW_FILTER_G = 1,        /* high-pass g_j = (-1)^j h_{1-j}, j = -7..8            */
+    LSW_FILTER_MOMENTS = 2,  /* M_p = int x^p phi, p = 0..15                         */
+    LSW_FILTER_MAGIC = 3,    /* magic filter w_l, l = -7..8                          */
+    LSW_FILTER_KIN_R = 4,    /* r_l = int phi phi''(. - l), l = -14..14              */
+    LSW_FILTER_KIN_HH = 5,   /* T_XY(l) = <X_0|d2/dx2|Y_l>, l = -14..14              */
+    LSW_FILTER_KIN_HG = 6,
+    LSW_FILTER_KIN_GH = 7,
+    LSW_FILTER_KIN_GG = 8,
+    LSW_FILTER_FWD_H = 9,    /* (w * h)_m = sum_k w_{m-k} h_k, m = -14..16           */
+    LSW_FILTER_FWD_G = 10    /* (w * g)_m, m = -14..16                               */
+} lsw_filter;
+
+typedef struct lsw_ctx_s* lsw_ctx;
+typedef struct lsw_system_s* lsw_system;
+
+/* Description of a system (all pointers host, read during lsw_system_create only). */
+typedef struct {
+    int32_t N[3];            /* coarse grid points per dimension (>= 1)              */
+    double h;                /* coarse grid spacing, bohr (> 0)                      */
+    int32_t n_atoms;         /* >= 1                                                 */
+    const double* pos;       /* [n_atoms][3] atom centres, bohr, box coordinates     */
+    const double* r_loc;     /* [n_atoms] locreg radius R_cut, bohr (> 0)            */
+    const double* r_fine;    /* [n_atoms] fine-sphere radius, bohr (>= 0)            */
+    const int32_t* n_sf;     /* [n_atoms] support functions on the atom (>= 0)       */
+    double lprime_margin;    /* L' radius = R_cut + lprime_margin * h; 8 in Sec. III.B */
+    double pair_cutoff;      /* LSW_PAIR_CUTOFF: bohr                                */
+    int32_t pair_mode;       /* lsw_pair_mode                                        */
+    int32_t fine_mode;       /* lsw_fine_mode                                        */
+    int32_t precision;       /* lsw_precision of phi, H phi and the convolutions     */
+} lsw_system_desc;
+
+/* Message describing the last failure on this thread ("" if none).  Never NULL. */
+const char* lsw_last_error(void);
+
+/* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream, on which work is never captured into CUDA
+ * graphs; pass a created stream to get graph replay).  device = LSW_HOST_ONLY
+ * makes a host-only context: filters, geometry, keys and pattern are available, every
+ * call that needs the device returns LSW_ERR_STATE.  Derives the filter tables (Sec. II.B readings:
+ * least-asymmetric order-16 Daubechies factor, magic filter with the moments of phi,
+ * Galerkin kinetic connection coefficients) in double-double arithmetic, rounds them
+ * to FP64/FP32 once and uploads them.  *out receives the handle.
+ * Errors: LSW_ERR_ARG (out NULL, bad device), LSW_ERR_CUDA. */
+lsw_status lsw_ctx_create(int device, void* stream, lsw_ctx* out);
+
+/* Destroy a context (all its systems must have been destroyed).  NULL is a no-op. */
+lsw_status lsw_ctx_destroy(lsw_ctx ctx);
+
+/* Copy filter table `which` (lsw_filter) to host `values` (capacity >= 32 doubles);
+ * *first = index of values[0], *count = number of entries.  Host only. */
+lsw_status lsw_filter_table(lsw_ctx ctx, int32_t which, int32_t* first, int32_t* count,
+                            double* values);
+
+/* Build a system: fine region, locregs L and L' of every atom (Eq. loccon, Sec. III.B),
+ * their segment keys, the compressed layout, the pair pattern (CSR) and the device
+ * plans and workspace.  Host work plus uploads; synchronous.
+ * Errors: LSW_ERR_ARG (sizes, radii, NULL arrays), LSW_ERR_OOM, LSW_ERR_CUDA,
+ * LSW_ERR_UNSUPPORTED (a locreg box too large for the on-chip pass tiles). */
+lsw_status lsw_system_create(lsw_ctx ctx, const lsw_system_desc* desc, lsw_system* out);
+
+/* Destroy a system after its device work has finished.  NULL is a no-op. */
+lsw_status lsw_system_destroy(lsw_system sys);
+
+/* Compressed layout: *n_sf functions; phi buffers hold total_L elements (of the
+ * system precision), H phi buffers total_Lp; off_L / off_Lp are host arrays of
+ * n_sf + 1 element offsets; sf_atom[f] is the atom of function f. */
+lsw_status lsw_system_layout(lsw_system sys, int64_t* n_sf, int64_t* total_L,
+                             int64_t* total_Lp, const int64_t** off_L,
+                             const int64_t** off_Lp, const int32_t** sf_atom);
+
+/* Segment keys of atom `atom`'s region (lsw_region) part (lsw_part): *nseg keys of
+ * three int64 each (first g, last g inclusive, coefficient offset within the part),
+ * sorted by g; a segment is a maximal run of members along i1. Host array. */
+lsw_status lsw_system_keys(lsw_system sys, int32_t atom, int32_t region, int32_t part,
+                           int64_t* nseg, const int64_t** keys);
+
+/* Pair pattern: CSR with n_sf rows, columns ascending, *nnz entries; host arrays. */
+lsw_status lsw_pattern(lsw_system sys, int64_t* nnz, const int64_t** row_ptr,
+                       const int32_t** col);
+
+/* Register the global potential: a device array of the system precision, stored
+ * [k][j][i] (x fastest) over fine indices fine_lo[d] .. fine_lo[d]+fine_dims[d]-1.
+ * It must cover [-14, 2 N_d + 14] in every dimension (every point the magic filter
+ * reaches, free boundary).  The pointer is kept (not copied): the caller keeps the
+ * buffer alive and unchanged while work that reads it is in flight.
+ * Errors: LSW_ERR_ARG (NULL, coverage). */
+lsw_status lsw_set_potential(lsw_system sys, const void* V_dev, const int64_t fine_lo[3],
+                             const int64_t fine_dims[3]);
+
+/* H phi for every support function (Sec. III.B): phi_dev (total_L elements, layout
+ * off_L) -> hphi_dev (total_Lp elements, layout off_Lp), both of the system precision.
+ * e_kin_dev / e_pot_dev (n_sf doubles each, may be NULL) receive <phi|T phi> and
+ * <phi|V phi>.  Asynchronous.  phi and hphi must not overlap.
+ * Errors: LSW_ERR_ARG (NULL buffers), LSW_ERR_STATE (no potential), LSW_ERR_CUDA. */
+lsw_status lsw_apply_hamiltonian(lsw_system sys, const void* phi_dev, void* hphi_dev,
+                                 double* e_kin_dev, double* e_pot_dev);
+
+/* Sparse matrices on the pattern (Sec. II.A): H_dev[k] = <phi_a|H phi_b> (raw, not
+ * symmetrized) and S_dev[k] = <phi_a|phi_b> for the k-th pattern entry (a, b); FP64
+ * accumulation in both precisions.  Asynchronous.
+ * Errors: LSW_ERR_ARG (NULL), LSW_ERR_CUDA. */
+lsw_status lsw_build_matrices(lsw_system sys, const void* phi_dev, const void* hphi_dev,
+                              double* H_dev, double* S_dev);
+
+/* Device workspace held by the system, bytes. */
+lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes);
+
+/* Wait for the system's enqueued work for at most timeout_s seconds (polling an
+ * event; never blocks longer).  Returns LSW_ERR_TIMEOUT if still running,
+ * LSW_ERR_CUDA on a device error, LSW_ERR_STATE if a device-side check fired. */
+lsw_status lsw_sync(lsw_system sys, double timeout_s);
+
+/* End-to-end step through host memory: copy phi from host (pinned or pageable),
+ * apply H, build H_ab and S_ab, and copy the results back; returns when done.
+ * hphi_host, e_kin_host and e_pot_host may be NULL (not copied back). */
+lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host,
+                         double* H_host, double* S_host, double* e_kin_host,
+                         double* e_pot_host);
+
+/* Device trace of the enqueued kernels.  enable = 1 records a CUDA event pair around
+ * every launch the system enqueues from now on (inside CUDA graphs as event-record
+ * nodes); enable = 0 stops.  Waits for the stream and drops cached graphs. */
+lsw_status lsw_profile(lsw_system sys, int32_t enable);
+
+/* Summed device milliseconds and launch counts per kernel kind since the last read,
+ * kinds in this order: 0 memset, 1 uncompress, 2 forward xy, 3 z stage with V,
+ * 4 backward xy, 5 kinetic, 6 compress, 7 H/S tiles.  Waits for the stream.  Writes
+ * min(max_kinds, *n_kinds) entries of ms[] and launches[]; resets the totals. */
+lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds, double* ms,
+                            int64_t* launches);
+
+/* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
+ * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points).
+ * Errors: LSW_ERR_ARG (unknown name or value). */
+lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSW_H */

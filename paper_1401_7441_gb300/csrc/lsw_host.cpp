@@ -1,0 +1,1135 @@
+// Host side of the C ABI (include/lsw.h): contexts, locreg geometry and segment keys,
+// compressed layout, pair pattern, device plans, graph capture and the call surface.
+//
+// Paper: Sec. II.B (two-resolution grid; fine region = union of the atoms' small
+// spheres; box with its origin at a corner), Sec. III Eq. loccon (locreg projector
+// L: coefficients kept within R_cut of the centre), Sec. III.B (L' with R_cut + 8
+// grid points; H phi = L' H L phi), Sec. II.A / Sec. IV.A (sparse H and S in
+// compressed form on the locreg-overlap pattern), App. D (the "transposed" layout:
+// partial matrices per region of the cell, here one H/S work item per grid tile).
+//
+// Membership tests are done in IEEE FP64 without contraction (this file is compiled
+// with -ffp-contract=off): d2 = ((x-X)*(x-X) + (y-Y)*(y-Y)) + (z-Z)*(z-Z), x = i*h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lsw.h"
+#include "lsw_internal.h"
+
+using namespace lsw;
+
+namespace {
+
+thread_local std::string g_err;
+
+lsw_status fail(lsw_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+lsw_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(LSW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                                       \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);  \
+    } while (0)
+
+struct DeviceBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DeviceBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t b) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = b;
+        if (b == 0) return cudaSuccess;
+        return cudaMalloc(&p, b);
+    }
+    template <class T>
+    cudaError_t upload(const std::vector<T>& v, cudaStream_t s) {
+        cudaError_t e = alloc(v.size() * sizeof(T));
+        if (e != cudaSuccess || v.empty()) return e;
+        e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(s);
+    }
+};
+
+struct RegionHost {
+    std::vector<int64_t> g;     // ascending
+    std::vector<int64_t> keys;  // 3 per segment: first g, last g, offset
+};
+
+struct LocregHost {
+    RegionHost c, f;
+    int32_t lo[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+};
+
+}  // namespace
+
+namespace lsw {
+struct EvPair {
+    int kind;
+    cudaEvent_t a, b;
+};
+struct Tracer {
+    std::vector<EvPair> ev;    // pairs recorded (or captured) so far
+    size_t used = 0;           // pairs in use for the current enqueue sequence
+    bool capturing = false;
+    bool pending = false;      // recorded work not read yet
+    int cur = -1;
+    ~Tracer() {
+        for (auto& p : ev) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+    }
+};
+void trace_begin(Tracer* tr, int kind, cudaStream_t s) {
+    if (!tr) return;
+    if (tr->used == tr->ev.size()) {
+        EvPair p{kind, nullptr, nullptr};
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        tr->ev.push_back(p);
+    }
+    EvPair& p = tr->ev[tr->used];
+    p.kind = kind;
+    tr->cur = static_cast<int>(tr->used);
+    if (tr->capturing)
+        cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(p.a, s);
+}
+void trace_end(Tracer* tr, cudaStream_t s) {
+    if (!tr || tr->cur < 0) return;
+    EvPair& p = tr->ev[tr->cur];
+    if (tr->capturing)
+        cudaEventRecordWithFlags(p.b, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(p.b, s);
+    tr->used++;
+    tr->cur = -1;
+    tr->pending = true;
+}
+}  // namespace lsw
+
+struct lsw_ctx_s {
+    int device = 0;
+    bool host_only = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    FilterSet filters;
+    size_t max_smem = 0;
+    int n_sm = 0;
+    int live_systems = 0;
+};
+
+struct GraphKey {
+    const void* a;
+    const void* b;
+    const void* c;
+    const void* d;
+    bool operator<(const GraphKey& o) const {
+        if (a != o.a) return a < o.a;
+        if (b != o.b) return b < o.b;
+        if (c != o.c) return c < o.c;
+        return d < o.d;
+    }
+};
+
+struct Batch {
+    int64_t fn0, nfn;
+    HphiLaunch proto;
+};
+
+struct lsw_system_s {
+    lsw_ctx ctx = nullptr;
+    int32_t N[3];
+    double h;
+    int prec;
+    size_t esize;
+    int32_t n_atoms;
+    std::vector<double> pos, r_loc, r_fine;
+    std::vector<int32_t> nsf;
+    double margin, cutoff;
+    int pair_mode, fine_mode;
+    std::vector<uint8_t> fine_mask;
+    std::vector<LocregHost> L, Lp;
+    std::vector<int32_t> sf_atom;
+    std::vector<int64_t> off_L, off_Lp;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    // device state
+    DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
+    DeviceBuf d_tile_org, d_tile_fine, d_listA, d_listB, d_work, d_ws, d_status, d_escratch;
+    std::vector<Batch> batches;
+    int64_t ws_elems = 0;
+    int batch_size = 0;
+    int tile = 8;
+    int use_graph = 1;
+    int nwork = 0;
+    // potential
+    const void* V = nullptr;
+    int64_t vlo[3] = {0, 0, 0}, vn[3] = {0, 0, 0};
+    // graphs (each with the event pairs captured into it when tracing is on)
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        std::unique_ptr<Tracer> tr;
+    };
+    std::map<GraphKey, GraphEntry> graphs_h, graphs_m;
+    int profiling = 0;
+    std::unique_ptr<Tracer> direct_tr;   // tracer of work enqueued without a graph
+    double prof_ms[TK_COUNT] = {0};
+    int64_t prof_n[TK_COUNT] = {0};
+    // host-API buffers
+    DeviceBuf d_phi, d_hphi, d_H, d_S, d_ek, d_ep;
+    cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+inline double d2_of(double x, double y, double z, const double* c) {
+    double dx = x - c[0];
+    double dy = y - c[1];
+    double dz = z - c[2];
+    double a = dx * dx;
+    double b = dy * dy;
+    double s = a + b;
+    double e = dz * dz;
+    return s + e;
+}
+
+void sphere_bounds(const int32_t* N, double h, const double* c, double R, int* lo, int* hi) {
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = std::max(0, static_cast<int>(std::floor((c[d] - R) / h)) - 1);
+        hi[d] = std::min(N[d] - 1, static_cast<int>(std::ceil((c[d] + R) / h)) + 1);
+    }
+}
+
+void make_keys(const int32_t* N, RegionHost* r) {
+    r->keys.clear();
+    const auto& g = r->g;
+    size_t i = 0;
+    while (i < g.size()) {
+        size_t j = i;
+        while (j + 1 < g.size() && g[j + 1] == g[j] + 1 && (g[j + 1] / N[0]) == (g[i] / N[0])) ++j;
+        r->keys.push_back(g[i]);
+        r->keys.push_back(g[j]);
+        r->keys.push_back(static_cast<int64_t>(i));
+        i = j + 1;
+    }
+}
+
+void build_locreg(lsw_system_s* s, const std::vector<uint8_t>& fine, int a, double R,
+                  LocregHost* out) {
+    const int32_t* N = s->N;
+    const double* c = &s->pos[3 * a];
+    const double R2 = R * R;
+    int lo[3], hi[3];
+    sphere_bounds(N, s->h, c, R, lo, hi);
+    double rf2 = s->r_fine[a] * s->r_fine[a];
+    out->c.g.clear();
+    out->f.g.clear();
+    int bl[3] = {N[0], N[1], N[2]}, bh[3] = {-1, -1, -1};
+    for (int k = lo[2]; k <= hi[2]; ++k) {
+        double z = static_cast<double>(k) * s->h;
+        for (int j = lo[1]; j <= hi[1]; ++j) {
+            double y = static_cast<double>(j) * s->h;
+            for (int i = lo[0]; i <= hi[0]; ++i) {
+                double x = static_cast<double>(i) * s->h;
+                if (!(d2_of(x, y, z, c) <= R2)) continue;
+                int64_t g = i + static_cast<int64_t>(N[0]) * (j + static_cast<int64_t>(N[1]) * k);
+                out->c.g.push_back(g);
+                bool isf;
+                if (s->fine_mode == LSW_FINE_UNION)
+                    isf = fine[g] != 0;
+                else
+                    isf = d2_of(x, y, z, c) <= rf2;
+                if (isf) out->f.g.push_back(g);
+                bl[0] = std::min(bl[0], i), bh[0] = std::max(bh[0], i);
+                bl[1] = std::min(bl[1], j), bh[1] = std::max(bh[1], j);
+                bl[2] = std::min(bl[2], k), bh[2] = std::max(bh[2], k);
+            }
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        out->lo[d] = out->c.g.empty() ? 0 : bl[d];
+        out->n[d] = out->c.g.empty() ? 0 : bh[d] - bl[d] + 1;
+    }
+    make_keys(N, &out->c);
+    make_keys(N, &out->f);
+}
+
+// box-local segments and per-row CSR of one region part
+void emit_segments(const int32_t* N, const LocregHost& loc, const RegionHost& r,
+                   std::vector<Seg>* seg, std::vector<int32_t>* rowptr, int64_t* seg0,
+                   int32_t* nseg, int64_t* row0) {
+    *seg0 = static_cast<int64_t>(seg->size());
+    *row0 = static_cast<int64_t>(rowptr->size());
+    const int nrows = loc.n[1] * loc.n[2];
+    std::vector<int32_t> cnt(nrows + 1, 0);
+    const size_t ns = r.keys.size() / 3;
+    for (size_t q = 0; q < ns; ++q) {
+        int64_t g0 = r.keys[3 * q], g1 = r.keys[3 * q + 1], off = r.keys[3 * q + 2];
+        int64_t i1 = g0 % N[0], i2 = (g0 / N[0]) % N[1], i3 = g0 / (static_cast<int64_t>(N[0]) * N[1]);
+        Seg sg;
+        sg.x0 = static_cast<int32_t>(i1 - loc.lo[0]);
+        sg.x1 = static_cast<int32_t>(sg.x0 + (g1 - g0));
+        sg.row = static_cast<int32_t>((i2 - loc.lo[1]) + static_cast<int64_t>(loc.n[1]) * (i3 - loc.lo[2]));
+        sg.off = static_cast<int32_t>(off);
+        seg->push_back(sg);
+        cnt[sg.row + 1]++;
+    }
+    for (int i = 0; i < nrows; ++i) cnt[i + 1] += cnt[i];
+    for (int i = 0; i <= nrows; ++i) rowptr->push_back(cnt[i]);
+    *nseg = static_cast<int32_t>(ns);
+}
+
+template <class F>
+void parallel_for(int n, F fn) {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 64 || nt == 1) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            for (int i = static_cast<int>(t); i < n; i += static_cast<int>(nt)) fn(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+lsw_status build_pattern(lsw_system_s* s) {
+    const int na = s->n_atoms;
+    double cmax = s->cutoff;
+    if (s->pair_mode == LSW_PAIR_SUM_OF_RADII) {
+        double rm = 0.0;
+        for (double r : s->r_loc) rm = std::max(rm, r);
+        cmax = 2.0 * rm;
+    }
+    double cell = std::max(cmax, 1e-3);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int a = 0; a < na; ++a)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], s->pos[3 * a + d]);
+            hi[d] = std::max(hi[d], s->pos[3 * a + d]);
+        }
+    int nc[3];
+    for (int d = 0; d < 3; ++d) nc[d] = std::max(1, std::min(1024, static_cast<int>((hi[d] - lo[d]) / cell) + 1));
+    auto cidx = [&](int a, int d) {
+        int c = static_cast<int>((s->pos[3 * a + d] - lo[d]) / cell);
+        return std::min(nc[d] - 1, std::max(0, c));
+    };
+    std::vector<std::vector<int>> cells(static_cast<size_t>(nc[0]) * nc[1] * nc[2]);
+    for (int a = 0; a < na; ++a)
+        cells[(static_cast<size_t>(cidx(a, 2)) * nc[1] + cidx(a, 1)) * nc[0] + cidx(a, 0)].push_back(a);
+    std::vector<std::vector<int>> nb(na);
+    parallel_for(na, [&](int a) {
+        int c0 = cidx(a, 0), c1 = cidx(a, 1), c2 = cidx(a, 2);
+        const double* pa = &s->pos[3 * a];
+        for (int z = std::max(0, c2 - 1); z <= std::min(nc[2] - 1, c2 + 1); ++z)
+            for (int y = std::max(0, c1 - 1); y <= std::min(nc[1] - 1, c1 + 1); ++y)
+                for (int x = std::max(0, c0 - 1); x <= std::min(nc[0] - 1, c0 + 1); ++x)
+                    for (int b : cells[(static_cast<size_t>(z) * nc[1] + y) * nc[0] + x]) {
+                        double c = s->pair_mode == LSW_PAIR_SUM_OF_RADII ? s->r_loc[b] + s->r_loc[a]
+                                                                          : s->cutoff;
+                        if (d2_of(s->pos[3 * b], s->pos[3 * b + 1], s->pos[3 * b + 2], pa) <= c * c)
+                            nb[a].push_back(b);
+                    }
+        std::sort(nb[a].begin(), nb[a].end());
+    });
+    std::vector<int64_t> first(na + 1, 0);
+    for (int a = 0; a < na; ++a) first[a + 1] = first[a] + s->nsf[a];
+    const int64_t nf = first[na];
+    s->row_ptr.assign(nf + 1, 0);
+    for (int64_t f = 0; f < nf; ++f) {
+        int a = s->sf_atom[f];
+        int64_t cnt = 0;
+        for (int b : nb[a]) cnt += s->nsf[b];
+        s->row_ptr[f + 1] = s->row_ptr[f] + cnt;
+    }
+    s->col.resize(s->row_ptr[nf]);
+    for (int64_t f = 0; f < nf; ++f) {
+        int a = s->sf_atom[f];
+        int64_t k = s->row_ptr[f];
+        for (int b : nb[a])
+            for (int64_t q = first[b]; q < first[b + 1]; ++q) s->col[k++] = static_cast<int32_t>(q);
+    }
+    return LSW_OK;
+}
+
+int64_t align64(int64_t x) { return (x + ALIGN_ELEMS - 1) / ALIGN_ELEMS * ALIGN_ELEMS; }
+
+// smem bytes of the three pass kernels for a function record
+void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, size_t* bwd) {
+    const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29, Z = 2 * r.n[2] + 29;
+    *fwd = es * static_cast<size_t>(4 * r.n[1] * r.n[0] + 2 * r.n[1] * X);
+    *z = es * static_cast<size_t>((2 * r.n[2] + Z) * zcols);
+    *bwd = es * static_cast<size_t>(Y * X + 2 * r.np[1] * X);
+}
+
+lsw_status build_plans(lsw_system_s* s) {
+    const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+    const int zcols = s->prec == LSW_FP64 ? 64 : 128;
+    std::vector<FnRec> recs(nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        FnRec& r = recs[f];
+        int a = s->sf_atom[f];
+        r.f = static_cast<int32_t>(f);
+        r.atom = a;
+        for (int d = 0; d < 3; ++d) {
+            r.lo[d] = s->L[a].lo[d];
+            r.n[d] = s->L[a].n[d];
+            r.lop[d] = s->Lp[a].lo[d];
+            r.np[d] = s->Lp[a].n[d];
+        }
+        r.off_phi = s->off_L[f];
+        r.off_hphi = s->off_Lp[f];
+    }
+    s->batches.clear();
+    int64_t ws_max = 0;
+    for (int64_t f0 = 0; f0 < nf; f0 += s->batch_size) {
+        Batch b;
+        b.fn0 = f0;
+        b.nfn = std::min<int64_t>(s->batch_size, nf - f0);
+        HphiLaunch& p = b.proto;
+        std::memset(&p, 0, sizeof(p));
+        p.prec = s->prec;
+        p.nfn = static_cast<int>(b.nfn);
+        p.zcols = zcols;
+        int64_t o = 0;
+        for (int64_t f = f0; f < f0 + b.nfn; ++f) {
+            recs[f].ws_D = o;
+            o += align64(8LL * recs[f].n[0] * recs[f].n[1] * recs[f].n[2]);
+        }
+        p.ws_D_elems = o;
+        for (int64_t f = f0; f < f0 + b.nfn; ++f) {
+            const FnRec& r = recs[f];
+            const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+            recs[f].ws_Bf = o;
+            o += align64(2LL * r.n[2] * Y * X);
+            recs[f].ws_Bb = o;
+            o += align64(2LL * r.np[2] * Y * X);
+            recs[f].ws_G = o;
+            o += align64(8LL * r.np[0] * r.np[1] * r.np[2]);
+        }
+        ws_max = std::max(ws_max, o);
+        for (int64_t f = f0; f < f0 + b.nfn; ++f) {
+            const FnRec& r = recs[f];
+            const LocregHost& Lh = s->L[r.atom];
+            const LocregHost& Ph = s->Lp[r.atom];
+            p.max_nz = std::max(p.max_nz, r.n[2]);
+            p.max_nzp = std::max(p.max_nzp, r.np[2]);
+            p.max_cols = std::max<int>(p.max_cols, (2 * r.n[1] + 29) * (2 * r.n[0] + 29));
+            p.max_rowsP = std::max(p.max_rowsP, r.np[1] * r.np[2]);
+            p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
+            p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
+            p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
+            size_t a1, a2, a3;
+            pass_smem(r, s->esize, zcols, &a1, &a2, &a3);
+            p.smem_fwd = std::max(p.smem_fwd, a1);
+            p.smem_z = std::max(p.smem_z, a2);
+            p.smem_bwd = std::max(p.smem_bwd, a3);
+        }
+        if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd > s->ctx->max_smem)
+            return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles (%zu/%zu/%zu > %zu bytes)",
+                        p.smem_fwd, p.smem_z, p.smem_bwd, s->ctx->max_smem);
+        s->batches.push_back(b);
+    }
+    s->ws_elems = ws_max;
+    cudaStream_t st = s->ctx->stream;
+    CUDA_TRY(s->d_fn.upload(recs, st));
+    for (auto& b : s->batches) b.proto.fn = static_cast<const FnRec*>(s->d_fn.p) + b.fn0;
+    CUDA_TRY(s->d_ws.alloc(static_cast<size_t>(ws_max) * s->esize));
+    return LSW_OK;
+}
+
+lsw_status build_hs_plan(lsw_system_s* s) {
+    const int T = s->tile;
+    const int32_t* N = s->N;
+    const int nt[3] = {(N[0] + T - 1) / T, (N[1] + T - 1) / T, (N[2] + T - 1) / T};
+    const int64_t ntiles = static_cast<int64_t>(nt[0]) * nt[1] * nt[2];
+    const int na = s->n_atoms;
+    auto tiles_of = [&](const RegionHost& r, std::vector<int64_t>* out) {
+        out->clear();
+        for (size_t q = 0; q < r.keys.size() / 3; ++q) {
+            int64_t g0 = r.keys[3 * q], g1 = r.keys[3 * q + 1];
+            int64_t i1 = g0 % N[0], i2 = (g0 / N[0]) % N[1], i3 = g0 / (static_cast<int64_t>(N[0]) * N[1]);
+            int64_t x1 = i1 + (g1 - g0);
+            for (int64_t tx = i1 / T; tx <= x1 / T; ++tx)
+                out->push_back(tx + nt[0] * ((i2 / T) + static_cast<int64_t>(nt[1]) * (i3 / T)));
+        }
+        std::sort(out->begin(), out->end());
+        out->erase(std::unique(out->begin(), out->end()), out->end());
+    };
+    std::vector<std::vector<int64_t>> tA(na), tB(na);
+    parallel_for(na, [&](int a) {
+        tiles_of(s->L[a].c, &tA[a]);
+        tiles_of(s->Lp[a].c, &tB[a]);
+    });
+    std::vector<int64_t> first(na + 1, 0);
+    for (int a = 0; a < na; ++a) first[a + 1] = first[a] + s->nsf[a];
+    // tile -> functions (through their atoms), counting sort
+    auto invert = [&](const std::vector<std::vector<int64_t>>& t, std::vector<int64_t>* ptr,
+                      std::vector<int32_t>* fl) {
+        ptr->assign(ntiles + 1, 0);
+        for (int a = 0; a < na; ++a)
+            for (int64_t x : t[a]) (*ptr)[x + 1] += s->nsf[a];
+        for (int64_t i = 0; i < ntiles; ++i) (*ptr)[i + 1] += (*ptr)[i];
+        fl->resize((*ptr)[ntiles]);
+        std::vector<int64_t> fill(ptr->begin(), ptr->end() - 1);
+        for (int a = 0; a < na; ++a)
+            for (int64_t x : t[a])
+                for (int64_t f = first[a]; f < first[a + 1]; ++f) (*fl)[fill[x]++] = static_cast<int32_t>(f);
+    };
+    std::vector<int64_t> pA, pB;
+    std::vector<int32_t> fA, fB;
+    invert(tA, &pA, &fA);
+    invert(tB, &pB, &fB);
+    std::vector<int32_t> org, fine;
+    std::vector<HSWork> work;
+    int32_t used = 0;
+    const int BLK = 32;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        int64_t na_t = pA[t + 1] - pA[t], nb_t = pB[t + 1] - pB[t];
+        if (na_t == 0 || nb_t == 0) continue;
+        int tx = static_cast<int>(t % nt[0]);
+        int ty = static_cast<int>((t / nt[0]) % nt[1]);
+        int tz = static_cast<int>(t / (static_cast<int64_t>(nt[0]) * nt[1]));
+        org.push_back(tx * T);
+        org.push_back(ty * T);
+        org.push_back(tz * T);
+        org.push_back(static_cast<int32_t>(fine.size()));
+        for (int z = 0; z < T; ++z)
+            for (int y = 0; y < T; ++y)
+                for (int x = 0; x < T; ++x) {
+                    int64_t gx = tx * T + x, gy = ty * T + y, gz = tz * T + z;
+                    if (gx >= N[0] || gy >= N[1] || gz >= N[2]) continue;
+                    int64_t g = gx + static_cast<int64_t>(N[0]) * (gy + static_cast<int64_t>(N[1]) * gz);
+                    if (s->fine_mask[g]) fine.push_back(x | (y << 8) | (z << 16));
+                }
+        for (int64_t a0 = pA[t]; a0 < pA[t + 1]; a0 += BLK)
+            for (int64_t b0 = pB[t]; b0 < pB[t + 1]; b0 += BLK) {
+                HSWork w;
+                w.tile = used;
+                w.a0 = static_cast<int32_t>(a0);
+                w.na = static_cast<int32_t>(std::min<int64_t>(BLK, pA[t + 1] - a0));
+                w.b0 = static_cast<int32_t>(b0);
+                w.nb = static_cast<int32_t>(std::min<int64_t>(BLK, pB[t + 1] - b0));
+                w.pad = 0;
+                work.push_back(w);
+            }
+        ++used;
+    }
+    org.push_back(0);
+    org.push_back(0);
+    org.push_back(0);
+    org.push_back(static_cast<int32_t>(fine.size()));  // sentinel: end of the last fine list
+    cudaStream_t st = s->ctx->stream;
+    CUDA_TRY(s->d_tile_org.upload(org, st));
+    CUDA_TRY(s->d_tile_fine.upload(fine, st));
+    CUDA_TRY(s->d_listA.upload(fA, st));
+    CUDA_TRY(s->d_listB.upload(fB, st));
+    CUDA_TRY(s->d_work.upload(work, st));
+    s->nwork = static_cast<int>(work.size());
+    return LSW_OK;
+}
+
+lsw_status upload_geometry(lsw_system_s* s) {
+    std::vector<AtomRec> recs(s->n_atoms);
+    std::vector<Seg> seg;
+    std::vector<int32_t> rowptr;
+    for (int a = 0; a < s->n_atoms; ++a) {
+        AtomRec& r = recs[a];
+        const LocregHost& L = s->L[a];
+        const LocregHost& P = s->Lp[a];
+        for (int d = 0; d < 3; ++d) {
+            r.lo[d] = L.lo[d];
+            r.n[d] = L.n[d];
+            r.lop[d] = P.lo[d];
+            r.np[d] = P.n[d];
+        }
+        r.ncL = static_cast<int32_t>(L.c.g.size());
+        r.nfL = static_cast<int32_t>(L.f.g.size());
+        r.ncP = static_cast<int32_t>(P.c.g.size());
+        r.nfP = static_cast<int32_t>(P.f.g.size());
+        emit_segments(s->N, L, L.c, &seg, &rowptr, &r.segLc, &r.nsegLc, &r.rowLc);
+        emit_segments(s->N, L, L.f, &seg, &rowptr, &r.segLf, &r.nsegLf, &r.rowLf);
+        emit_segments(s->N, P, P.c, &seg, &rowptr, &r.segPc, &r.nsegPc, &r.rowPc);
+        emit_segments(s->N, P, P.f, &seg, &rowptr, &r.segPf, &r.nsegPf, &r.rowPf);
+    }
+    cudaStream_t st = s->ctx->stream;
+    CUDA_TRY(s->d_atoms.upload(recs, st));
+    CUDA_TRY(s->d_seg.upload(seg, st));
+    CUDA_TRY(s->d_rowptr.upload(rowptr, st));
+    CUDA_TRY(s->d_offL.upload(s->off_L, st));
+    CUDA_TRY(s->d_offLp.upload(s->off_Lp, st));
+    CUDA_TRY(s->d_sfatom.upload(s->sf_atom, st));
+    CUDA_TRY(s->d_rowp.upload(s->row_ptr, st));
+    CUDA_TRY(s->d_col.upload(s->col, st));
+    return LSW_OK;
+}
+
+void drop_graphs(lsw_system_s* s) {
+    for (auto& kv : s->graphs_h) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& kv : s->graphs_m) cudaGraphExecDestroy(kv.second.exec);
+    s->graphs_h.clear();
+    s->graphs_m.clear();
+}
+
+// fold the elapsed times of a tracer's recorded pairs into the system's totals
+void harvest(lsw_system_s* s, Tracer* tr) {
+    if (!tr || !tr->pending) return;
+    for (size_t i = 0; i < tr->used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, tr->ev[i].a, tr->ev[i].b) == cudaSuccess) {
+            s->prof_ms[tr->ev[i].kind] += ms;
+            s->prof_n[tr->ev[i].kind] += 1;
+        }
+    }
+    tr->pending = false;
+}
+
+lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hphi, double* ek, double* ep) {
+    cudaStream_t st = s->ctx->stream;
+    const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+    CUDA_TRY(cudaMemsetAsync(ek, 0, nf * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(ep, 0, nf * sizeof(double), st));
+    for (const Batch& b : s->batches) {
+        HphiLaunch p = b.proto;
+        p.tr = tr;
+        p.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
+        p.seg = static_cast<const Seg*>(s->d_seg.p);
+        p.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
+        p.phi = phi;
+        p.hphi = hphi;
+        p.e_kin = ek;
+        p.e_pot = ep;
+        p.V = s->V;
+        for (int d = 0; d < 3; ++d) {
+            p.vlo[d] = s->vlo[d];
+            p.vn[d] = s->vn[d];
+        }
+        p.ws = s->d_ws.p;
+        p.kin_scale = -1.0 / (2.0 * s->h * s->h);
+        p.status = static_cast<int*>(s->d_status.p);
+        CUDA_TRY(enqueue_hphi_batch(p, st));
+    }
+    return LSW_OK;
+}
+
+lsw_status enqueue_matrices(lsw_system_s* s, Tracer* tr, const void* phi, const void* hphi, double* H, double* S) {
+    cudaStream_t st = s->ctx->stream;
+    const int64_t nnz = static_cast<int64_t>(s->col.size());
+    CUDA_TRY(cudaMemsetAsync(H, 0, nnz * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(S, 0, nnz * sizeof(double), st));
+    if (s->nwork == 0) return LSW_OK;
+    HSLaunch p;
+    std::memset(&p, 0, sizeof(p));
+    p.tr = tr;
+    p.prec = s->prec;
+    p.work = static_cast<const HSWork*>(s->d_work.p);
+    p.nwork = s->nwork;
+    p.tile_org = static_cast<const int32_t*>(s->d_tile_org.p);
+    p.tile_fine = static_cast<const int32_t*>(s->d_tile_fine.p);
+    p.listA = static_cast<const int32_t*>(s->d_listA.p);
+    p.listB = static_cast<const int32_t*>(s->d_listB.p);
+    p.sf_atom = static_cast<const int32_t*>(s->d_sfatom.p);
+    p.off_L = static_cast<const int64_t*>(s->d_offL.p);
+    p.off_Lp = static_cast<const int64_t*>(s->d_offLp.p);
+    p.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
+    p.seg = static_cast<const Seg*>(s->d_seg.p);
+    p.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
+    p.row_ptr = static_cast<const int64_t*>(s->d_rowp.p);
+    p.col = static_cast<const int32_t*>(s->d_col.p);
+    p.phi = phi;
+    p.hphi = hphi;
+    p.H = H;
+    p.S = S;
+    p.tile = s->tile;
+    p.status = static_cast<int*>(s->d_status.p);
+    CUDA_TRY(enqueue_hs(p, st));
+    return LSW_OK;
+}
+
+// Run `enq(tracer)` directly, or through a cached CUDA graph keyed by the buffer
+// pointers; with profiling on, event pairs are recorded around every launch (captured
+// as external event-record nodes inside graphs).
+template <class Enq>
+lsw_status run_maybe_graph(lsw_system_s* s, std::map<GraphKey, lsw_system_s::GraphEntry>* cache, GraphKey key,
+                           Enq enq) {
+    cudaStream_t st = s->ctx->stream;
+    if (!s->use_graph || st == nullptr) {
+        Tracer* tr = nullptr;
+        if (s->profiling) {
+            if (!s->direct_tr) s->direct_tr.reset(new Tracer());
+            tr = s->direct_tr.get();
+            if (!tr->pending) tr->used = 0;
+        }
+        return enq(tr);
+    }
+    auto it = cache->find(key);
+    if (it == cache->end()) {
+        lsw_system_s::GraphEntry ge;
+        if (s->profiling) {
+            ge.tr.reset(new Tracer());
+            ge.tr->capturing = true;
+        }
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        lsw_status rs = enq(ge.tr.get());
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (ge.tr) {
+            ge.tr->capturing = false;
+            ge.tr->pending = false;
+        }
+        if (rs != LSW_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rs;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        it = cache->emplace(key, std::move(ge)).first;
+    }
+    if (it->second.tr) harvest(s, it->second.tr.get());  // a previous replay not read yet
+    CUDA_TRY(cudaGraphLaunch(it->second.exec, st));
+    if (it->second.tr) it->second.tr->pending = true;
+    return LSW_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+const char* lsw_last_error(void) { return g_err.c_str(); }
+
+lsw_status lsw_ctx_create(int device, void* stream, lsw_ctx* out) {
+    g_err.clear();
+    if (!out) return fail(LSW_ERR_ARG, "lsw_ctx_create: out is NULL");
+    *out = nullptr;
+    if (device == LSW_HOST_ONLY) {
+        std::unique_ptr<lsw_ctx_s> c(new (std::nothrow) lsw_ctx_s());
+        if (!c) return fail(LSW_ERR_OOM, "lsw_ctx_create: host allocation");
+        c->host_only = true;
+        c->device = LSW_HOST_ONLY;
+        std::string err;
+        if (!derive_filters(&c->filters, &err)) return fail(LSW_ERR_STATE, "filter derivation: %s", err.c_str());
+        *out = c.release();
+        return LSW_OK;
+    }
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(LSW_ERR_ARG, "lsw_ctx_create: device %d of %d", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+    std::unique_ptr<lsw_ctx_s> c(new (std::nothrow) lsw_ctx_s());
+    if (!c) return fail(LSW_ERR_OOM, "lsw_ctx_create: host allocation");
+    c->device = device;
+    std::string err;
+    if (!derive_filters(&c->filters, &err)) return fail(LSW_ERR_STATE, "filter derivation: %s", err.c_str());
+    int smem = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    CUDA_TRY(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device));
+    c->max_smem = static_cast<size_t>(smem);
+    c->stream = static_cast<cudaStream_t>(stream);  // NULL: the legacy default stream
+    CUDA_TRY(upload_filters(c->filters, device));
+    CUDA_TRY(configure_kernels(c->max_smem));
+    *out = c.release();
+    return LSW_OK;
+}
+
+lsw_status lsw_ctx_destroy(lsw_ctx ctx) {
+    g_err.clear();
+    if (!ctx) return LSW_OK;
+    if (ctx->live_systems != 0) return fail(LSW_ERR_STATE, "lsw_ctx_destroy: %d systems alive", ctx->live_systems);
+    if (!ctx->host_only && ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LSW_OK;
+}
+
+lsw_status lsw_filter_table(lsw_ctx ctx, int32_t which, int32_t* first, int32_t* count, double* values) {
+    g_err.clear();
+    if (!ctx || !first || !count || !values) return fail(LSW_ERR_ARG, "lsw_filter_table: NULL argument");
+    const FilterSet& f = ctx->filters;
+    const double* src = nullptr;
+    int lo = 0, n = 0;
+    switch (which) {
+        case LSW_FILTER_H: src = f.h, lo = H_LO, n = D16; break;
+        case LSW_FILTER_G: src = f.g, lo = H_LO, n = D16; break;
+        case LSW_FILTER_MOMENTS: src = f.moments, lo = 0, n = D16; break;
+        case LSW_FILTER_MAGIC: src = f.magic, lo = H_LO, n = D16; break;
+        case LSW_FILTER_KIN_R: src = f.kin_r, lo = -KIN_HALF, n = KIN_TAPS; break;
+        case LSW_FILTER_KIN_HH: case LSW_FILTER_KIN_HG: case LSW_FILTER_KIN_GH: case LSW_FILTER_KIN_GG:
+            src = f.kin[which - LSW_FILTER_KIN_HH], lo = -KIN_HALF, n = KIN_TAPS; break;
+        case LSW_FILTER_FWD_H: case LSW_FILTER_FWD_G:
+            src = f.fwd[which - LSW_FILTER_FWD_H], lo = FWD_LO, n = FWD_TAPS; break;
+        default: return fail(LSW_ERR_ARG, "lsw_filter_table: unknown table %d", which);
+    }
+    *first = lo;
+    *count = n;
+    std::memcpy(values, src, n * sizeof(double));
+    return LSW_OK;
+}
+
+lsw_status lsw_system_create(lsw_ctx ctx, const lsw_system_desc* d, lsw_system* out) {
+    g_err.clear();
+    if (!ctx || !d || !out) return fail(LSW_ERR_ARG, "lsw_system_create: NULL argument");
+    *out = nullptr;
+    if (d->N[0] < 1 || d->N[1] < 1 || d->N[2] < 1 || d->N[0] > 4096 || d->N[1] > 4096 || d->N[2] > 4096)
+        return fail(LSW_ERR_ARG, "lsw_system_create: grid %d x %d x %d out of range", d->N[0], d->N[1], d->N[2]);
+    if (static_cast<double>(d->N[0]) * d->N[1] * d->N[2] > 2.0e9)
+        return fail(LSW_ERR_ARG, "lsw_system_create: grid has more than 2e9 points");
+    if (!(d->h > 0) || !std::isfinite(d->h)) return fail(LSW_ERR_ARG, "lsw_system_create: h must be > 0");
+    if (d->n_atoms < 1 || !d->pos || !d->r_loc || !d->r_fine || !d->n_sf)
+        return fail(LSW_ERR_ARG, "lsw_system_create: no atoms or NULL atom arrays");
+    if (d->precision != LSW_FP64 && d->precision != LSW_FP32)
+        return fail(LSW_ERR_ARG, "lsw_system_create: precision %d", d->precision);
+    if (d->fine_mode != LSW_FINE_UNION && d->fine_mode != LSW_FINE_OWN)
+        return fail(LSW_ERR_ARG, "lsw_system_create: fine_mode %d", d->fine_mode);
+    if (d->pair_mode != LSW_PAIR_CUTOFF && d->pair_mode != LSW_PAIR_SUM_OF_RADII)
+        return fail(LSW_ERR_ARG, "lsw_system_create: pair_mode %d", d->pair_mode);
+    if (!(d->lprime_margin >= 0) || !std::isfinite(d->lprime_margin))
+        return fail(LSW_ERR_ARG, "lsw_system_create: lprime_margin must be >= 0");
+    if (d->pair_mode == LSW_PAIR_CUTOFF && (!(d->pair_cutoff >= 0) || !std::isfinite(d->pair_cutoff)))
+        return fail(LSW_ERR_ARG, "lsw_system_create: pair_cutoff must be >= 0");
+    for (int a = 0; a < d->n_atoms; ++a) {
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(d->pos[3 * a + k])) return fail(LSW_ERR_ARG, "atom %d: position not finite", a);
+        if (!(d->r_loc[a] > 0) || !std::isfinite(d->r_loc[a])) return fail(LSW_ERR_ARG, "atom %d: r_loc must be > 0", a);
+        if (!(d->r_fine[a] >= 0) || !std::isfinite(d->r_fine[a])) return fail(LSW_ERR_ARG, "atom %d: r_fine must be >= 0", a);
+        if (d->n_sf[a] < 0 || d->n_sf[a] > 64) return fail(LSW_ERR_ARG, "atom %d: n_sf %d", a, d->n_sf[a]);
+    }
+    if (!ctx->host_only) CUDA_TRY(cudaSetDevice(ctx->device));
+    std::unique_ptr<lsw_system_s> s(new (std::nothrow) lsw_system_s());
+    if (!s) return fail(LSW_ERR_OOM, "lsw_system_create: host allocation");
+    s->ctx = ctx;
+    for (int k = 0; k < 3; ++k) s->N[k] = d->N[k];
+    s->h = d->h;
+    s->prec = d->precision;
+    s->esize = s->prec == LSW_FP64 ? 8 : 4;
+    s->n_atoms = d->n_atoms;
+    s->pos.assign(d->pos, d->pos + 3 * d->n_atoms);
+    s->r_loc.assign(d->r_loc, d->r_loc + d->n_atoms);
+    s->r_fine.assign(d->r_fine, d->r_fine + d->n_atoms);
+    s->nsf.assign(d->n_sf, d->n_sf + d->n_atoms);
+    s->margin = d->lprime_margin;
+    s->cutoff = d->pair_cutoff;
+    s->pair_mode = d->pair_mode;
+    s->fine_mode = d->fine_mode;
+    s->batch_size = s->prec == LSW_FP64 ? 16 : 32;
+    for (int a = 0; a < s->n_atoms; ++a)
+        for (int k = 0; k < s->nsf[a]; ++k) s->sf_atom.push_back(a);
+    if (s->sf_atom.empty()) return fail(LSW_ERR_ARG, "lsw_system_create: no support functions");
+    try {
+        // global fine region: union of the fine spheres (Sec. II.B)
+        const int64_t npts = static_cast<int64_t>(s->N[0]) * s->N[1] * s->N[2];
+        s->fine_mask.assign(npts, 0);
+        for (int a = 0; a < s->n_atoms; ++a) {
+            const double* c = &s->pos[3 * a];
+            const double R = s->r_fine[a];
+            const double R2 = R * R;
+            int lo[3], hi[3];
+            sphere_bounds(s->N, s->h, c, R, lo, hi);
+            for (int k = lo[2]; k <= hi[2]; ++k)
+                for (int j = lo[1]; j <= hi[1]; ++j)
+                    for (int i = lo[0]; i <= hi[0]; ++i) {
+                        double x = static_cast<double>(i) * s->h, y = static_cast<double>(j) * s->h,
+                               z = static_cast<double>(k) * s->h;
+                        if (d2_of(x, y, z, c) <= R2)
+                            s->fine_mask[i + static_cast<int64_t>(s->N[0]) * (j + static_cast<int64_t>(s->N[1]) * k)] = 1;
+                    }
+        }
+        s->L.resize(s->n_atoms);
+        s->Lp.resize(s->n_atoms);
+        lsw_system_s* sp = s.get();
+        parallel_for(s->n_atoms, [&](int a) {
+            build_locreg(sp, sp->fine_mask, a, sp->r_loc[a], &sp->L[a]);
+            const double Rp = sp->r_loc[a] + sp->margin * sp->h;
+            build_locreg(sp, sp->fine_mask, a, Rp, &sp->Lp[a]);
+        });
+        for (int a = 0; a < s->n_atoms; ++a)
+            if (s->nsf[a] > 0 && s->L[a].c.g.empty())
+                return fail(LSW_ERR_ARG, "atom %d: its locreg holds no grid point", a);
+        const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+        s->off_L.assign(nf + 1, 0);
+        s->off_Lp.assign(nf + 1, 0);
+        for (int64_t f = 0; f < nf; ++f) {
+            int a = s->sf_atom[f];
+            int64_t nL = static_cast<int64_t>(s->L[a].c.g.size() + 7 * s->L[a].f.g.size());
+            int64_t nP = static_cast<int64_t>(s->Lp[a].c.g.size() + 7 * s->Lp[a].f.g.size());
+            s->off_L[f + 1] = s->off_L[f] + align64(nL);
+            s->off_Lp[f + 1] = s->off_Lp[f] + align64(nP);
+        }
+        lsw_status st = build_pattern(s.get());
+        if (st != LSW_OK) return st;
+        if (ctx->host_only) {
+            ctx->live_systems++;
+            *out = s.release();
+            return LSW_OK;
+        }
+        st = upload_geometry(s.get());
+        if (st != LSW_OK) return st;
+        st = build_plans(s.get());
+        if (st != LSW_OK) return st;
+        st = build_hs_plan(s.get());
+        if (st != LSW_OK) return st;
+    } catch (const std::bad_alloc&) {
+        return fail(LSW_ERR_OOM, "lsw_system_create: host allocation");
+    }
+    CUDA_TRY(s->d_status.alloc(sizeof(int)));
+    CUDA_TRY(cudaMemset(s->d_status.p, 0, sizeof(int)));
+    CUDA_TRY(s->d_escratch.alloc(2 * s->sf_atom.size() * sizeof(double)));
+    CUDA_TRY(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
+    ctx->live_systems++;
+    *out = s.release();
+    return LSW_OK;
+}
+
+lsw_status lsw_system_destroy(lsw_system sys) {
+    g_err.clear();
+    if (!sys) return LSW_OK;
+    if (!sys->ctx->host_only) cudaSetDevice(sys->ctx->device);
+    drop_graphs(sys);
+    if (sys->done) cudaEventDestroy(sys->done);
+    sys->ctx->live_systems--;
+    delete sys;
+    return LSW_OK;
+}
+
+lsw_status lsw_system_layout(lsw_system sys, int64_t* n_sf, int64_t* total_L, int64_t* total_Lp,
+                             const int64_t** off_L, const int64_t** off_Lp, const int32_t** sf_atom) {
+    g_err.clear();
+    if (!sys) return fail(LSW_ERR_ARG, "lsw_system_layout: NULL system");
+    if (n_sf) *n_sf = static_cast<int64_t>(sys->sf_atom.size());
+    if (total_L) *total_L = sys->off_L.back();
+    if (total_Lp) *total_Lp = sys->off_Lp.back();
+    if (off_L) *off_L = sys->off_L.data();
+    if (off_Lp) *off_Lp = sys->off_Lp.data();
+    if (sf_atom) *sf_atom = sys->sf_atom.data();
+    return LSW_OK;
+}
+
+lsw_status lsw_system_keys(lsw_system sys, int32_t atom, int32_t region, int32_t part, int64_t* nseg,
+                           const int64_t** keys) {
+    g_err.clear();
+    if (!sys || !nseg || !keys) return fail(LSW_ERR_ARG, "lsw_system_keys: NULL argument");
+    if (atom < 0 || atom >= sys->n_atoms) return fail(LSW_ERR_ARG, "lsw_system_keys: atom %d", atom);
+    if (region != LSW_REGION_L && region != LSW_REGION_LP) return fail(LSW_ERR_ARG, "lsw_system_keys: region %d", region);
+    if (part != LSW_PART_COARSE && part != LSW_PART_FINE) return fail(LSW_ERR_ARG, "lsw_system_keys: part %d", part);
+    const LocregHost& L = region == LSW_REGION_L ? sys->L[atom] : sys->Lp[atom];
+    const RegionHost& r = part == LSW_PART_COARSE ? L.c : L.f;
+    *nseg = static_cast<int64_t>(r.keys.size() / 3);
+    *keys = r.keys.data();
+    return LSW_OK;
+}
+
+lsw_status lsw_pattern(lsw_system sys, int64_t* nnz, const int64_t** row_ptr, const int32_t** col) {
+    g_err.clear();
+    if (!sys) return fail(LSW_ERR_ARG, "lsw_pattern: NULL system");
+    if (nnz) *nnz = static_cast<int64_t>(sys->col.size());
+    if (row_ptr) *row_ptr = sys->row_ptr.data();
+    if (col) *col = sys->col.data();
+    return LSW_OK;
+}
+
+lsw_status lsw_set_potential(lsw_system sys, const void* V_dev, const int64_t fine_lo[3], const int64_t fine_dims[3]) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !V_dev || !fine_lo || !fine_dims) return fail(LSW_ERR_ARG, "lsw_set_potential: NULL argument");
+    for (int d = 0; d < 3; ++d) {
+        const int64_t need_lo = -V_REACH, need_hi = 2LL * sys->N[d] + V_REACH;
+        if (fine_dims[d] < 1 || fine_lo[d] > need_lo || fine_lo[d] + fine_dims[d] - 1 < need_hi)
+            return fail(LSW_ERR_ARG, "lsw_set_potential: dimension %d covers [%lld, %lld], needs [%lld, %lld]", d,
+                        static_cast<long long>(fine_lo[d]), static_cast<long long>(fine_lo[d] + fine_dims[d] - 1),
+                        static_cast<long long>(need_lo), static_cast<long long>(need_hi));
+    }
+    if (sys->V != V_dev) drop_graphs(sys);
+    for (int d = 0; d < 3; ++d) {
+        if (sys->vlo[d] != fine_lo[d] || sys->vn[d] != fine_dims[d]) drop_graphs(sys);
+        sys->vlo[d] = fine_lo[d];
+        sys->vn[d] = fine_dims[d];
+    }
+    sys->V = V_dev;
+    return LSW_OK;
+}
+
+lsw_status lsw_apply_hamiltonian(lsw_system sys, const void* phi, void* hphi, double* ek, double* ep) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !phi || !hphi) return fail(LSW_ERR_ARG, "lsw_apply_hamiltonian: NULL buffer");
+    if (!sys->V) return fail(LSW_ERR_STATE, "lsw_apply_hamiltonian: no potential (lsw_set_potential)");
+    const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
+    double* e0 = static_cast<double*>(sys->d_escratch.p);
+    if (!ek) ek = e0;
+    if (!ep) ep = e0 + nf;
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    GraphKey key{phi, hphi, ek, ep};
+    return run_maybe_graph(sys, &sys->graphs_h, key, [&](Tracer* tr) { return enqueue_apply(sys, tr, phi, hphi, ek, ep); });
+}
+
+lsw_status lsw_build_matrices(lsw_system sys, const void* phi, const void* hphi, double* H, double* S) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !phi || !hphi || !H || !S) return fail(LSW_ERR_ARG, "lsw_build_matrices: NULL buffer");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    GraphKey key{phi, hphi, H, S};
+    return run_maybe_graph(sys, &sys->graphs_m, key, [&](Tracer* tr) { return enqueue_matrices(sys, tr, phi, hphi, H, S); });
+}
+
+lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
+    g_err.clear();
+    if (!sys || !bytes) return fail(LSW_ERR_ARG, "lsw_workspace_bytes: NULL argument");
+    const DeviceBuf* bufs[] = {&sys->d_atoms, &sys->d_seg, &sys->d_rowptr, &sys->d_fn, &sys->d_offL, &sys->d_offLp,
+                               &sys->d_sfatom, &sys->d_rowp, &sys->d_col, &sys->d_tile_org, &sys->d_tile_fine,
+                               &sys->d_listA, &sys->d_listB, &sys->d_work, &sys->d_ws, &sys->d_status,
+                               &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
+                               &sys->d_ep};
+    int64_t b = 0;
+    for (auto* p : bufs) b += static_cast<int64_t>(p->bytes);
+    *bytes = b;
+    return LSW_OK;
+}
+
+lsw_status lsw_sync(lsw_system sys, double timeout_s) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys) return fail(LSW_ERR_ARG, "lsw_sync: NULL system");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    CUDA_TRY(cudaEventRecord(sys->done, sys->ctx->stream));
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(sys->done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "lsw_sync");
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(LSW_ERR_TIMEOUT, "lsw_sync: not finished after %.3f s", el);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, sys->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        cudaMemset(sys->d_status.p, 0, sizeof(int));
+        return fail(LSW_ERR_STATE, "device-side check failed (status bits 0x%x)", st);
+    }
+    return LSW_OK;
+}
+
+lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host, double* H_host, double* S_host,
+                         double* ek_host, double* ep_host) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !phi_host || !H_host || !S_host) return fail(LSW_ERR_ARG, "lsw_step_host: NULL argument");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
+    const size_t bphi = static_cast<size_t>(sys->off_L.back()) * sys->esize;
+    const size_t bhphi = static_cast<size_t>(sys->off_Lp.back()) * sys->esize;
+    const size_t bnnz = sys->col.size() * sizeof(double);
+    if (!sys->d_phi.p) {
+        CUDA_TRY(sys->d_phi.alloc(bphi));
+        CUDA_TRY(sys->d_hphi.alloc(bhphi));
+        CUDA_TRY(sys->d_H.alloc(std::max<size_t>(bnnz, 8)));
+        CUDA_TRY(sys->d_S.alloc(std::max<size_t>(bnnz, 8)));
+        CUDA_TRY(sys->d_ek.alloc(nf * sizeof(double)));
+        CUDA_TRY(sys->d_ep.alloc(nf * sizeof(double)));
+    }
+    cudaStream_t st = sys->ctx->stream;
+    CUDA_TRY(cudaMemcpyAsync(sys->d_phi.p, phi_host, bphi, cudaMemcpyHostToDevice, st));
+    lsw_status r = lsw_apply_hamiltonian(sys, sys->d_phi.p, sys->d_hphi.p, static_cast<double*>(sys->d_ek.p),
+                                         static_cast<double*>(sys->d_ep.p));
+    if (r != LSW_OK) return r;
+    r = lsw_build_matrices(sys, sys->d_phi.p, sys->d_hphi.p, static_cast<double*>(sys->d_H.p),
+                           static_cast<double*>(sys->d_S.p));
+    if (r != LSW_OK) return r;
+    CUDA_TRY(cudaMemcpyAsync(H_host, sys->d_H.p, bnnz, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(S_host, sys->d_S.p, bnnz, cudaMemcpyDeviceToHost, st));
+    if (hphi_host) CUDA_TRY(cudaMemcpyAsync(hphi_host, sys->d_hphi.p, bhphi, cudaMemcpyDeviceToHost, st));
+    if (ek_host) CUDA_TRY(cudaMemcpyAsync(ek_host, sys->d_ek.p, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (ep_host) CUDA_TRY(cudaMemcpyAsync(ep_host, sys->d_ep.p, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return lsw_sync(sys, 600.0);
+}
+
+lsw_status lsw_profile(lsw_system sys, int32_t enable) {
+    g_err.clear();
+    if (!sys) return fail(LSW_ERR_ARG, "lsw_profile: NULL system");
+    if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (enable != 0 && enable != 1) return fail(LSW_ERR_ARG, "lsw_profile: enable %d", enable);
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+    drop_graphs(sys);
+    sys->direct_tr.reset();
+    sys->profiling = enable;
+    for (int k = 0; k < TK_COUNT; ++k) sys->prof_ms[k] = 0.0, sys->prof_n[k] = 0;
+    return LSW_OK;
+}
+
+lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds, double* ms, int64_t* launches) {
+    g_err.clear();
+    if (!sys || !n_kinds || !ms || !launches) return fail(LSW_ERR_ARG, "lsw_profile_read: NULL argument");
+    if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+    harvest(sys, sys->direct_tr.get());
+    for (auto* c : {&sys->graphs_h, &sys->graphs_m})
+        for (auto& kv : *c) harvest(sys, kv.second.tr.get());
+    *n_kinds = TK_COUNT;
+    for (int k = 0; k < TK_COUNT && k < max_kinds; ++k) {
+        ms[k] = sys->prof_ms[k];
+        launches[k] = sys->prof_n[k];
+        sys->prof_ms[k] = 0.0;
+        sys->prof_n[k] = 0;
+    }
+    return LSW_OK;
+}
+
+lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !name) return fail(LSW_ERR_ARG, "lsw_set_option: NULL argument");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    if (std::strcmp(name, "batch") == 0) {
+        if (value < 1 || value > 4096) return fail(LSW_ERR_ARG, "lsw_set_option: batch %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+        drop_graphs(sys);
+        sys->batch_size = static_cast<int>(value);
+        return build_plans(sys);
+    }
+    if (std::strcmp(name, "graph") == 0) {
+        if (value != 0 && value != 1) return fail(LSW_ERR_ARG, "lsw_set_option: graph %lld", static_cast<long long>(value));
+        sys->use_graph = static_cast<int>(value);
+        return LSW_OK;
+    }
+    if (std::strcmp(name, "tile") == 0) {
+        if (value < 2 || value > 16) return fail(LSW_ERR_ARG, "lsw_set_option: tile %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+        drop_graphs(sys);
+        sys->tile = static_cast<int>(value);
+        return build_hs_plan(sys);
+    }
+    return fail(LSW_ERR_ARG, "lsw_set_option: unknown option '%s'", name);
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Internal declarations shared by the host code (lsw_host.cpp, lsw_filters.cpp) and
+// the CUDA kernels (lsw_kernels.cu).  Not part of the public ABI (include/lsw.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+namespace lsw {
+
+constexpr int D16 = 16;          // filter length 2m, m = 8 (Sec. II.B)
+constexpr int H_LO = -7;         // h, g, magic filter indices -7..8
+constexpr int KIN_HALF = 14;     // kinetic blocks l = -14..14
+constexpr int KIN_TAPS = 2 * KIN_HALF + 1;
+constexpr int FWD_LO = -14;      // combined filters (w * h), (w * g): m = -14..16
+constexpr int FWD_TAPS = 31;
+constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [2lo-14, 2hi+16]
+constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
+
+// Filter tables, FP64 (rounded once from double-double).
+struct FilterSet {
+    double h[D16], g[D16], moments[D16], magic[D16];
+    double kin_r[KIN_TAPS];
+    double kin[4][KIN_TAPS];     // hh, hg, gh, gg: <X_0|d2|Y_l>
+    double fwd[2][FWD_TAPS];     // (w*h)_m, (w*g)_m
+};
+
+// Derive the whole table (lsw_filters.cpp).  Returns false with a message on failure.
+bool derive_filters(FilterSet* out, std::string* err);
+
+// A run of members along x inside a box: x0..x1 inclusive (box-local), row = y + ny*z
+// (box-local), off = coefficient offset of x0 within its part.
+struct Seg {
+    int32_t x0, x1, row, off;
+};
+
+// Geometry of one atom's locregs as seen by the kernels.
+struct AtomRec {
+    int32_t lo[3], n[3];         // L box (coarse bounding box of the L members)
+    int32_t lop[3], np[3];       // L' box
+    int32_t ncL, nfL, ncP, nfP;  // member counts (coarse, fine) of L and L'
+    int32_t nsegLc, nsegLf, nsegPc, nsegPf;
+    int64_t segLc, segLf, segPc, segPf;  // first index in the global Seg array
+    int64_t rowLc, rowLf, rowPc, rowPf;  // first index of the per-row CSR (n_rows + 1)
+};
+
+// One support function inside an H phi batch.
+struct FnRec {
+    int32_t f, atom;
+    int32_t lo[3], n[3], lop[3], np[3];
+    int64_t off_phi, off_hphi;
+    int64_t ws_D, ws_Bf, ws_Bb, ws_G;    // element offsets inside the batch workspace
+};
+
+// One H/S work item: tile `tile`, functions listA[a0 .. a0+na) x listB[b0 .. b0+nb).
+struct HSWork {
+    int32_t tile, a0, na, b0, nb, pad;
+};
+
+// Kernel kinds of the per-launch device trace (lsw_profile / lsw_profile_read).
+enum TraceKind : int {
+    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_COMPRESS, TK_HS, TK_COUNT
+};
+
+// Host-side recorder of CUDA event pairs around launches; NULL = no tracing.
+struct Tracer;
+void trace_begin(Tracer* tr, int kind, cudaStream_t s);
+void trace_end(Tracer* tr, cudaStream_t s);
+
+struct HphiLaunch {
+    Tracer* tr;
+    int prec;                    // 0 FP64, 1 FP32
+    const FnRec* fn;             // device records of this batch
+    int nfn;
+    int max_nz, max_nzp;         // largest L / L' z extents in the batch
+    int max_cols;                // largest (2ny+29)(2nx+29) in the batch
+    int max_rowsP;               // largest ny'*nz' of L'
+    int64_t max_ptsP;            // largest nx'*ny'*nz' of L'
+    int max_segL;                // largest coarse+fine segment count of L
+    int max_segP;
+    size_t smem_fwd, smem_z, smem_bwd;
+    int zcols;                   // columns per CTA of the z stage
+    const AtomRec* atoms;
+    const Seg* seg;
+    const int32_t* rowptr;
+    const void* phi;
+    void* hphi;
+    double* e_kin;
+    double* e_pot;
+    const void* V;
+    int64_t vlo[3], vn[3];
+    void* ws;                    // batch workspace base
+    int64_t ws_D_elems;          // D region size (memset)
+    double kin_scale;            // -1 / (2 h^2)
+    int* status;
+};
+
+struct HSLaunch {
+    Tracer* tr;
+    int prec;
+    const HSWork* work;
+    int nwork;
+    const int32_t* tile_org;     // [ntiles][4]: x0, y0, z0, first fine point
+    const int32_t* tile_fine;    // fine points: local x | y << 8 | z << 16
+    const int32_t* listA;
+    const int32_t* listB;
+    const int32_t* sf_atom;
+    const int64_t* off_L;
+    const int64_t* off_Lp;
+    const AtomRec* atoms;
+    const Seg* seg;
+    const int32_t* rowptr;
+    const int64_t* row_ptr;      // pattern CSR
+    const int32_t* col;
+    const void* phi;
+    const void* hphi;
+    double* H;
+    double* S;
+    int tile;                    // tile edge (coarse points)
+    int* status;
+};
+
+// Device entry points (lsw_kernels.cu).
+cudaError_t upload_filters(const FilterSet& fs, int device);
+cudaError_t configure_kernels(size_t max_smem);
+cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s);
+cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s);
+
+// Status word bits set by device-side checks.
+enum : int {
+    ST_BAD_BOX = 1,
+    ST_BAD_SEG = 2,
+    ST_BAD_PAIR = 4,
+};
+
+}  // namespace lsw

@@ -1,0 +1,175 @@
+"""GPU parity: the sm_103a path through the C ABI against the FP64 oracle, element by
+element (tolerances of the method's reading: FP64 path 1e-12, FP32 path 1e-5, scaled
+by Cauchy-Schwarz bounds of each quantity)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import geometry as G
+from oracle import hamiltonian as Hm
+from oracle import matrices as Mx
+from paper_1401_7441_gb300 import inputs as I
+from paper_1401_7441_gb300 import lsw
+from tests.lib_support import gpu_run
+from tests.oracle_support import desc_of
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lsw.LSW_FP64: 1e-12, lsw.LSW_FP32: 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def phi_fn(wl):
+    return lambda f, a, gc, gf: I.phi_values(wl, f, a, gc, gf)
+
+
+def oracle_hphi(wl, geo, fs, V):
+    out = {}
+    for f in fs:
+        a = geo.sf_atom[f]
+        phi = I.phi_values(wl, f, a, geo.L[a].coarse.g, geo.L[a].fine.g)
+        h, ek, ep = Hm.apply_hamiltonian(geo, f, phi, V, wl.V_lo)
+        out[f] = (phi, h, ek, ep)
+    return out
+
+
+def check_functions(wl, geo, gpu, ref, tol):
+    worst = 0.0
+    for f, (phi, h, ek, ep) in ref.items():
+        o = gpu["off_Lp"][f]
+        gh = gpu["hphi"][o:o + len(h)]
+        assert np.all(np.isfinite(gh)), f          # every member of L' was written
+        err = np.linalg.norm(gh - h) / np.linalg.norm(h)
+        worst = max(worst, err)
+        assert err <= tol, (f, err)
+        scale = np.linalg.norm(phi) * np.linalg.norm(h)
+        assert abs(gpu["ek"][f] - ek) <= tol * scale, (f, gpu["ek"][f], ek)
+        assert abs(gpu["ep"][f] - ep) <= tol * scale, (f, gpu["ep"][f], ep)
+    return worst
+
+
+def check_rows(wl, geo, gpu, ref, rows, tol, h_cols=None):
+    rp, col = gpu["row_ptr"], gpu["col"]
+    for a in rows:
+        phi_a = ref[a][0]
+        for k in range(rp[a], rp[a + 1]):
+            b = int(col[k])
+            phi_b = ref[b][0] if b in ref else I.phi_values(
+                wl, b, geo.sf_atom[b], geo.L[geo.sf_atom[b]].coarse.g, geo.L[geo.sf_atom[b]].fine.g)
+            s_ref = Mx.overlap_entry(geo, a, b, phi_a, phi_b)
+            assert abs(gpu["S"][k] - s_ref) <= tol * np.linalg.norm(phi_a) * np.linalg.norm(phi_b), (a, b)
+            if h_cols is None or b in h_cols:
+                hb = ref[b][1]
+                h_ref = Mx.hamiltonian_entry(geo, a, b, phi_a, hb)
+                assert abs(gpu["H"][k] - h_ref) <= tol * np.linalg.norm(phi_a) * np.linalg.norm(hb), (a, b)
+
+
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+def test_single_function_box(prec):
+    wl = I.single_sf_24()
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    ref = oracle_hphi(wl, geo, [0], V)
+    gpu = gpu_run(wl, phi_fn(wl), prec)
+    check_functions(wl, geo, gpu, ref, TOL[prec])
+    check_rows(wl, geo, gpu, ref, [0], TOL[prec])
+    # H_aa = E_kin + E_pot, S_aa = |phi|^2 = 1
+    assert abs(gpu["S"][0] - 1.0) <= TOL[prec]
+    assert abs(gpu["H"][0] - (gpu["ek"][0] + gpu["ep"][0])) <= TOL[prec] * abs(gpu["ek"][0])
+
+
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+def test_small_system_every_function_and_entry(prec):
+    wl = I.scaled("atoms64", 8, seed=5)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    n = len(geo.sf_atom)
+    ref = oracle_hphi(wl, geo, range(n), V)
+    gpu = gpu_run(wl, phi_fn(wl), prec)
+    check_functions(wl, geo, gpu, ref, TOL[prec])
+    check_rows(wl, geo, gpu, ref, range(n), TOL[prec])
+
+
+@pytest.mark.parametrize("variant", ["own", "margin3", "margin0", "clipped"])
+def test_region_variants(variant):
+    wl = I.scaled("atoms64", 5, seed=8)
+    fm = "union"
+    margin = None
+    if variant == "own":
+        fm = "own"
+        wl.fine_mode = "own"
+    elif variant == "margin3":
+        margin = 3.0
+        wl.lprime_margin = 3.0
+    elif variant == "margin0":
+        margin = 0.0
+        wl.lprime_margin = 0.0
+    elif variant == "clipped":
+        wl.pos[0] = [0.2, 0.3, 0.1]          # locreg clipped by the box corner
+        wl.pos[1] = [wl.N[0] * wl.h - 0.5, 3.0, wl.N[2] * wl.h - 0.7]
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    n = len(geo.sf_atom)
+    ref = oracle_hphi(wl, geo, range(n), V)
+    gpu = gpu_run(wl, phi_fn(wl), lsw.LSW_FP64, fine_mode=fm, lprime_margin=margin)
+    check_functions(wl, geo, gpu, ref, 1e-12)
+    check_rows(wl, geo, gpu, ref, range(n), 1e-12)
+
+
+def test_options_do_not_change_results():
+    wl = I.scaled("atoms64", 8, seed=6)
+    base = gpu_run(wl, phi_fn(wl), lsw.LSW_FP64)
+    # the alignment gaps between functions are never written (NaN from the fill)
+    gap = np.isnan(base["hphi"])
+    for opts in ({"batch": 1}, {"batch": 7, "graph": 0}, {"tile": 4}, {"tile": 5, "batch": 64}):
+        o = gpu_run(wl, phi_fn(wl), lsw.LSW_FP64, options=opts, repeat=2)
+        assert np.array_equal(np.isnan(o["hphi"]), gap), opts
+        d = np.abs(o["hphi"][~gap] - base["hphi"][~gap])
+        assert np.max(d) <= 1e-13 * np.max(np.abs(base["hphi"][~gap])), opts
+        assert np.max(np.abs(o["S"] - base["S"])) <= 1e-13, opts
+        assert np.max(np.abs(o["H"] - base["H"])) <= 1e-12 * np.max(np.abs(base["H"])), opts
+
+
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+def test_atoms64_full_size_sampled(prec):
+    wl = I.atoms64()
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    gpu = gpu_run(wl, phi_fn(wl), prec)
+    rows = [0, 101]
+    need = set(rows)
+    for a in rows:
+        need |= set(int(b) for b in gpu["col"][gpu["row_ptr"][a]:gpu["row_ptr"][a + 1]])
+    need |= {57, 207}
+    ref = oracle_hphi(wl, geo, sorted(need), V)
+    check_functions(wl, geo, gpu, ref, TOL[prec])
+    check_rows(wl, geo, gpu, ref, rows, TOL[prec])
+
+
+def test_step_host_equals_device_calls():
+    import torch
+    from tests.lib_support import ensure_built, keys_to_g
+    ensure_built()
+    wl = I.scaled("atoms64", 6, seed=9)
+    dev = gpu_run(wl, phi_fn(wl), lsw.LSW_FP64)
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   precision=lsw.LSW_FP64, device=0, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        V = torch.tensor(I.potential(wl), dtype=torch.float64, device="cuda")
+        lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
+        H = np.zeros(len(S.col))
+        Sm = np.zeros(len(S.col))
+        hphi = np.zeros(S.total_Lp)
+        lsw.lsw_step_host(S.sys, dev["phi"], hphi, H, Sm)
+        assert np.max(np.abs(hphi - dev["hphi"])) <= 1e-13 * np.max(np.abs(dev["hphi"]))
+        assert np.max(np.abs(H - dev["H"])) <= 1e-12 * np.max(np.abs(dev["H"]))
+        assert np.max(np.abs(Sm - dev["S"])) <= 1e-13
+    finally:
+        S.close()
