@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--tile", type=int, default=0)
+    p.add_argument("--sync-each", action="store_true",
+                   help="warm-up only: wait for the device and check its status after every call")
     return p.parse_args()
 
 
@@ -327,7 +329,13 @@ def gpu_main(args):
         lsw.lsw_build_matrices(S.sys, phi, hphi, Hm, Sm)
 
     for _ in range(args.warmup):
-        step()
+        if args.sync_each:
+            lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
+            lsw.lsw_sync(S.sys, 600.0)
+            lsw.lsw_build_matrices(S.sys, phi, hphi, Hm, Sm)
+            lsw.lsw_sync(S.sys, 600.0)
+        else:
+            step()
     torch.cuda.synchronize()
     lsw.lsw_profile(S.sys, 1)
     step()                      # capture the traced graphs outside the timed region

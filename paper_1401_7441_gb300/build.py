@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "liblsw.so")
+CHECKED = os.environ.get("LSW_CHECKED", "0") == "1"   # self-checking build (bounds on every access)
+LIB = os.path.join(HERE, "liblsw_checked.so" if CHECKED else "liblsw.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -40,17 +41,18 @@ def build(verbose: bool = False, force: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD + ("_checked" if CHECKED else "")
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     host_flags = "-fPIC,-O2,-ffp-contract=off,-fno-fast-math"
     procs = []
     objs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", ARCH, "-lineinfo",
-               "-Xcompiler", host_flags, "--fmad=true"] + inc
+               "-Xcompiler", host_flags, "--fmad=true", "-diag-suppress=177"] + inc + (["-DLSW_CHECKED"] if CHECKED else [])
         if src.endswith(".cpp"):
             cmd = [nvcc, "-x", "c++", "-c", src, "-o", obj, "-std=c++17", "-Xcompiler", host_flags] + inc
         if verbose:

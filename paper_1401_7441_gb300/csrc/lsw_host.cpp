@@ -384,9 +384,11 @@ int64_t align64(int64_t x) { return (x + ALIGN_ELEMS - 1) / ALIGN_ELEMS * ALIGN_
 // smem bytes of the three pass kernels for a function record
 void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, size_t* bwd) {
     const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29, Z = 2 * r.n[2] + 29;
-    *fwd = es * static_cast<size_t>(4 * r.n[1] * r.n[0] + 2 * r.n[1] * X);
+    const int64_t RS = r.n[0] | 1;
+    *fwd = es * static_cast<size_t>(4 * r.n[1] * RS + 2 * r.n[1] * X);
     *z = es * static_cast<size_t>((2 * r.n[2] + Z) * zcols);
-    *bwd = es * static_cast<size_t>(Y * X + 2 * r.np[1] * X);
+    const int64_t plA = std::max<int64_t>(Y * X, 4LL * r.np[1] * r.np[0]);
+    *bwd = es * static_cast<size_t>(plA + 2 * r.np[1] * X + 4 * r.n[1] * RS);
 }
 
 lsw_status build_plans(lsw_system_s* s) {
@@ -444,6 +446,7 @@ lsw_status build_plans(lsw_system_s* s) {
             p.max_cols = std::max<int>(p.max_cols, (2 * r.n[1] + 29) * (2 * r.n[0] + 29));
             p.max_rowsP = std::max(p.max_rowsP, r.np[1] * r.np[2]);
             p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
+            p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
             size_t a1, a2, a3;
@@ -634,6 +637,13 @@ lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hph
         p.ws = s->d_ws.p;
         p.kin_scale = -1.0 / (2.0 * s->h * s->h);
         p.status = static_cast<int*>(s->d_status.p);
+        p.phi_n = s->off_L.back();
+        p.hphi_n = s->off_Lp.back();
+        p.v_n = s->vn[0] * s->vn[1] * s->vn[2];
+        p.ws_n = s->ws_elems;
+        p.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
+        p.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
+        p.n_atoms = s->n_atoms;
         CUDA_TRY(enqueue_hphi_batch(p, st));
     }
     return LSW_OK;
@@ -669,6 +679,17 @@ lsw_status enqueue_matrices(lsw_system_s* s, Tracer* tr, const void* phi, const 
     p.S = S;
     p.tile = s->tile;
     p.status = static_cast<int*>(s->d_status.p);
+    p.phi_n = s->off_L.back();
+    p.hphi_n = s->off_Lp.back();
+    p.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
+    p.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
+    p.fine_n = static_cast<int64_t>(s->d_tile_fine.bytes / sizeof(int32_t));
+    p.listA_n = static_cast<int64_t>(s->d_listA.bytes / sizeof(int32_t));
+    p.listB_n = static_cast<int64_t>(s->d_listB.bytes / sizeof(int32_t));
+    p.nnz = nnz;
+    p.org_n = static_cast<int64_t>(s->d_tile_org.bytes / sizeof(int32_t));
+    p.n_atoms = s->n_atoms;
+    p.n_sf = static_cast<int>(s->sf_atom.size());
     CUDA_TRY(enqueue_hs(p, st));
     return LSW_OK;
 }
@@ -900,8 +921,8 @@ lsw_status lsw_system_create(lsw_ctx ctx, const lsw_system_desc* d, lsw_system* 
     } catch (const std::bad_alloc&) {
         return fail(LSW_ERR_OOM, "lsw_system_create: host allocation");
     }
-    CUDA_TRY(s->d_status.alloc(sizeof(int)));
-    CUDA_TRY(cudaMemset(s->d_status.p, 0, sizeof(int)));
+    CUDA_TRY(s->d_status.alloc(STATUS_WORDS * sizeof(int)));
+    CUDA_TRY(cudaMemset(s->d_status.p, 0, STATUS_WORDS * sizeof(int)));
     CUDA_TRY(s->d_escratch.alloc(2 * s->sf_atom.size() * sizeof(double)));
     CUDA_TRY(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
     ctx->live_systems++;
@@ -1029,11 +1050,15 @@ lsw_status lsw_sync(lsw_system sys, double timeout_s) {
         if (el > timeout_s) return fail(LSW_ERR_TIMEOUT, "lsw_sync: not finished after %.3f s", el);
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    int st = 0;
-    CUDA_TRY(cudaMemcpy(&st, sys->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (st != 0) {
-        cudaMemset(sys->d_status.p, 0, sizeof(int));
-        return fail(LSW_ERR_STATE, "device-side check failed (status bits 0x%x)", st);
+    int st[STATUS_WORDS] = {0};
+    CUDA_TRY(cudaMemcpy(st, sys->d_status.p, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st[0] != 0) {
+        cudaMemset(sys->d_status.p, 0, sizeof(st));
+        long long idx, bound;
+        std::memcpy(&idx, st + 4, 8);
+        std::memcpy(&bound, st + 6, 8);
+        return fail(LSW_ERR_STATE, "device-side check failed (status bits 0x%x; kernel %d line %d block %d index %lld bound %lld)",
+                    st[0], st[1], st[2], st[3], idx, bound);
     }
     return LSW_OK;
 }

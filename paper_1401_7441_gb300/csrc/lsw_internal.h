@@ -78,6 +78,7 @@ struct HphiLaunch {
     int max_cols;                // largest (2ny+29)(2nx+29) in the batch
     int max_rowsP;               // largest ny'*nz' of L'
     int64_t max_ptsP;            // largest nx'*ny'*nz' of L'
+    int max_colsP;               // largest nx'*ny' of L'
     int max_segL;                // largest coarse+fine segment count of L
     int max_segP;
     size_t smem_fwd, smem_z, smem_bwd;
@@ -95,6 +96,9 @@ struct HphiLaunch {
     int64_t ws_D_elems;          // D region size (memset)
     double kin_scale;            // -1 / (2 h^2)
     int* status;
+    // extents used by the self-checking build (-DLSW_CHECKED)
+    int64_t phi_n, hphi_n, v_n, ws_n, seg_n, rowptr_n;
+    int n_atoms;
 };
 
 struct HSLaunch {
@@ -120,6 +124,9 @@ struct HSLaunch {
     double* S;
     int tile;                    // tile edge (coarse points)
     int* status;
+    // extents used by the self-checking build (-DLSW_CHECKED)
+    int64_t phi_n, hphi_n, seg_n, rowptr_n, fine_n, listA_n, listB_n, nnz, org_n;
+    int n_atoms, n_sf;
 };
 
 // Device entry points (lsw_kernels.cu).
@@ -133,6 +140,11 @@ enum : int {
     ST_BAD_BOX = 1,
     ST_BAD_SEG = 2,
     ST_BAD_PAIR = 4,
+    ST_BAD_INDEX = 8,   // self-checking build: an index fell outside its buffer
 };
+
+// Layout of the device status block (int32 words): [0] status bits, [1] first bad
+// kernel id, [2] source line, [3] block, [4..5] index (int64), [6..7] bound (int64).
+constexpr int STATUS_WORDS = 8;
 
 }  // namespace lsw

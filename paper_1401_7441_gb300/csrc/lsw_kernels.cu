@@ -8,8 +8,10 @@
 //   k_z           per (x', y') column: the same along z -> real-space u; v = V u
 //                 (E_pot += V u^2); then the transposed filters back to coarse z on
 //                 the L' box
-//   k_bwd_xy      per coarse z plane of L': transposed filters along y then x -> G
-//   k_kinetic     G += -1/(2h^2) sum_d T_{b_d b'_d} along d on D (E_kin = <phi|T phi>)
+//   k_bwd_xy      per coarse z plane of L': transposed filters along y then x, plus
+//                 the kinetic arms along x and y (T = -1/(2h^2) sum_d T_{b_d b'_d} along
+//                 d, Galerkin blocks of the two-level basis) -> G; E_kin partials
+//   k_kin_z       per (x'', y'') column: kinetic arm along z, G += ...; E_kin partials
 //   k_compress    G on the members of L' -> compressed H phi
 //   k_hs          per grid tile (App. D "transposed" layout): panels of phi and
 //                 H phi of the functions touching the tile; S_ab += <phi_a|phi_b>,
@@ -47,10 +49,54 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Checked accesses: plain loads/stores in the normal build; with -DLSW_CHECKED an
+// index outside [0, n) records (kernel, line, block, index, bound) in the status
+// block and the access is skipped (a load returns 0).  Never traps, never returns
+// early, so barriers stay balanced.
+__device__ __noinline__ void lsw_report(int* st, int kid, int line, int64_t idx, int64_t n) {
+    if ((atomicOr(st, ST_BAD_INDEX) & ST_BAD_INDEX) == 0) {
+        st[1] = kid;
+        st[2] = line;
+        st[3] = static_cast<int>(blockIdx.x + 65536u * blockIdx.y);
+        reinterpret_cast<long long*>(st + 4)[0] = idx;
+        reinterpret_cast<long long*>(st + 4)[1] = n;
+    }
+}
+#ifdef LSW_CHECKED
+#define LD(p, i, n) ld_chk(p, static_cast<int64_t>(i), static_cast<int64_t>(n), ST_, KID, __LINE__)
+#define ST(p, i, n, v) st_chk(p, static_cast<int64_t>(i), static_cast<int64_t>(n), v, ST_, KID, __LINE__)
+#else
+#define LD(p, i, n) ((p)[i])
+#define ST(p, i, n, v) ((p)[i] = (v))
+#endif
+template <class T>
+__device__ __forceinline__ T ld_chk(const T* p, int64_t i, int64_t n, int* st, int kid, int line) {
+    if (i < 0 || i >= n) {
+        lsw_report(st, kid, line, i, n);
+        return T{};
+    }
+    return p[i];
+}
+template <class T, class V>
+__device__ __forceinline__ void st_chk(T* p, int64_t i, int64_t n, V v, int* st, int kid, int line) {
+    if (i < 0 || i >= n) {
+        lsw_report(st, kid, line, i, n);
+        return;
+    }
+    p[i] = static_cast<T>(v);
+}
+#define FWD(b, m) Tab<T>::fwd(b, m)
+#ifdef LSW_CHECKED
+#undef FWD
+#define FWD(b, m) (((m) >= 0 && (m) < FWD_TAPS) ? Tab<T>::fwd(b, m) : (lsw_report(ST_, KID, __LINE__, (m), FWD_TAPS), T(0)))
+#endif
+
 // ---------------------------------------------------------------- uncompress / compress
 
 template <class T>
 __global__ void k_uncompress(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 1;
     const FnRec r = a.fn[blockIdx.y];
     const AtomRec& at = a.atoms[r.atom];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -58,10 +104,11 @@ __global__ void k_uncompress(HphiLaunch a) {
     const int nseg = at.nsegLc + at.nsegLf;
     if (sidx >= nseg) return;
     const bool fine = sidx >= at.nsegLc;
-    const Seg sg = a.seg[fine ? at.segLf + (sidx - at.nsegLc) : at.segLc + sidx];
+    const Seg sg = LD(a.seg, fine ? at.segLf + (sidx - at.nsegLc) : at.segLc + sidx, a.seg_n);
     const int64_t plane = static_cast<int64_t>(r.n[0]) * r.n[1] * r.n[2];
     T* D = static_cast<T*>(a.ws) + r.ws_D;
     const T* phi = static_cast<const T*>(a.phi) + r.off_phi;
+    const int64_t phi_room = a.phi_n - r.off_phi;
     const int len = sg.x1 - sg.x0 + 1;
     if (sg.x0 < 0 || sg.x1 >= r.n[0] || sg.row < 0 || sg.row >= r.n[1] * r.n[2]) {
         if (lane == 0) atomicOr(a.status, ST_BAD_SEG);
@@ -70,17 +117,20 @@ __global__ void k_uncompress(HphiLaunch a) {
     const int64_t base = static_cast<int64_t>(sg.row) * r.n[0] + sg.x0;
     for (int k = lane; k < len; k += 32) {
         if (!fine) {
-            D[base + k] = phi[sg.off + k];
+            ST(D, base + k, 8 * plane, LD(phi, sg.off + k, phi_room));
         } else {
 #pragma unroll
             for (int t = 1; t < 8; ++t)
-                D[t * plane + base + k] = phi[at.ncL + static_cast<int64_t>(t - 1) * at.nfL + sg.off + k];
+                ST(D, t * plane + base + k, 8 * plane,
+                   LD(phi, at.ncL + static_cast<int64_t>(t - 1) * at.nfL + sg.off + k, phi_room));
         }
     }
 }
 
 template <class T>
 __global__ void k_compress(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 6;
     const FnRec r = a.fn[blockIdx.y];
     const AtomRec& at = a.atoms[r.atom];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -88,10 +138,11 @@ __global__ void k_compress(HphiLaunch a) {
     const int nseg = at.nsegPc + at.nsegPf;
     if (sidx >= nseg) return;
     const bool fine = sidx >= at.nsegPc;
-    const Seg sg = a.seg[fine ? at.segPf + (sidx - at.nsegPc) : at.segPc + sidx];
+    const Seg sg = LD(a.seg, fine ? at.segPf + (sidx - at.nsegPc) : at.segPc + sidx, a.seg_n);
     const int64_t plane = static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2];
     const T* G = static_cast<const T*>(a.ws) + r.ws_G;
     T* out = static_cast<T*>(a.hphi) + r.off_hphi;
+    const int64_t out_room = a.hphi_n - r.off_hphi;
     const int len = sg.x1 - sg.x0 + 1;
     if (sg.x0 < 0 || sg.x1 >= r.np[0] || sg.row < 0 || sg.row >= r.np[1] * r.np[2]) {
         if (lane == 0) atomicOr(a.status, ST_BAD_SEG);
@@ -100,22 +151,89 @@ __global__ void k_compress(HphiLaunch a) {
     const int64_t base = static_cast<int64_t>(sg.row) * r.np[0] + sg.x0;
     for (int k = lane; k < len; k += 32) {
         if (!fine) {
-            out[sg.off + k] = G[base + k];
+            ST(out, sg.off + k, out_room, LD(G, base + k, 8 * plane));
         } else {
 #pragma unroll
             for (int t = 1; t < 8; ++t)
-                out[at.ncP + static_cast<int64_t>(t - 1) * at.nfP + sg.off + k] = G[t * plane + base + k];
+                ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + sg.off + k, out_room,
+                   LD(G, t * plane + base + k, 8 * plane));
         }
+    }
+}
+
+// ---------------------------------------------------------------- register-blocked 1D blocks
+//
+// Forward (synthesis + magic filter, upsampling by 2): u[2p+e] = sum_{k} F_b[2k+e] in_b[p-k],
+// k = 0..15 (e = 0) or 0..14 (e = 1), summed over the two input types b (s and d).  A
+// block produces the 8 outputs 2p0 .. 2p0+7 from the window in_b[p0-15 .. p0+3] (19
+// values per type) held in registers; taps are compile-time immediates.
+constexpr int FB = 4;                 // coarse steps per forward block (8 outputs)
+constexpr int FW = FB + 15;           // forward window
+constexpr int BB = 4;                 // outputs per backward / kinetic block
+constexpr int BW = 2 * BB + 29;       // backward window (fine points)
+constexpr int KW = BB + 2 * KIN_HALF; // kinetic window
+
+template <class T>
+__device__ __forceinline__ void fwd_block(const T (&w0)[FW], const T (&w1)[FW], T (&u)[2 * FB]) {
+#pragma unroll
+    for (int j = 0; j < FB; ++j) {
+        T ue = 0, uo = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            ue += Tab<T>::fwd(0, 2 * k) * w0[j + 15 - k];
+            ue += Tab<T>::fwd(1, 2 * k) * w1[j + 15 - k];
+            if (k < 15) {
+                uo += Tab<T>::fwd(0, 2 * k + 1) * w0[j + 15 - k];
+                uo += Tab<T>::fwd(1, 2 * k + 1) * w1[j + 15 - k];
+            }
+        }
+        u[2 * j] = ue;
+        u[2 * j + 1] = uo;
+    }
+}
+
+// Backward (transposed filters, decimation by 2): s_j = sum_m F_0[m] v[2j+m],
+// d_j = sum_m F_1[m] v[2j+m], m = 0..30, from the window v[0 .. 2*BB+28].
+template <class T>
+__device__ __forceinline__ void bwd_block(const T (&w)[BW], T (&s)[BB], T (&d)[BB]) {
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int m = 0; m < FWD_TAPS; ++m) {
+            a0 += Tab<T>::fwd(0, m) * w[2 * j + m];
+            a1 += Tab<T>::fwd(1, m) * w[2 * j + m];
+        }
+        s[j] = a0;
+        d[j] = a1;
+    }
+}
+
+// Kinetic arm along one axis for the two types of a pair differing in that axis' bit:
+// out_o[j] += sum_l K_{o,0}(l) in_0[j+14+l] + K_{o,1}(l) in_1[j+14+l], o = 0, 1.
+template <class T>
+__device__ __forceinline__ void kin_block(const T (&k0)[KW], const T (&k1)[KW], T (&o0)[BB], T (&o1)[BB]) {
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int l = 0; l < KIN_TAPS; ++l) {
+            a0 += Tab<T>::kin(0, l) * k0[j + l];
+            a0 += Tab<T>::kin(1, l) * k1[j + l];
+            a1 += Tab<T>::kin(2, l) * k0[j + l];
+            a1 += Tab<T>::kin(3, l) * k1[j + l];
+        }
+        o0[j] = a0;
+        o1[j] = a1;
     }
 }
 
 // ---------------------------------------------------------------- forward x, y
 
-// first a with 0 <= o - 2a <= 30, clamped to 0
-__device__ __forceinline__ int up_lo(int o) { return o >= 30 ? (o - 29) >> 1 : 0; }
-
 template <class T>
-__global__ void k_fwd_xy(HphiLaunch a) {
+__global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[blockIdx.y];
@@ -123,37 +241,65 @@ __global__ void k_fwd_xy(HphiLaunch a) {
     if (z >= r.n[2]) return;
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int X = 2 * nx + 29, Y = 2 * ny + 29;
-    T* in = sm;                 // [4][ny][nx]
-    T* mid = sm + 4 * ny * nx;  // [2][ny][X]
+    const int RS = nx | 1;                   // odd row stride: rows land in different banks
+    T* in = sm;                              // [4][ny][RS], type tb = bx + 2 by
+    T* mid = sm + 4 * ny * RS;               // [2][ny][X]
+    const int64_t smem_n = static_cast<int64_t>(a.smem_fwd / sizeof(T));
+    const int64_t mid_n = smem_n - 4 * ny * RS;
     const T* D = static_cast<const T*>(a.ws) + r.ws_D;
     const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
     const int pn = nx * ny;
     for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
         const int tb = i / pn, rem = i - tb * pn;
-        in[i] = D[(tb + 4 * bz) * plane + static_cast<int64_t>(z) * pn + rem];
+        const int y = rem / nx, x = rem - y * nx;
+        ST(in, (tb * ny + y) * RS + x, smem_n,
+           LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(z) * pn + rem, 8 * plane));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * ny * X; i += blockDim.x) {
-        const int by = i / (ny * X), rem = i - by * ny * X;
-        const int y = rem / X, xo = rem - y * X;
-        const T* s = in + (2 * by) * pn + y * nx;
-        const T* d = s + pn;
-        const int lo = up_lo(xo), hi = min(nx - 1, xo >> 1);
-        T acc = 0;
-        for (int q = lo; q <= hi; ++q) acc += Tab<T>::fwd(0, xo - 2 * q) * s[q] + Tab<T>::fwd(1, xo - 2 * q) * d[q];
-        mid[i] = acc;
+    // x pass: rows (by, y), blocks of 8 outputs along x'
+    const int nbx = (nx + 15 + FB - 1) / FB;
+    for (int task = threadIdx.x; task < 2 * ny * nbx; task += blockDim.x) {
+        const int row = task % (2 * ny), blk = task / (2 * ny);
+        const int by = row / ny, y = row - by * ny;
+        const int p0 = blk * FB;
+        const int s0 = ((2 * by) * ny + y) * RS, d0 = s0 + ny * RS;
+        T w0[FW], w1[FW], u[2 * FB];
+#pragma unroll
+        for (int i = 0; i < FW; ++i) {
+            const int q = p0 - 15 + i;
+            const bool ok = q >= 0 && q < nx;
+            w0[i] = ok ? LD(in, s0 + q, smem_n) : T(0);
+            w1[i] = ok ? LD(in, d0 + q, smem_n) : T(0);
+        }
+        fwd_block(w0, w1, u);
+#pragma unroll
+        for (int k = 0; k < 2 * FB; ++k) {
+            const int xo = 2 * p0 + k;
+            if (xo < X) ST(mid, row * X + xo, mid_n, u[k]);
+        }
     }
     __syncthreads();
+    // y pass: columns x', blocks of 8 outputs along y'
     T* Bf = static_cast<T*>(a.ws) + r.ws_Bf + (static_cast<int64_t>(bz) * nz + z) * Y * X;
-    for (int i = threadIdx.x; i < Y * X; i += blockDim.x) {
-        const int yo = i / X, xo = i - yo * X;
-        const T* s = mid + xo;
-        const T* d = mid + ny * X + xo;
-        const int lo = up_lo(yo), hi = min(ny - 1, yo >> 1);
-        T acc = 0;
-        for (int q = lo; q <= hi; ++q)
-            acc += Tab<T>::fwd(0, yo - 2 * q) * s[q * X] + Tab<T>::fwd(1, yo - 2 * q) * d[q * X];
-        Bf[i] = acc;
+    const int64_t bf_room = 2LL * nz * Y * X - (static_cast<int64_t>(bz) * nz + z) * Y * X;
+    const int nby = (ny + 15 + FB - 1) / FB;
+    for (int task = threadIdx.x; task < X * nby; task += blockDim.x) {
+        const int xo = task % X, blk = task / X;
+        const int p0 = blk * FB;
+        T w0[FW], w1[FW], u[2 * FB];
+#pragma unroll
+        for (int i = 0; i < FW; ++i) {
+            const int q = p0 - 15 + i;
+            const bool ok = q >= 0 && q < ny;
+            w0[i] = ok ? LD(mid, q * X + xo, mid_n) : T(0);
+            w1[i] = ok ? LD(mid, (ny + q) * X + xo, mid_n) : T(0);
+        }
+        fwd_block(w0, w1, u);
+#pragma unroll
+        for (int k = 0; k < 2 * FB; ++k) {
+            const int yo = 2 * p0 + k;
+            if (yo < Y) ST(Bf, static_cast<int64_t>(yo) * X + xo, bf_room, u[k]);
+        }
     }
 }
 
@@ -161,6 +307,8 @@ __global__ void k_fwd_xy(HphiLaunch a) {
 
 template <class T>
 __global__ void k_z(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[blockIdx.y];
@@ -172,141 +320,286 @@ __global__ void k_z(HphiLaunch a) {
     if (blockIdx.x * C >= cols) return;
     const bool valid = c < cols;
     const int t = threadIdx.x;
-    T* Bs = sm;              // [2][nz][C]
-    T* vs = sm + 2 * nz * C;  // [Z][C]
+    T* cin = sm;                  // [2][nz][C]  (each thread owns its column)
+    T* vs = sm + 2 * nz * C;      // [Z][C]
+    const int64_t smem_n = static_cast<int64_t>(a.smem_z / sizeof(T));
+    const int64_t vs_n = smem_n - 2 * nz * C;
     const T* Bf = static_cast<const T*>(a.ws) + r.ws_Bf;
-    for (int q = 0; q < 2 * nz; ++q) Bs[q * C + t] = valid ? Bf[static_cast<int64_t>(q) * cols + c] : T(0);
+    for (int q = 0; q < 2 * nz; ++q)
+        ST(cin, q * C + t, smem_n, valid ? LD(Bf, static_cast<int64_t>(q) * cols + c, 2LL * nz * cols) : T(0));
     double epot = 0.0;
     if (valid) {
         const int xo = c % X, yo = c / X;
         const int64_t jx = 2LL * r.lo[0] - V_REACH + xo - a.vlo[0];
         const int64_t jy = 2LL * r.lo[1] - V_REACH + yo - a.vlo[1];
         const int64_t jz0 = 2LL * r.lo[2] - V_REACH - a.vlo[2];
-        const T* V = static_cast<const T*>(a.V) + (jy + 0) * a.vn[0] + jx;
+        const T* V = static_cast<const T*>(a.V);
+        const int64_t vrow = jy * a.vn[0] + jx;
         const int64_t vstride = a.vn[0] * a.vn[1];
-        for (int zo = 0; zo < Z; ++zo) {
-            const int lo = up_lo(zo), hi = min(nz - 1, zo >> 1);
-            T u = 0;
-            for (int q = lo; q <= hi; ++q)
-                u += Tab<T>::fwd(0, zo - 2 * q) * Bs[q * C + t] + Tab<T>::fwd(1, zo - 2 * q) * Bs[(nz + q) * C + t];
-            const T vv = V[(jz0 + zo) * vstride];
-            const T v = vv * u;
-            epot += static_cast<double>(v) * static_cast<double>(u);
-            vs[zo * C + t] = v;
+        for (int p0 = 0; 2 * p0 < Z; p0 += FB) {
+            T w0[FW], w1[FW], u[2 * FB];
+#pragma unroll
+            for (int i = 0; i < FW; ++i) {
+                const int q = p0 - 15 + i;
+                const bool ok = q >= 0 && q < nz;
+                w0[i] = ok ? LD(cin, q * C + t, smem_n) : T(0);
+                w1[i] = ok ? LD(cin, (nz + q) * C + t, smem_n) : T(0);
+            }
+            fwd_block(w0, w1, u);
+#pragma unroll
+            for (int k = 0; k < 2 * FB; ++k) {
+                const int zo = 2 * p0 + k;
+                if (zo < Z) {
+                    const T vv = LD(V, (jz0 + zo) * vstride + vrow, a.v_n);
+                    const T v = vv * u[k];
+                    epot += static_cast<double>(v) * static_cast<double>(u[k]);
+                    ST(vs, zo * C + t, vs_n, v);
+                }
+            }
         }
         const int nzp = r.np[2];
         const int dz = r.lop[2] - r.lo[2];
         T* Bb = static_cast<T*>(a.ws) + r.ws_Bb;
-        for (int b = 0; b < nzp; ++b) {
-            const int b2 = 2 * (b + dz);
-            const int lo = max(0, b2), hi = min(Z - 1, b2 + 30);
-            T s = 0, d = 0;
-            for (int zo = lo; zo <= hi; ++zo) {
-                const T v = vs[zo * C + t];
-                s += Tab<T>::fwd(0, zo - b2) * v;
-                d += Tab<T>::fwd(1, zo - b2) * v;
+        for (int b0 = 0; b0 < nzp; b0 += BB) {
+            const int base = 2 * (b0 + dz);
+            T w[BW], s[BB], d[BB];
+#pragma unroll
+            for (int i = 0; i < BW; ++i) {
+                const int zo = base + i;
+                w[i] = (zo >= 0 && zo < Z) ? LD(vs, zo * C + t, vs_n) : T(0);
             }
-            Bb[static_cast<int64_t>(b) * cols + c] = s;
-            Bb[static_cast<int64_t>(nzp + b) * cols + c] = d;
+            bwd_block(w, s, d);
+#pragma unroll
+            for (int j = 0; j < BB; ++j) {
+                const int b = b0 + j;
+                if (b < nzp) {
+                    ST(Bb, static_cast<int64_t>(b) * cols + c, 2LL * nzp * cols, s[j]);
+                    ST(Bb, static_cast<int64_t>(nzp + b) * cols + c, 2LL * nzp * cols, d[j]);
+                }
+            }
         }
     }
     epot = warp_sum(epot);
     if ((threadIdx.x & 31) == 0 && epot != 0.0) atomicAdd(a.e_pot + r.f, epot);
 }
 
-// ---------------------------------------------------------------- backward y, x
+// ---------------------------------------------------------------- backward y, x + kinetic x, y
 
+// Per plane (z'', bz) of the L' box: transposed filters along y then x (potential part)
+// plus the kinetic arms along x and y of the four output types with z bit bz.
 template <class T>
-__global__ void k_bwd_xy(HphiLaunch a) {
+__global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[blockIdx.y];
     const int zb = blockIdx.x >> 1, bz = blockIdx.x & 1;
     if (zb >= r.np[2]) return;
-    const int nx = r.n[0], ny = r.n[1];
+    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int X = 2 * nx + 29, Y = 2 * ny + 29;
     const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
-    const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1];
-    T* pl = sm;           // [Y][X]
-    T* mid = sm + Y * X;  // [2][nyp][X]
+    const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
+    const int RS = nx | 1;
+    const int plA = max(Y * X, 4 * nyp * nxp);
+    T* pl = sm;                         // [Y][X], later Gs [4][nyp][nxp]
+    T* Gs = sm;
+    T* mid = sm + plA;                  // [2][nyp][X]
+    T* Dp = mid + 2 * nyp * X;          // [4][ny][RS] D plane at zL = zb + dz
+    const int64_t smem_n = static_cast<int64_t>(a.smem_bwd / sizeof(T));
+    const int zL = zb + dz;
+    const bool dplane = zL >= 0 && zL < nz;
     const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
-    for (int i = threadIdx.x; i < Y * X; i += blockDim.x) pl[i] = Bb[i];
+    const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
+    for (int i = threadIdx.x; i < Y * X; i += blockDim.x) ST(pl, i, smem_n, LD(Bb, i, bb_room));
+    const T* D = static_cast<const T*>(a.ws) + r.ws_D;
+    const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
+    const int pn = nx * ny;
+    if (dplane)
+        for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
+            const int tb = i / pn, rem = i - tb * pn;
+            const int y = rem / nx, x = rem - y * nx;
+            ST(Dp, (tb * ny + y) * RS + x, smem_n - plA - 2 * nyp * X,
+               LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem, 8 * plane));
+        }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * nyp * X; i += blockDim.x) {
-        const int by = i / (nyp * X), rem = i - by * nyp * X;
-        const int b = rem / X, xo = rem - b * X;
-        const int b2 = 2 * (b + dy);
-        const int lo = max(0, b2), hi = min(Y - 1, b2 + 30);
-        T acc = 0;
-        for (int yo = lo; yo <= hi; ++yo) acc += Tab<T>::fwd(by, yo - b2) * pl[yo * X + xo];
-        mid[i] = acc;
+    const int64_t mid_n = 2LL * nyp * X;
+    const int64_t dp_n = smem_n - plA - mid_n;
+    // y pass (transposed filters, decimating): columns x', blocks of BB outputs b
+    const int nbb = (nyp + BB - 1) / BB;
+    for (int task = threadIdx.x; task < X * nbb; task += blockDim.x) {
+        const int xo = task % X, b0 = (task / X) * BB;
+        const int base = 2 * (b0 + dy);
+        T w[BW], s[BB], d[BB];
+#pragma unroll
+        for (int i = 0; i < BW; ++i) {
+            const int yo = base + i;
+            w[i] = (yo >= 0 && yo < Y) ? LD(pl, yo * X + xo, smem_n) : T(0);
+        }
+        bwd_block(w, s, d);
+#pragma unroll
+        for (int j = 0; j < BB; ++j) {
+            const int b = b0 + j;
+            if (b < nyp) {
+                ST(mid, static_cast<int64_t>(b) * X + xo, mid_n, s[j]);
+                ST(mid, static_cast<int64_t>(nyp + b) * X + xo, mid_n, d[j]);
+            }
+        }
+    }
+    __syncthreads();   // pl is dead from here on: Gs reuses it
+    const T ks = static_cast<T>(a.kin_scale);
+    double ekin = 0.0;
+    // x pass + kinetic x arm: rows (by, b), blocks of BB outputs along x''
+    const int nbx = (nxp + BB - 1) / BB;
+    const int64_t gs_n = 4LL * nyp * nxp;
+    for (int task = threadIdx.x; task < 2 * nyp * nbx; task += blockDim.x) {
+        const int row = task % (2 * nyp), x0 = (task / (2 * nyp)) * BB;
+        const int by = row / nyp, b = row - by * nyp;
+        const int base = 2 * (x0 + dx);
+        T w[BW], s[BB], d[BB];
+#pragma unroll
+        for (int i = 0; i < BW; ++i) {
+            const int xo = base + i;
+            w[i] = (xo >= 0 && xo < X) ? LD(mid, row * X + xo, mid_n) : T(0);
+        }
+        bwd_block(w, s, d);
+        const int y = b + dy;
+        if (dplane && y >= 0 && y < ny) {
+            T k0[KW], k1[KW], o0[BB], o1[BB];
+            const int r0 = ((2 * by) * ny + y) * RS, r1 = r0 + ny * RS;
+#pragma unroll
+            for (int i = 0; i < KW; ++i) {
+                const int x = x0 + dx - KIN_HALF + i;
+                const bool ok = x >= 0 && x < nx;
+                k0[i] = ok ? LD(Dp, r0 + x, dp_n) : T(0);
+                k1[i] = ok ? LD(Dp, r1 + x, dp_n) : T(0);
+            }
+            kin_block(k0, k1, o0, o1);
+#pragma unroll
+            for (int j = 0; j < BB; ++j) {
+                o0[j] *= ks;
+                o1[j] *= ks;
+                s[j] += o0[j];
+                d[j] += o1[j];
+                const int x = x0 + dx + j;
+                if (x >= 0 && x < nx && x0 + j < nxp) {
+                    ekin += static_cast<double>(k0[KIN_HALF + j]) * static_cast<double>(o0[j]);
+                    ekin += static_cast<double>(k1[KIN_HALF + j]) * static_cast<double>(o1[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < BB; ++j) {
+            const int xb = x0 + j;
+            if (xb < nxp) {
+                ST(Gs, ((0 + 2 * by) * nyp + b) * nxp + xb, gs_n, s[j]);
+                ST(Gs, ((1 + 2 * by) * nyp + b) * nxp + xb, gs_n, d[j]);
+            }
+        }
+    }
+    __syncthreads();
+    // kinetic y arm: columns (bx, x''), blocks of BB outputs along y''
+    if (dplane) {
+        const int nbyk = (nyp + BB - 1) / BB;
+        for (int task = threadIdx.x; task < 2 * nxp * nbyk; task += blockDim.x) {
+            const int colx = task % (2 * nxp), b0 = (task / (2 * nxp)) * BB;
+            const int bx = colx / nxp, xb = colx - bx * nxp;
+            const int x = xb + dx;
+            if (x < 0 || x >= nx) continue;
+            T k0[KW], k1[KW], o0[BB], o1[BB];
+#pragma unroll
+            for (int i = 0; i < KW; ++i) {
+                const int y = b0 + dy - KIN_HALF + i;
+                const bool ok = y >= 0 && y < ny;
+                k0[i] = ok ? LD(Dp, ((bx + 0) * ny + y) * RS + x, dp_n) : T(0);
+                k1[i] = ok ? LD(Dp, ((bx + 2) * ny + y) * RS + x, dp_n) : T(0);
+            }
+            kin_block(k0, k1, o0, o1);
+#pragma unroll
+            for (int j = 0; j < BB; ++j) {
+                const int b = b0 + j;
+                if (b < nyp) {
+                    o0[j] *= ks;
+                    o1[j] *= ks;
+                    const int64_t g0 = (static_cast<int64_t>(bx + 0) * nyp + b) * nxp + xb;
+                    const int64_t g1 = (static_cast<int64_t>(bx + 2) * nyp + b) * nxp + xb;
+                    ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
+                    ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
+                    const int y = b + dy;
+                    if (y >= 0 && y < ny) {
+                        ekin += static_cast<double>(k0[KIN_HALF + j]) * static_cast<double>(o0[j]);
+                        ekin += static_cast<double>(k1[KIN_HALF + j]) * static_cast<double>(o1[j]);
+                    }
+                }
+            }
+        }
     }
     __syncthreads();
     T* G = static_cast<T*>(a.ws) + r.ws_G;
-    const int64_t plane = static_cast<int64_t>(nxp) * nyp * nzp;
-    const int pn = nxp * nyp;
-    for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
-        const int tb = i / pn, rem = i - tb * pn;
-        const int bx = tb & 1, by = tb >> 1;
-        const int b = rem / nxp, xb = rem - b * nxp;
-        const int b2 = 2 * (xb + dx);
-        const int lo = max(0, b2), hi = min(X - 1, b2 + 30);
-        const T* m = mid + (by * nyp + b) * X;
-        T acc = 0;
-        for (int xo = lo; xo <= hi; ++xo) acc += Tab<T>::fwd(bx, xo - b2) * m[xo];
-        G[(tb + 4 * bz) * plane + static_cast<int64_t>(zb) * pn + rem] = acc;
+    const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
+    const int pnp = nxp * nyp;
+    for (int i = threadIdx.x; i < 4 * pnp; i += blockDim.x) {
+        const int tb = i / pnp, rem = i - tb * pnp;
+        ST(G, (tb + 4 * bz) * gplane + static_cast<int64_t>(zb) * pnp + rem, 8 * gplane, LD(Gs, i, gs_n));
     }
+    ekin = warp_sum(ekin);
+    if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
 }
 
-// ---------------------------------------------------------------- kinetic
+// ---------------------------------------------------------------- kinetic z arm
 
+// Per (x'', y'') column of the L' box inside the L box's x, y range: the kinetic arm
+// along z of the four type pairs (t, t + 4), added to G.
 template <class T>
-__global__ void k_kinetic(HphiLaunch a) {
+__global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 5;
     const FnRec r = a.fn[blockIdx.y];
+    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
-    const int64_t pn = static_cast<int64_t>(nxp) * nyp * nzp;
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     double ekin = 0.0;
-    if (p < pn) {
-        const int xp = static_cast<int>(p % nxp), yp = static_cast<int>((p / nxp) % nyp), zp = static_cast<int>(p / (static_cast<int64_t>(nxp) * nyp));
-        const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
-        const int q[3] = {xp + r.lop[0] - r.lo[0], yp + r.lop[1] - r.lo[1], zp + r.lop[2] - r.lo[2]};
-        const int n[3] = {nx, ny, nz};
-        const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
-        const int64_t stride[3] = {1, nx, static_cast<int64_t>(nx) * ny};
-        const T* D = static_cast<const T*>(a.ws) + r.ws_D;
-        T* G = static_cast<T*>(a.ws) + r.ws_G;
-        // the point must lie within reach (14) of the L box along every axis but one
-        int out_axes = 0;
-        for (int d = 0; d < 3; ++d) out_axes += (q[d] < 0 || q[d] >= n[d]);
-        const bool inside = out_axes == 0;
-        if (out_axes <= 1) {
-            for (int b = 0; b < 8; ++b) {
-                T acc = 0;
-                for (int d = 0; d < 3; ++d) {
-                    // the other two coordinates must be inside the L box
-                    bool ok = true;
-                    for (int e = 0; e < 3; ++e)
-                        if (e != d && (q[e] < 0 || q[e] >= n[e])) ok = false;
-                    if (!ok) continue;
-                    const int bit = (b >> d) & 1;
-                    int64_t base = 0;
-                    for (int e = 0; e < 3; ++e)
-                        if (e != d) base += q[e] * stride[e];
-                    const int l0 = max(-KIN_HALF, -q[d]), l1 = min(KIN_HALF, n[d] - 1 - q[d]);
-                    for (int bp = 0; bp < 2; ++bp) {
-                        const int src = (b & ~(1 << d)) | (bp << d);
-                        const T* Dp = D + src * plane + base;
-                        const int k = bit * 2 + bp;
-                        for (int l = l0; l <= l1; ++l)
-                            acc += Tab<T>::kin(k, l + KIN_HALF) * Dp[static_cast<int64_t>(q[d] + l) * stride[d]];
+    if (c < nxp * nyp) {
+        const int yb = c / nxp, xb = c - yb * nxp;
+        const int x = xb + dx, y = yb + dy;
+        if (x >= 0 && x < nx && y >= 0 && y < ny) {
+            const T* D = static_cast<const T*>(a.ws) + r.ws_D;
+            T* G = static_cast<T*>(a.ws) + r.ws_G;
+            const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
+            const int64_t pn = static_cast<int64_t>(nx) * ny;
+            const int64_t col = static_cast<int64_t>(y) * nx + x;
+            const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
+            const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
+            const T ks = static_cast<T>(a.kin_scale);
+            for (int tb = 0; tb < 4; ++tb) {
+                for (int b0 = 0; b0 < nzp; b0 += BB) {
+                    T k0[KW], k1[KW], o0[BB], o1[BB];
+#pragma unroll
+                    for (int i = 0; i < KW; ++i) {
+                        const int z = b0 + dz - KIN_HALF + i;
+                        const bool ok = z >= 0 && z < nz;
+                        k0[i] = ok ? LD(D, tb * plane + z * pn + col, 8 * plane) : T(0);
+                        k1[i] = ok ? LD(D, (tb + 4) * plane + z * pn + col, 8 * plane) : T(0);
                     }
-                }
-                const T kv = static_cast<T>(a.kin_scale) * acc;
-                G[b * pn + p] += kv;
-                if (inside) {
-                    const int64_t qi = q[0] + q[1] * stride[1] + q[2] * stride[2];
-                    ekin += static_cast<double>(D[b * plane + qi]) * static_cast<double>(kv);
+                    kin_block(k0, k1, o0, o1);
+#pragma unroll
+                    for (int j = 0; j < BB; ++j) {
+                        const int b = b0 + j;
+                        if (b < nzp) {
+                            o0[j] *= ks;
+                            o1[j] *= ks;
+                            const int64_t g0 = tb * gplane + b * pnp + c;
+                            const int64_t g1 = (tb + 4) * gplane + b * pnp + c;
+                            ST(G, g0, 8 * gplane, LD(G, g0, 8 * gplane) + o0[j]);
+                            ST(G, g1, 8 * gplane, LD(G, g1, 8 * gplane) + o1[j]);
+                            const int z = b + dz;
+                            if (z >= 0 && z < nz) {
+                                ekin += static_cast<double>(k0[KIN_HALF + j]) * static_cast<double>(o0[j]);
+                                ekin += static_cast<double>(k1[KIN_HALF + j]) * static_cast<double>(o1[j]);
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -320,32 +613,36 @@ __global__ void k_kinetic(HphiLaunch a) {
 constexpr int HS_BLK = 32;
 constexpr int HS_KC = 64;
 
-// value of one compressed vector at box-local (x, y, z) of a region part; 0 if absent
-template <class T>
-__device__ __forceinline__ const T* seg_find(const Seg* seg, const int32_t* rowptr, int64_t seg0, int64_t row0,
-                                             const int32_t* lo, const int32_t* n, int gx, int gy, int gz,
-                                             const T* base) {
+// offset (within its part) of the member at global (gx, gy, gz) of one region part, -1 if
+// the point is not a member
+__device__ __forceinline__ int64_t seg_find(const HSLaunch& a, int64_t seg0, int64_t row0, const int32_t* lo,
+                                            const int32_t* n, int gx, int gy, int gz) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 8;
     const int x = gx - lo[0], y = gy - lo[1], z = gz - lo[2];
-    if (x < 0 || y < 0 || z < 0 || x >= n[0] || y >= n[1] || z >= n[2]) return nullptr;
+    if (x < 0 || y < 0 || z < 0 || x >= n[0] || y >= n[1] || z >= n[2]) return -1;
     const int row = y + n[1] * z;
-    const int s0 = rowptr[row0 + row], s1 = rowptr[row0 + row + 1];
+    const int s0 = LD(a.rowptr, row0 + row, a.rowptr_n), s1 = LD(a.rowptr, row0 + row + 1, a.rowptr_n);
     for (int s = s0; s < s1; ++s) {
-        const Seg sg = seg[seg0 + s];
-        if (x >= sg.x0 && x <= sg.x1) return base + sg.off + (x - sg.x0);
+        const Seg sg = LD(a.seg, seg0 + s, a.seg_n);
+        if (x >= sg.x0 && x <= sg.x1) return sg.off + (x - sg.x0);
     }
-    return nullptr;
+    return -1;
 }
 
 template <class T>
 __global__ void k_hs(HSLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 7;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* P = reinterpret_cast<T*>(smem_raw);       // [BLK][KC+1]  phi_a
-    T* PB = P + HS_BLK * (HS_KC + 1);             // [BLK][KC+1]  phi_b
-    T* Q = PB + HS_BLK * (HS_KC + 1);             // [BLK][KC+1]  H phi_b
+    // P: [3][BLK][KC+1] = phi_a panel, phi_b panel, H phi_b panel
+    T* P = reinterpret_cast<T*>(smem_raw);
     const HSWork w = a.work[blockIdx.x];
-    const int* org = a.tile_org + 4 * w.tile;
-    const int ox = org[0], oy = org[1], oz = org[2];
-    const int f0 = org[3], f1 = org[7];
+    const int* org = a.tile_org;
+    const int64_t o4 = 4LL * w.tile;
+    const int ox = LD(org, o4, a.org_n), oy = LD(org, o4 + 1, a.org_n), oz = LD(org, o4 + 2, a.org_n);
+    const int f0 = LD(org, o4 + 3, a.org_n), f1 = LD(org, o4 + 7, a.org_n);
+    constexpr int PN = 3 * HS_BLK * (HS_KC + 1);
     const int T3 = a.tile * a.tile * a.tile;
     const int nfine = f1 - f0;
     const int tid = threadIdx.x;
@@ -375,48 +672,50 @@ __global__ void k_hs(HSLaunch a) {
                 ly = (k / a.tile) % a.tile;
                 lz = k / (a.tile * a.tile);
             } else {
-                const int code = a.tile_fine[f0 + (ch - n_coarse_chunks) * fpc + kp];
+                const int code = LD(a.tile_fine, f0 + (ch - n_coarse_chunks) * fpc + kp, a.fine_n);
                 lx = code & 255;
                 ly = (code >> 8) & 255;
                 lz = code >> 16;
             }
             const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
             const bool isA = slot < w.na;
-            const int f = isA ? a.listA[w.a0 + slot] : a.listB[w.b0 + slot - w.na];
-            const AtomRec& at = a.atoms[a.sf_atom[f]];
-            const T* pL = phi + a.off_L[f];
-            T* dstP = isA ? P + slot * (HS_KC + 1) : PB + (slot - w.na) * (HS_KC + 1);
+            const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
+            const AtomRec& at = a.atoms[LD(a.sf_atom, f, a.n_sf)];
+            const int64_t oL = LD(a.off_L, f, a.n_sf + 1), oP = LD(a.off_Lp, f, a.n_sf + 1);
+            const int dst0 = isA ? slot * (HS_KC + 1) : HS_BLK * (HS_KC + 1) + (slot - w.na) * (HS_KC + 1);
+            const int q0 = 2 * HS_BLK * (HS_KC + 1) + (slot - w.na) * (HS_KC + 1);
             if (coarse) {
-                const T* v = seg_find<T>(a.seg, a.rowptr, at.segLc, at.rowLc, at.lo, at.n, gx, gy, gz, pL);
-                dstP[kp] = v ? *v : T(0);
+                const int64_t v = seg_find(a, at.segLc, at.rowLc, at.lo, at.n, gx, gy, gz);
+                ST(P, dst0 + kp, PN, v >= 0 ? LD(phi, oL + v, a.phi_n) : T(0));
                 if (!isA) {
-                    const T* hv = seg_find<T>(a.seg, a.rowptr, at.segPc, at.rowPc, at.lop, at.np, gx, gy, gz,
-                                              hphi + a.off_Lp[f]);
-                    Q[(slot - w.na) * (HS_KC + 1) + kp] = hv ? *hv : T(0);
+                    const int64_t hv = seg_find(a, at.segPc, at.rowPc, at.lop, at.np, gx, gy, gz);
+                    ST(P, q0 + kp, PN, hv >= 0 ? LD(hphi, oP + hv, a.hphi_n) : T(0));
                 }
             } else {
-                const T* v = seg_find<T>(a.seg, a.rowptr, at.segLf, at.rowLf, at.lo, at.n, gx, gy, gz, pL + at.ncL);
+                const int64_t v = seg_find(a, at.segLf, at.rowLf, at.lo, at.n, gx, gy, gz);
 #pragma unroll
-                for (int t = 0; t < 7; ++t) dstP[7 * kp + t] = v ? v[static_cast<int64_t>(t) * at.nfL] : T(0);
+                for (int t = 0; t < 7; ++t)
+                    ST(P, dst0 + 7 * kp + t, PN,
+                       v >= 0 ? LD(phi, oL + at.ncL + v + static_cast<int64_t>(t) * at.nfL, a.phi_n) : T(0));
                 if (!isA) {
-                    const T* hv = seg_find<T>(a.seg, a.rowptr, at.segPf, at.rowPf, at.lop, at.np, gx, gy, gz,
-                                              hphi + a.off_Lp[f] + at.ncP);
-                    T* q = Q + (slot - w.na) * (HS_KC + 1) + 7 * kp;
+                    const int64_t hv = seg_find(a, at.segPf, at.rowPf, at.lop, at.np, gx, gy, gz);
 #pragma unroll
-                    for (int t = 0; t < 7; ++t) q[t] = hv ? hv[static_cast<int64_t>(t) * at.nfP] : T(0);
+                    for (int t = 0; t < 7; ++t)
+                        ST(P, q0 + 7 * kp + t, PN,
+                           hv >= 0 ? LD(hphi, oP + at.ncP + hv + static_cast<int64_t>(t) * at.nfP, a.hphi_n) : T(0));
                 }
             }
         }
         __syncthreads();
         if (pi < w.na) {
             T ps[4] = {0, 0, 0, 0}, ph[4] = {0, 0, 0, 0};
-            const T* pa = P + pi * (HS_KC + 1);
+            const int pa = pi * (HS_KC + 1);
             for (int k = 0; k < kcount; ++k) {
-                const T va = pa[k];
+                const T va = LD(P, pa + k, PN);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    ps[u] += va * PB[(pj0 + u) * (HS_KC + 1) + k];
-                    ph[u] += va * Q[(pj0 + u) * (HS_KC + 1) + k];
+                    ps[u] += va * LD(P, HS_BLK * (HS_KC + 1) + (pj0 + u) * (HS_KC + 1) + k, PN);
+                    ph[u] += va * LD(P, 2 * HS_BLK * (HS_KC + 1) + (pj0 + u) * (HS_KC + 1) + k, PN);
                 }
             }
 #pragma unroll
@@ -428,18 +727,18 @@ __global__ void k_hs(HSLaunch a) {
         __syncthreads();
     }
     if (pi >= w.na) return;
-    const int fa = a.listA[w.a0 + pi];
-    const int64_t r0 = a.row_ptr[fa], r1 = a.row_ptr[fa + 1];
+    const int fa = LD(a.listA, w.a0 + pi, a.listA_n);
+    const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int j = pj0 + u;
         if (j >= w.nb) continue;
-        const int fb = a.listB[w.b0 + j];
+        const int fb = LD(a.listB, w.b0 + j, a.listB_n);
         int64_t lo = r0, hi = r1 - 1;
         int64_t pos = -1;
         while (lo <= hi) {
             const int64_t mid = (lo + hi) >> 1;
-            const int cm = a.col[mid];
+            const int cm = LD(a.col, mid, a.nnz);
             if (cm == fb) {
                 pos = mid;
                 break;
@@ -450,6 +749,10 @@ __global__ void k_hs(HSLaunch a) {
                 hi = mid - 1;
         }
         if (pos < 0) continue;
+        if (pos >= a.nnz) {
+            lsw_report(ST_, KID, __LINE__, pos, a.nnz);
+            continue;
+        }
         if (hacc[u] != 0.0) atomicAdd(a.H + pos, hacc[u]);
         if (sacc[u] != 0.0) atomicAdd(a.S + pos, sacc[u]);
     }
@@ -504,7 +807,7 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
     TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
     TRACED(a.tr, TK_KINETIC, s,
-           (k_kinetic<T><<<dim3(static_cast<unsigned>((a.max_ptsP + 255) / 256), nf), 256, 0, s>>>(a)));
+           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsP + 127) / 128), nf), 128, 0, s>>>(a)));
     TRACED(a.tr, TK_COMPRESS, s, (k_compress<T><<<dim3((a.max_segP + 7) / 8, nf), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }
