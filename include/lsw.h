@@ -163,6 +163,30 @@ lsw_status lsw_set_potential(lsw_system sys, const void* V_dev, const int64_t fi
 lsw_status lsw_apply_hamiltonian(lsw_system sys, const void* phi_dev, void* hphi_dev,
                                  double* e_kin_dev, double* e_pot_dev);
 
+/* Allocation-free H phi.  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate device memory while they work - a serving process
+ * that reserves its HBM budget up front and forbids allocation on the request path,
+ * an application whose device memory belongs to another allocator's pool (where a
+ * stray cudaMalloc bypasses the pool's accounting and fails once the pool holds the
+ * memory), or code issuing work inside a stream capture it does not own.
+ * Same arguments, layouts and results as lsw_apply_hamiltonian (tolerance of the
+ * precision), computed batch by batch in a fixed 32 MiB device array that the library
+ * defines at file scope: it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Limits and rules:
+ * - Every GPU that loads the library holds the 32 MiB array until the process exits.
+ * - The first call on a device looks up the array's device address (this may load the
+ *   library's module); make that first call before any stream capture.
+ * - All calls share the one array and leave the last call's contents in it; calls
+ *   whose work overlaps on the GPU (other streams, other systems, other threads) race
+ *   and produce wrong results: serialize them.
+ * - A support function whose workspace exceeds the array returns LSW_ERR_UNSUPPORTED.
+ * Asynchronous on the context stream (the per-batch records are copied from host
+ * stack memory, which may wait for earlier work on the stream).
+ * Errors: LSW_ERR_ARG (NULL buffers), LSW_ERR_STATE (no potential, host-only context),
+ * LSW_ERR_UNSUPPORTED, LSW_ERR_CUDA. */
+lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi_dev, void* hphi_dev,
+                                         double* e_kin_dev, double* e_pot_dev);
+
 /* Sparse matrices on the pattern (Sec. II.A): H_dev[k] = <phi_a|H phi_b> (raw, not
  * symmetrized) and S_dev[k] = <phi_a|phi_b> for the k-th pattern entry (a, b); FP64
  * accumulation in both precisions.  Asynchronous.

@@ -1021,6 +1021,134 @@ lsw_status lsw_build_matrices(lsw_system sys, const void* phi, const void* hphi,
     return run_maybe_graph(sys, &sys->graphs_m, key, [&](Tracer* tr) { return enqueue_matrices(sys, tr, phi, hphi, H, S); });
 }
 
+// Allocation-free variant of lsw_apply_hamiltonian.  Works like it, batch by batch, but
+// every batch's workspace and its function records live in the library's fixed device
+// array (noalloc_scratch); the batches are planned here on the stack, the records are
+// copied into the head of the array, and the existing batch kernels run on the rest.
+lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* hphi, double* ek, double* ep) {
+    g_err.clear();
+    if (!sys || !phi || !hphi) return fail(LSW_ERR_ARG, "lsw_apply_hamiltonian_noalloc: NULL buffer");
+    if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys->V) return fail(LSW_ERR_STATE, "lsw_apply_hamiltonian_noalloc: no potential (lsw_set_potential)");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    void* scratch = nullptr;
+    CUDA_TRY(noalloc_scratch(sys->ctx->device, &scratch));
+    const size_t head = (NOALLOC_MAX_BATCH * sizeof(FnRec) + 255) / 256 * 256;
+    const int64_t cap = static_cast<int64_t>((NOALLOC_SCRATCH_BYTES - head) / sys->esize);
+    const int zcols = sys->prec == LSW_FP64 ? 64 : 128;
+    cudaStream_t st = sys->ctx->stream;
+    const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
+    double* e0 = static_cast<double*>(sys->d_escratch.p);
+    if (!ek) ek = e0;
+    if (!ep) ep = e0 + nf;
+    CUDA_TRY(cudaMemsetAsync(ek, 0, nf * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(ep, 0, nf * sizeof(double), st));
+    FnRec recs[NOALLOC_MAX_BATCH];
+    int64_t sizeD[NOALLOC_MAX_BATCH], sizeR[NOALLOC_MAX_BATCH];
+    int64_t f = 0;
+    while (f < nf) {
+        int nb = 0;
+        int64_t needD = 0, needR = 0;
+        while (f + nb < nf && nb < NOALLOC_MAX_BATCH) {
+            FnRec r;
+            std::memset(&r, 0, sizeof(r));
+            const int a = sys->sf_atom[f + nb];
+            r.f = static_cast<int32_t>(f + nb);
+            r.atom = a;
+            for (int d = 0; d < 3; ++d) {
+                r.lo[d] = sys->L[a].lo[d];
+                r.n[d] = sys->L[a].n[d];
+                r.lop[d] = sys->Lp[a].lo[d];
+                r.np[d] = sys->Lp[a].n[d];
+            }
+            r.off_phi = sys->off_L[f + nb];
+            r.off_hphi = sys->off_Lp[f + nb];
+            const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+            const int64_t sD = align64(8LL * r.n[0] * r.n[1] * r.n[2]);
+            const int64_t sR = align64(2LL * r.n[2] * Y * X) + align64(2LL * r.np[2] * Y * X) +
+                               align64(8LL * r.np[0] * r.np[1] * r.np[2]);
+            if (needD + sD + needR + sR > cap) break;
+            recs[nb] = r;
+            sizeD[nb] = sD;
+            sizeR[nb] = sR;
+            needD += sD;
+            needR += sR;
+            ++nb;
+        }
+        if (nb == 0)
+            return fail(LSW_ERR_UNSUPPORTED,
+                        "lsw_apply_hamiltonian_noalloc: support function %lld needs more workspace than the %zu-byte "
+                        "fixed device scratch",
+                        static_cast<long long>(f), NOALLOC_SCRATCH_BYTES);
+        HphiLaunch p;
+        std::memset(&p, 0, sizeof(p));
+        p.prec = sys->prec;
+        p.nfn = nb;
+        p.zcols = zcols;
+        int64_t o = 0;
+        for (int k = 0; k < nb; ++k) {
+            recs[k].ws_D = o;
+            o += sizeD[k];
+        }
+        p.ws_D_elems = o;
+        for (int k = 0; k < nb; ++k) {
+            const FnRec& r = recs[k];
+            const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+            recs[k].ws_Bf = o;
+            o += align64(2LL * r.n[2] * Y * X);
+            recs[k].ws_Bb = o;
+            o += align64(2LL * r.np[2] * Y * X);
+            recs[k].ws_G = o;
+            o += align64(8LL * r.np[0] * r.np[1] * r.np[2]);
+            const LocregHost& Lh = sys->L[r.atom];
+            const LocregHost& Ph = sys->Lp[r.atom];
+            p.max_nz = std::max(p.max_nz, r.n[2]);
+            p.max_nzp = std::max(p.max_nzp, r.np[2]);
+            p.max_cols = std::max<int>(p.max_cols, (2 * r.n[1] + 29) * (2 * r.n[0] + 29));
+            p.max_rowsP = std::max(p.max_rowsP, r.np[1] * r.np[2]);
+            p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
+            p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
+            p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
+            p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
+            size_t a1, a2, a3;
+            pass_smem(r, sys->esize, zcols, &a1, &a2, &a3);
+            p.smem_fwd = std::max(p.smem_fwd, a1);
+            p.smem_z = std::max(p.smem_z, a2);
+            p.smem_bwd = std::max(p.smem_bwd, a3);
+        }
+        if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd > sys->ctx->max_smem)
+            return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
+        // records into the head of the scratch (pageable source: reusable on return)
+        CUDA_TRY(cudaMemcpyAsync(scratch, recs, nb * sizeof(FnRec), cudaMemcpyHostToDevice, st));
+        p.fn = static_cast<const FnRec*>(scratch);
+        p.atoms = static_cast<const AtomRec*>(sys->d_atoms.p);
+        p.seg = static_cast<const Seg*>(sys->d_seg.p);
+        p.rowptr = static_cast<const int32_t*>(sys->d_rowptr.p);
+        p.phi = phi;
+        p.hphi = hphi;
+        p.e_kin = ek;
+        p.e_pot = ep;
+        p.V = sys->V;
+        for (int d = 0; d < 3; ++d) {
+            p.vlo[d] = sys->vlo[d];
+            p.vn[d] = sys->vn[d];
+        }
+        p.ws = static_cast<unsigned char*>(scratch) + head;
+        p.kin_scale = -1.0 / (2.0 * sys->h * sys->h);
+        p.status = static_cast<int*>(sys->d_status.p);
+        p.phi_n = sys->off_L.back();
+        p.hphi_n = sys->off_Lp.back();
+        p.v_n = sys->vn[0] * sys->vn[1] * sys->vn[2];
+        p.ws_n = cap;
+        p.seg_n = static_cast<int64_t>(sys->d_seg.bytes / sizeof(Seg));
+        p.rowptr_n = static_cast<int64_t>(sys->d_rowptr.bytes / sizeof(int32_t));
+        p.n_atoms = sys->n_atoms;
+        CUDA_TRY(enqueue_hphi_batch(p, st));
+        f += nb;
+    }
+    return LSW_OK;
+}
+
 lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
     g_err.clear();
     if (!sys || !bytes) return fail(LSW_ERR_ARG, "lsw_workspace_bytes: NULL argument");

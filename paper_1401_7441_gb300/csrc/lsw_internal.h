@@ -129,6 +129,12 @@ struct HSLaunch {
     int n_atoms, n_sf;
 };
 
+// Fixed device scratch of the allocation-free Hamiltonian entry point (lsw_kernels.cu).
+constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(32) << 20;   // 32 MiB
+constexpr int NOALLOC_MAX_DEVICES = 64;
+constexpr int NOALLOC_MAX_BATCH = 64;      // functions per batch (records kept in the scratch)
+cudaError_t noalloc_scratch(int device, void** ptr);
+
 // Device entry points (lsw_kernels.cu).
 cudaError_t upload_filters(const FilterSet& fs, int device);
 cudaError_t configure_kernels(size_t max_smem);

@@ -21,6 +21,7 @@
 // and matrix accumulations are FP64.  Device-side checks set bits of a status word
 // (never trap).
 #include <cstdint>
+#include <mutex>
 
 #include "lsw_internal.h"
 
@@ -756,6 +757,30 @@ __global__ void k_hs(HSLaunch a) {
         if (hacc[u] != 0.0) atomicAdd(a.H + pos, hacc[u]);
         if (sacc[u] != 0.0) atomicAdd(a.S + pos, sacc[u]);
     }
+}
+
+// ---------------------------------------------------------------- fixed device scratch
+
+// Workspace of lsw_apply_hamiltonian_noalloc: a file-scope device array, so that this
+// entry point never allocates.  Every GPU that loads the library holds it until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of the array on `device` (which must be current).  The first call for
+// a device looks the address up with cudaGetSymbolAddress (this may load the module, so
+// it belongs before any stream capture); later calls return the cached address.
+cudaError_t noalloc_scratch(int device, void** ptr) {
+    static std::mutex mu;
+    static void* addr[NOALLOC_MAX_DEVICES] = {};
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (addr[device] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[device] = p;
+    }
+    *ptr = addr[device];
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- host entry points

@@ -64,6 +64,7 @@ _SIGS = {
     "lsw_set_potential": (C.c_int, [_P, _P, _I64P, _I64P]),
     "lsw_apply_hamiltonian": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_build_matrices": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lsw_apply_hamiltonian_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_workspace_bytes": (C.c_int, [_P, _I64P]),
     "lsw_sync": (C.c_int, [_P, C.c_double]),
     "lsw_step_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -177,6 +178,12 @@ def lsw_set_potential(sys, V, fine_lo, fine_dims):
 
 def lsw_apply_hamiltonian(sys, phi, hphi, e_kin=None, e_pot=None):
     check(lib().lsw_apply_hamiltonian(sys, _ptr(phi), _ptr(hphi), _ptr(e_kin), _ptr(e_pot)))
+
+
+def lsw_apply_hamiltonian_noalloc(sys, phi, hphi, e_kin=None, e_pot=None):
+    """H phi without any device allocation (workspace in the library's fixed 32 MiB
+    device array); for callers that must not allocate.  See include/lsw.h."""
+    check(lib().lsw_apply_hamiltonian_noalloc(sys, _ptr(phi), _ptr(hphi), _ptr(e_kin), _ptr(e_pot)))
 
 
 def lsw_build_matrices(sys, phi, hphi, H, S):
