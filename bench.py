@@ -156,6 +156,28 @@ def reference_main(args):
     return 0
 
 
+# ---------------------------------------------------------------- multi-process aggregation
+
+def aggregate(local_value, world, device=None, op="max"):
+    """Max (or sum) of a per-rank scalar over all ranks; the identity on one rank.
+
+    Replicas run the same workload on every rank without any data-path collective;
+    this is the only collective of the benchmark (timing), as the contract asks:
+    the job time is the slowest rank's."""
+    if world <= 1:
+        return float(local_value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_value(n_sf, steps, world, max_ms):
+    """Support functions per second of the whole job: every rank processes n_sf per step."""
+    return world * n_sf * steps / (max_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- GPU leg
 
 class ClockSampler:
@@ -209,60 +231,58 @@ class ClockSampler:
 
 
 def kernel_work(S, wl, prec):
-    """Algorithmic FLOPs of each kernel kind for one full step (exact in-range tap
-    counts of the separable filters), and compulsory bytes."""
+    """Algorithmic FLOPs per kernel kind for one full step: the in-range taps of each
+    separable filter (zero padding and out-of-box taps are not counted),
+    and the compulsory bytes of a step (phi in, H phi out, H and S values out)."""
     es = 8 if prec == "fp64" else 4
     fl = {"fwd_xy": 0.0, "z_stage": 0.0, "bwd_xy": 0.0, "kinetic": 0.0}
 
     def up_taps(nout, nin):
-        # sum over outputs o of #{q: 0<=q<nin, 0<=o-2q<=30}
+        # sum over fine outputs o of #{coarse q in [0, nin): 0 <= o - 2q <= 30}
         o = np.arange(nout)[:, None]
         q = np.arange(nin)[None, :]
         return int(np.sum((o - 2 * q >= 0) & (o - 2 * q <= 30)))
 
     def down_taps(nout, off, nin):
+        # sum over coarse outputs b (L' box, offset off) of #{fine o in [0, nin): 0 <= o - 2(b+off) <= 30}
         b = np.arange(nout)[:, None] + off
         o = np.arange(nin)[None, :]
         return int(np.sum((o - 2 * b >= 0) & (o - 2 * b <= 30)))
+
+    def kin_taps(nout, off, nin):
+        # sum over L' outputs of #{l in [-14, 14]: 0 <= out + off + l < nin}
+        o = np.arange(nout)[:, None] + off
+        l = np.arange(-14, 15)[None, :]
+        return int(np.sum((o + l >= 0) & (o + l < nin)))
+
+    def box(k, N):
+        g0, g1 = k[:, 0], k[:, 1]
+        x0, x1 = g0 % N[0], g1 % N[0]
+        y = (g0 // N[0]) % N[1]
+        z = g0 // (N[0] * N[1])
+        lo = np.array([x0.min(), y.min(), z.min()])
+        hi = np.array([x1.max(), y.max(), z.max()])
+        return lo, hi - lo + 1
 
     cache = {}
     for f in range(S.n_sf):
         a = int(S.sf_atom[f])
         if a not in cache:
-            kc = S.keys(a, 0, 0)
-            kp = S.keys(a, 1, 0)
-            def box(k):
-                g0, g1 = k[:, 0], k[:, 1]
-                N = wl.N
-                x0, x1 = g0 % N[0], g1 % N[0]
-                y = (g0 // N[0]) % N[1]
-                z = g0 // (N[0] * N[1])
-                lo = np.array([x0.min(), y.min(), z.min()])
-                hi = np.array([x1.max(), y.max(), z.max()])
-                return lo, hi - lo + 1
-            lo, n = box(kc)
-            lop, npp = box(kp)
+            lo, n = box(S.keys(a, 0, 0), wl.N)
+            lop, npp = box(S.keys(a, 1, 0), wl.N)
             X, Y, Z = (2 * n + 29)
             d = lop - lo
-            fx = 4 * n[1] * n[2] * 2 * up_taps(X, n[0])                      # 4 type pairs, 2 inputs
+            fx = 4 * n[1] * n[2] * 2 * up_taps(X, n[0])       # 4 (by, bz) rows x 2 input types
             fy = 2 * n[2] * X * 2 * up_taps(Y, n[1])
             fz = X * Y * 2 * up_taps(Z, n[2])
-            bz = X * Y * 2 * down_taps(npp[2], d[2], Z)
+            bz = X * Y * 2 * down_taps(npp[2], d[2], Z)        # 2 output types
             by = npp[2] * 2 * X * 2 * down_taps(npp[1], d[1], Y)
-            bx = npp[2] * 4 * npp[1] * down_taps(npp[0], d[0], X) * 2
-            # kinetic: 8 output types x 3 axes x 2 input types x in-range taps, per L' point
-            kin = 0
-            for ax in range(3):
-                o = np.arange(npp[ax])[:, None] + d[ax]
-                l = np.arange(-14, 15)[None, :]
-                taps = int(np.sum((o + l >= 0) & (o + l < n[ax])))
-                others = [k for k in range(3) if k != ax]
-                inside = 1
-                for e in others:
-                    ob = np.arange(npp[e]) + d[e]
-                    inside *= int(np.sum((ob >= 0) & (ob < n[e])))
-                kin += 8 * 2 * taps * inside
-            cache[a] = (2.0 * (fx + fy), 2.0 * (fz + bz), 2.0 * (by + bx), 2.0 * kin)
+            bx = npp[2] * 4 * npp[1] * 2 * down_taps(npp[0], d[0], X)
+            # kinetic arms: per output point and output type, 2 input types x in-range taps
+            kx = 8 * n[2] * n[1] * 2 * kin_taps(npp[0], d[0], n[0])
+            ky = 8 * n[2] * n[0] * 2 * kin_taps(npp[1], d[1], n[1])
+            kz = 8 * n[1] * n[0] * 2 * kin_taps(npp[2], d[2], n[2])
+            cache[a] = (2.0 * (fx + fy), 2.0 * (fz + bz), 2.0 * (by + bx + kx + ky), 2.0 * kz)
         c = cache[a]
         fl["fwd_xy"] += c[0]
         fl["z_stage"] += c[1]
@@ -301,17 +321,10 @@ def gpu_main(args):
         lsw.lsw_set_option(S.sys, "tile", args.tile)
     # inputs on the device: phi from the counter generator, V sampled on the fine grid
     phi = torch.zeros(S.total_L, dtype=dt, device="cuda")
-    first = 0
-    atom_g = {}
-    for f in range(S.n_sf):
-        a = int(S.sf_atom[f])
-        if a not in atom_g:
-            atom_g = {a: (torch.as_tensor(keys_to_g(S.keys(a, 0, 0)), device="cuda"),
-                          torch.as_tensor(keys_to_g(S.keys(a, 0, 1)), device="cuda"))}
-        gc, gf = atom_g[a]
-        v = I.phi_values(wl, f, a, gc, gf, xp=torch, device="cuda")
-        phi[S.off_L[f]:S.off_L[f] + v.numel()] = v.to(dt)
-    _ = first
+    atoms = sorted(set(int(a) for a in S.sf_atom))
+    cg = {a: keys_to_g(S.keys(a, 0, 0)) for a in atoms}
+    fg = {a: keys_to_g(S.keys(a, 0, 1)) for a in atoms}
+    I.fill_phi(wl, phi, S.off_L, S.sf_atom, cg, fg)
     V = I.potential(wl, xp=torch, device="cuda").to(dt)
     lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
     hphi = torch.zeros(S.total_Lp, dtype=dt, device="cuda")
@@ -359,14 +372,10 @@ def gpu_main(args):
                 a, b = prof.get(k, (0.0, 0))
                 prof[k] = (a + ms, b + n)
     step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = aggregate(sum(step_ms), world, device="cuda")
     lsw.lsw_profile(S.sys, 0)
     clocks = clk.summary(local)
-    value = world * S.n_sf * args.steps / (total_ms / 1000.0)
+    value = job_value(S.n_sf, args.steps, world, total_ms)
 
     # end to end through host buffers (pinned)
     e2e = None
@@ -382,12 +391,8 @@ def gpu_main(args):
         t0 = time.perf_counter()
         for _ in range(k2):
             lsw.lsw_step_host(S.sys, phi_h, None, H_h, S_h)
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * S.n_sf * k2 / el, "unit": "support_functions/s",
+        el = aggregate(time.perf_counter() - t0, world, device="cuda")
+        e2e = {"value": job_value(S.n_sf, k2, world, 1000.0 * el), "unit": "support_functions/s",
                "h2d_bytes_per_step": int(phi_h.numel() * phi_h.element_size()),
                "d2h_bytes_per_step": int(2 * nnz * 8)}
         _ = hphi_h
@@ -431,6 +436,7 @@ def gpu_main(args):
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
                 "kernel_share": kshare,
+                "algorithmic_tflop_per_step": {k: v / 1e12 for k, v in flops.items()},
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
                 "compulsory_gb_per_step": comp_bytes / 1e9,
                 "setup_s": t_setup, "step_ms": step_ms}

@@ -222,7 +222,7 @@ lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds,
                             int64_t* launches);
 
 /* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
- * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points).
+ * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8).
  * Errors: LSW_ERR_ARG (unknown name or value). */
 lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value);
 

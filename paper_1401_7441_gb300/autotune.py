@@ -1,0 +1,60 @@
+"""Autotuner for the library's launch shapes: functions per H phi batch ("batch") and
+the H/S tile edge ("tile").
+
+Each candidate is set through lsw_set_option, warmed once, then timed with CUDA events
+on the system's stream; the fastest is kept.  Everything runs in the library's kernels;
+this module only picks knob values.  Run it before a timed region (setting "batch"
+rebuilds the batch plans and reallocates the workspace).
+"""
+from __future__ import annotations
+
+from . import lsw
+
+BATCH_CANDIDATES = (8, 16, 32, 64, 128)
+TILE_CANDIDATES = (4, 6, 8)
+
+
+def _time(fn, stream, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDIDATES,
+             tiles=TILE_CANDIDATES, reps=2, budget_bytes=None):
+    """Pick "batch" and "tile" for ``system`` (an lsw.System); returns a report dict.
+
+    ``budget_bytes`` caps the workspace a batch may take (None: no cap)."""
+    report = {"batch": {}, "tile": {}}
+    n_sf = system.n_sf
+    best_b, best_t = None, None
+    for b in batches:
+        if b > max(8, n_sf):
+            continue
+        lsw.lsw_set_option(system.sys, "batch", b)
+        ws = lsw.lsw_workspace_bytes(system.sys)
+        if budget_bytes is not None and ws > budget_bytes:
+            continue
+        ms = _time(lambda: lsw.lsw_apply_hamiltonian(system.sys, phi, hphi, e_kin, e_pot), stream, reps)
+        report["batch"][b] = ms
+        if best_b is None or ms < report["batch"][best_b]:
+            best_b = b
+    lsw.lsw_set_option(system.sys, "batch", best_b)
+    lsw.lsw_apply_hamiltonian(system.sys, phi, hphi, e_kin, e_pot)
+    for t in tiles:
+        lsw.lsw_set_option(system.sys, "tile", t)
+        ms = _time(lambda: lsw.lsw_build_matrices(system.sys, phi, hphi, H, S), stream, reps)
+        report["tile"][t] = ms
+        if best_t is None or ms < report["tile"][best_t]:
+            best_t = t
+    lsw.lsw_set_option(system.sys, "tile", best_t)
+    report["chosen"] = {"batch": best_b, "tile": best_t}
+    return report

@@ -447,6 +447,7 @@ lsw_status build_plans(lsw_system_s* s) {
             p.max_rowsP = std::max(p.max_rowsP, r.np[1] * r.np[2]);
             p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
             p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
+            p.max_colsL = std::max(p.max_colsL, r.n[0] * r.n[1]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
             size_t a1, a2, a3;
@@ -513,7 +514,7 @@ lsw_status build_hs_plan(lsw_system_s* s) {
     std::vector<int32_t> org, fine;
     std::vector<HSWork> work;
     int32_t used = 0;
-    const int BLK = 32;
+    const int BLK = 64;   // functions per side of a work item (k_hs)
     for (int64_t t = 0; t < ntiles; ++t) {
         int64_t na_t = pA[t + 1] - pA[t], nb_t = pB[t + 1] - pB[t];
         if (na_t == 0 || nb_t == 0) continue;
@@ -1108,6 +1109,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             p.max_rowsP = std::max(p.max_rowsP, r.np[1] * r.np[2]);
             p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
             p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
+            p.max_colsL = std::max(p.max_colsL, r.n[0] * r.n[1]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
             size_t a1, a2, a3;
@@ -1276,7 +1278,7 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         return LSW_OK;
     }
     if (std::strcmp(name, "tile") == 0) {
-        if (value < 2 || value > 16) return fail(LSW_ERR_ARG, "lsw_set_option: tile %lld", static_cast<long long>(value));
+        if (value < 2 || value > 8) return fail(LSW_ERR_ARG, "lsw_set_option: tile %lld", static_cast<long long>(value));
         CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
         drop_graphs(sys);
         sys->tile = static_cast<int>(value);

@@ -328,7 +328,7 @@ __global__ void k_z(HphiLaunch a) {
     const T* Bf = static_cast<const T*>(a.ws) + r.ws_Bf;
     for (int q = 0; q < 2 * nz; ++q)
         ST(cin, q * C + t, smem_n, valid ? LD(Bf, static_cast<int64_t>(q) * cols + c, 2LL * nz * cols) : T(0));
-    double epot = 0.0;
+    T epot_t = 0;   // per-thread partial in the kernel's precision (no FP64 in FP32 loops)
     if (valid) {
         const int xo = c % X, yo = c / X;
         const int64_t jx = 2LL * r.lo[0] - V_REACH + xo - a.vlo[0];
@@ -353,7 +353,7 @@ __global__ void k_z(HphiLaunch a) {
                 if (zo < Z) {
                     const T vv = LD(V, (jz0 + zo) * vstride + vrow, a.v_n);
                     const T v = vv * u[k];
-                    epot += static_cast<double>(v) * static_cast<double>(u[k]);
+                    epot_t += v * u[k];
                     ST(vs, zo * C + t, vs_n, v);
                 }
             }
@@ -380,7 +380,7 @@ __global__ void k_z(HphiLaunch a) {
             }
         }
     }
-    epot = warp_sum(epot);
+    const double epot = warp_sum(static_cast<double>(epot_t));
     if ((threadIdx.x & 31) == 0 && epot != 0.0) atomicAdd(a.e_pot + r.f, epot);
 }
 
@@ -389,7 +389,7 @@ __global__ void k_z(HphiLaunch a) {
 // Per plane (z'', bz) of the L' box: transposed filters along y then x (potential part)
 // plus the kinetic arms along x and y of the four output types with z bit bz.
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -449,8 +449,8 @@ __global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
     }
     __syncthreads();   // pl is dead from here on: Gs reuses it
     const T ks = static_cast<T>(a.kin_scale);
-    double ekin = 0.0;
-    // x pass + kinetic x arm: rows (by, b), blocks of BB outputs along x''
+    T ekin_t = 0;     // per-thread partial in the kernel's precision
+    // x pass (transposed filters): rows (by, b), blocks of BB outputs along x''
     const int nbx = (nxp + BB - 1) / BB;
     const int64_t gs_n = 4LL * nyp * nxp;
     for (int task = threadIdx.x; task < 2 * nyp * nbx; task += blockDim.x) {
@@ -464,8 +464,23 @@ __global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
             w[i] = (xo >= 0 && xo < X) ? LD(mid, row * X + xo, mid_n) : T(0);
         }
         bwd_block(w, s, d);
-        const int y = b + dy;
-        if (dplane && y >= 0 && y < ny) {
+#pragma unroll
+        for (int j = 0; j < BB; ++j) {
+            const int xb = x0 + j;
+            if (xb < nxp) {
+                ST(Gs, ((0 + 2 * by) * nyp + b) * nxp + xb, gs_n, s[j]);
+                ST(Gs, ((1 + 2 * by) * nyp + b) * nxp + xb, gs_n, d[j]);
+            }
+        }
+    }
+    if (dplane) {
+        __syncthreads();
+        // kinetic x arm: rows (by, y''), blocks of BB outputs along x''; pair (bx = 0, 1)
+        for (int task = threadIdx.x; task < 2 * nyp * nbx; task += blockDim.x) {
+            const int row = task % (2 * nyp), x0 = (task / (2 * nyp)) * BB;
+            const int by = row / nyp, b = row - by * nyp;
+            const int y = b + dy;
+            if (y < 0 || y >= ny) continue;
             T k0[KW], k1[KW], o0[BB], o1[BB];
             const int r0 = ((2 * by) * ny + y) * RS, r1 = r0 + ny * RS;
 #pragma unroll
@@ -478,29 +493,21 @@ __global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
             kin_block(k0, k1, o0, o1);
 #pragma unroll
             for (int j = 0; j < BB; ++j) {
-                o0[j] *= ks;
-                o1[j] *= ks;
-                s[j] += o0[j];
-                d[j] += o1[j];
-                const int x = x0 + dx + j;
-                if (x >= 0 && x < nx && x0 + j < nxp) {
-                    ekin += static_cast<double>(k0[KIN_HALF + j]) * static_cast<double>(o0[j]);
-                    ekin += static_cast<double>(k1[KIN_HALF + j]) * static_cast<double>(o1[j]);
+                const int xb = x0 + j;
+                if (xb < nxp) {
+                    o0[j] *= ks;
+                    o1[j] *= ks;
+                    const int64_t g0 = ((0 + 2 * by) * nyp + b) * nxp + xb;
+                    const int64_t g1 = ((1 + 2 * by) * nyp + b) * nxp + xb;
+                    ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
+                    ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
+                    const int x = x0 + dx + j;
+                    if (x >= 0 && x < nx) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
                 }
             }
         }
-#pragma unroll
-        for (int j = 0; j < BB; ++j) {
-            const int xb = x0 + j;
-            if (xb < nxp) {
-                ST(Gs, ((0 + 2 * by) * nyp + b) * nxp + xb, gs_n, s[j]);
-                ST(Gs, ((1 + 2 * by) * nyp + b) * nxp + xb, gs_n, d[j]);
-            }
-        }
-    }
-    __syncthreads();
-    // kinetic y arm: columns (bx, x''), blocks of BB outputs along y''
-    if (dplane) {
+        __syncthreads();
+        // kinetic y arm: columns (bx, x''), blocks of BB outputs along y''; pair (by = 0, 1)
         const int nbyk = (nyp + BB - 1) / BB;
         for (int task = threadIdx.x; task < 2 * nxp * nbyk; task += blockDim.x) {
             const int colx = task % (2 * nxp), b0 = (task / (2 * nxp)) * BB;
@@ -527,10 +534,7 @@ __global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
                     ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
                     ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
                     const int y = b + dy;
-                    if (y >= 0 && y < ny) {
-                        ekin += static_cast<double>(k0[KIN_HALF + j]) * static_cast<double>(o0[j]);
-                        ekin += static_cast<double>(k1[KIN_HALF + j]) * static_cast<double>(o1[j]);
-                    }
+                    if (y >= 0 && y < ny) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
                 }
             }
         }
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(256) k_bwd_xy(HphiLaunch a) {
         const int tb = i / pnp, rem = i - tb * pnp;
         ST(G, (tb + 4 * bz) * gplane + static_cast<int64_t>(zb) * pnp + rem, 8 * gplane, LD(Gs, i, gs_n));
     }
-    ekin = warp_sum(ekin);
+    const double ekin = warp_sum(static_cast<double>(ekin_t));
     if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
 }
 
@@ -559,19 +563,19 @@ __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
     const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    double ekin = 0.0;
-    if (c < nxp * nyp) {
-        const int yb = c / nxp, xb = c - yb * nxp;
-        const int x = xb + dx, y = yb + dy;
-        if (x >= 0 && x < nx && y >= 0 && y < ny) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;   // column (x, y) of the L box
+    T ekin_t = 0;
+    if (c < nx * ny) {
+        const int y = c / nx, x = c - y * nx;
+        const int xb = x - dx, yb = y - dy;             // the same column in the L' box
+        if (xb >= 0 && xb < nxp && yb >= 0 && yb < nyp) {
             const T* D = static_cast<const T*>(a.ws) + r.ws_D;
             T* G = static_cast<T*>(a.ws) + r.ws_G;
             const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
             const int64_t pn = static_cast<int64_t>(nx) * ny;
-            const int64_t col = static_cast<int64_t>(y) * nx + x;
             const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
             const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
+            const int64_t gcol = static_cast<int64_t>(yb) * nxp + xb;
             const T ks = static_cast<T>(a.kin_scale);
             for (int tb = 0; tb < 4; ++tb) {
                 for (int b0 = 0; b0 < nzp; b0 += BB) {
@@ -580,8 +584,8 @@ __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
                     for (int i = 0; i < KW; ++i) {
                         const int z = b0 + dz - KIN_HALF + i;
                         const bool ok = z >= 0 && z < nz;
-                        k0[i] = ok ? LD(D, tb * plane + z * pn + col, 8 * plane) : T(0);
-                        k1[i] = ok ? LD(D, (tb + 4) * plane + z * pn + col, 8 * plane) : T(0);
+                        k0[i] = ok ? LD(D, tb * plane + z * pn + c, 8 * plane) : T(0);
+                        k1[i] = ok ? LD(D, (tb + 4) * plane + z * pn + c, 8 * plane) : T(0);
                     }
                     kin_block(k0, k1, o0, o1);
 #pragma unroll
@@ -590,29 +594,27 @@ __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
                         if (b < nzp) {
                             o0[j] *= ks;
                             o1[j] *= ks;
-                            const int64_t g0 = tb * gplane + b * pnp + c;
-                            const int64_t g1 = (tb + 4) * gplane + b * pnp + c;
+                            const int64_t g0 = tb * gplane + b * pnp + gcol;
+                            const int64_t g1 = (tb + 4) * gplane + b * pnp + gcol;
                             ST(G, g0, 8 * gplane, LD(G, g0, 8 * gplane) + o0[j]);
                             ST(G, g1, 8 * gplane, LD(G, g1, 8 * gplane) + o1[j]);
                             const int z = b + dz;
-                            if (z >= 0 && z < nz) {
-                                ekin += static_cast<double>(k0[KIN_HALF + j]) * static_cast<double>(o0[j]);
-                                ekin += static_cast<double>(k1[KIN_HALF + j]) * static_cast<double>(o1[j]);
-                            }
+                            if (z >= 0 && z < nz) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
                         }
                     }
                 }
             }
         }
     }
-    ekin = warp_sum(ekin);
+    const double ekin = warp_sum(static_cast<double>(ekin_t));
     if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
 }
 
 // ---------------------------------------------------------------- sparse H / S
 
-constexpr int HS_BLK = 32;
-constexpr int HS_KC = 64;
+constexpr int HS_BLK = 64;     // functions per side of one work item
+constexpr int HS_KC = 64;      // panel columns per chunk
+constexpr int HS_LD = HS_KC + 1;
 
 // offset (within its part) of the member at global (gx, gy, gz) of one region part, -1 if
 // the point is not a member
@@ -631,131 +633,202 @@ __device__ __forceinline__ int64_t seg_find(const HSLaunch& a, int64_t seg0, int
     return -1;
 }
 
+// One tile row (x = ox .. ox+T-1 at fixed gy, gz) of a region part: dst[i] = the value
+// of the member at x = ox + i, or 0.  One row lookup, then contiguous copies.
 template <class T>
-__global__ void k_hs(HSLaunch a) {
+__device__ __forceinline__ void row_gather(const HSLaunch& a, int64_t seg0, int64_t row0, const int32_t* lo,
+                                           const int32_t* n, int ox, int gy, int gz, int tile, const T* base,
+                                           int64_t base_room, T* dst, int dst_room) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 9;
+    for (int i = 0; i < tile; ++i) ST(dst, i, dst_room, T(0));
+    const int y = gy - lo[1], z = gz - lo[2];
+    if (y < 0 || z < 0 || y >= n[1] || z >= n[2]) return;
+    const int row = y + n[1] * z;
+    const int s0 = LD(a.rowptr, row0 + row, a.rowptr_n), s1 = LD(a.rowptr, row0 + row + 1, a.rowptr_n);
+    const int xl0 = ox - lo[0];
+    for (int s = s0; s < s1; ++s) {
+        const Seg sg = LD(a.seg, seg0 + s, a.seg_n);
+        const int x0 = max(sg.x0, xl0), x1 = min(sg.x1, xl0 + tile - 1);
+        for (int x = x0; x <= x1; ++x) ST(dst, x - xl0, dst_room, LD(base, sg.off + (x - sg.x0), base_room));
+    }
+}
+
+// Tile-panel H/S (the "transposed" layout of App. D on one GPU): a work item takes one
+// grid tile and up to 64 functions a whose L touches it and 64 functions b whose L'
+// touches it; it gathers their coefficients on the tile's points into shared panels
+// chunk by chunk and accumulates S_ab (phi_a . phi_b) and H_ab (phi_a . H phi_b) for
+// all 64 x 64 pairs, 4 x 4 per thread; pattern pairs are added to the CSR in FP64.
+template <class T>
+__global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 7;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // P: [3][BLK][KC+1] = phi_a panel, phi_b panel, H phi_b panel
+    // [3][BLK][LD] = phi_a panel, phi_b panel, H phi_b panel
     T* P = reinterpret_cast<T*>(smem_raw);
+    constexpr int PN = 3 * HS_BLK * HS_LD;
+    T* PA = P;
+    T* PB = P + HS_BLK * HS_LD;
+    T* PQ = P + 2 * HS_BLK * HS_LD;
     const HSWork w = a.work[blockIdx.x];
     const int* org = a.tile_org;
     const int64_t o4 = 4LL * w.tile;
     const int ox = LD(org, o4, a.org_n), oy = LD(org, o4 + 1, a.org_n), oz = LD(org, o4 + 2, a.org_n);
     const int f0 = LD(org, o4 + 3, a.org_n), f1 = LD(org, o4 + 7, a.org_n);
-    constexpr int PN = 3 * HS_BLK * (HS_KC + 1);
-    const int T3 = a.tile * a.tile * a.tile;
+    const int TL = a.tile;
+    const int rows_per_chunk = HS_KC / TL;                 // tile rows per coarse chunk
+    const int n_rows = TL * TL;
+    const int n_coarse_chunks = (n_rows + rows_per_chunk - 1) / rows_per_chunk;
     const int nfine = f1 - f0;
-    const int tid = threadIdx.x;
-    const int pi = tid >> 3, pj0 = (tid & 7) * 4;
-    double sacc[4] = {0, 0, 0, 0}, hacc[4] = {0, 0, 0, 0};
-    const int n_coarse_chunks = (T3 + HS_KC - 1) / HS_KC;
-    const int fpc = HS_KC / 7;  // fine points per chunk
+    const int fpc = HS_KC / 7;
     const int n_fine_chunks = (nfine + fpc - 1) / fpc;
+    const int tid = threadIdx.x;
+    const int ti = tid >> 4, tj = tid & 15;                // pairs (ti + 16u, tj + 16v)
+    double sacc[4][4], hacc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sacc[u][v] = 0.0, hacc[u][v] = 0.0;
     const T* phi = static_cast<const T*>(a.phi);
     const T* hphi = static_cast<const T*>(a.hphi);
+    const int nslot = w.na + w.nb;
     for (int ch = 0; ch < n_coarse_chunks + n_fine_chunks; ++ch) {
         const bool coarse = ch < n_coarse_chunks;
         int kcount;
-        if (coarse)
-            kcount = min(HS_KC, T3 - ch * HS_KC);
-        else
-            kcount = 7 * min(fpc, nfine - (ch - n_coarse_chunks) * fpc);
-        // gather: task = (slot, k-point); slots 0..na-1 -> A, na..na+nb-1 -> B
-        const int npts = coarse ? kcount : kcount / 7;
-        const int nslot = w.na + w.nb;
-        for (int task = tid; task < nslot * npts; task += blockDim.x) {
-            const int slot = task / npts, kp = task - slot * npts;
-            int lx, ly, lz;
-            if (coarse) {
-                const int k = ch * HS_KC + kp;
-                lx = k % a.tile;
-                ly = (k / a.tile) % a.tile;
-                lz = k / (a.tile * a.tile);
-            } else {
-                const int code = LD(a.tile_fine, f0 + (ch - n_coarse_chunks) * fpc + kp, a.fine_n);
-                lx = code & 255;
-                ly = (code >> 8) & 255;
-                lz = code >> 16;
-            }
-            const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-            const bool isA = slot < w.na;
-            const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
-            const AtomRec& at = a.atoms[LD(a.sf_atom, f, a.n_sf)];
-            const int64_t oL = LD(a.off_L, f, a.n_sf + 1), oP = LD(a.off_Lp, f, a.n_sf + 1);
-            const int dst0 = isA ? slot * (HS_KC + 1) : HS_BLK * (HS_KC + 1) + (slot - w.na) * (HS_KC + 1);
-            const int q0 = 2 * HS_BLK * (HS_KC + 1) + (slot - w.na) * (HS_KC + 1);
-            if (coarse) {
-                const int64_t v = seg_find(a, at.segLc, at.rowLc, at.lo, at.n, gx, gy, gz);
-                ST(P, dst0 + kp, PN, v >= 0 ? LD(phi, oL + v, a.phi_n) : T(0));
-                if (!isA) {
-                    const int64_t hv = seg_find(a, at.segPc, at.rowPc, at.lop, at.np, gx, gy, gz);
-                    ST(P, q0 + kp, PN, hv >= 0 ? LD(hphi, oP + hv, a.hphi_n) : T(0));
+        if (coarse) {
+            const int r0 = ch * rows_per_chunk;
+            const int nr = min(rows_per_chunk, n_rows - r0);
+            kcount = nr * TL;
+            // task = (slot, tile row)
+            for (int task = tid; task < nslot * nr; task += blockDim.x) {
+                const int slot = task / nr, rr = r0 + (task - slot * nr);
+                const int gy = oy + rr % TL, gz = oz + rr / TL;
+                const int col0 = (rr - r0) * TL;
+                const bool isA = slot < w.na;
+                const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
+                const AtomRec& at = a.atoms[LD(a.sf_atom, f, a.n_sf)];
+                const int64_t oL = LD(a.off_L, f, a.n_sf + 1);
+                if (isA) {
+                    row_gather<T>(a, at.segLc, at.rowLc, at.lo, at.n, ox, gy, gz, TL, phi + oL, a.phi_n - oL,
+                                  PA + slot * HS_LD + col0, PN - slot * HS_LD - col0);
+                } else {
+                    const int sb = slot - w.na;
+                    const int64_t oP = LD(a.off_Lp, f, a.n_sf + 1);
+                    row_gather<T>(a, at.segLc, at.rowLc, at.lo, at.n, ox, gy, gz, TL, phi + oL, a.phi_n - oL,
+                                  PB + sb * HS_LD + col0, PN - HS_BLK * HS_LD - sb * HS_LD - col0);
+                    row_gather<T>(a, at.segPc, at.rowPc, at.lop, at.np, ox, gy, gz, TL, hphi + oP, a.hphi_n - oP,
+                                  PQ + sb * HS_LD + col0, PN - 2 * HS_BLK * HS_LD - sb * HS_LD - col0);
                 }
-            } else {
+            }
+        } else {
+            const int q0 = (ch - n_coarse_chunks) * fpc;
+            const int npts = min(fpc, nfine - q0);
+            kcount = 7 * npts;
+            for (int task = tid; task < nslot * npts; task += blockDim.x) {
+                const int slot = task / npts, kp = task - slot * npts;
+                const int code = LD(a.tile_fine, f0 + q0 + kp, a.fine_n);
+                const int gx = ox + (code & 255), gy = oy + ((code >> 8) & 255), gz = oz + (code >> 16);
+                const bool isA = slot < w.na;
+                const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
+                const AtomRec& at = a.atoms[LD(a.sf_atom, f, a.n_sf)];
+                const int64_t oL = LD(a.off_L, f, a.n_sf + 1);
+                const int dst0 = isA ? slot * HS_LD : HS_BLK * HS_LD + (slot - w.na) * HS_LD;
                 const int64_t v = seg_find(a, at.segLf, at.rowLf, at.lo, at.n, gx, gy, gz);
 #pragma unroll
                 for (int t = 0; t < 7; ++t)
                     ST(P, dst0 + 7 * kp + t, PN,
                        v >= 0 ? LD(phi, oL + at.ncL + v + static_cast<int64_t>(t) * at.nfL, a.phi_n) : T(0));
                 if (!isA) {
+                    const int64_t oP = LD(a.off_Lp, f, a.n_sf + 1);
+                    const int q0b = 2 * HS_BLK * HS_LD + (slot - w.na) * HS_LD;
                     const int64_t hv = seg_find(a, at.segPf, at.rowPf, at.lop, at.np, gx, gy, gz);
 #pragma unroll
                     for (int t = 0; t < 7; ++t)
-                        ST(P, q0 + 7 * kp + t, PN,
+                        ST(P, q0b + 7 * kp + t, PN,
                            hv >= 0 ? LD(hphi, oP + at.ncP + hv + static_cast<int64_t>(t) * at.nfP, a.hphi_n) : T(0));
                 }
             }
         }
         __syncthreads();
-        if (pi < w.na) {
-            T ps[4] = {0, 0, 0, 0}, ph[4] = {0, 0, 0, 0};
-            const int pa = pi * (HS_KC + 1);
+        // 4 x 4 pairs per thread over this chunk (rows ti + 16u of A, tj + 16v of B);
+        // FP32 panels: per-chunk partial sums (<= 64 terms) in FP32, then FP64
+        if constexpr (sizeof(T) == 8) {
             for (int k = 0; k < kcount; ++k) {
-                const T va = LD(P, pa + k, PN);
+                T va[4], vb[4], vq[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    ps[u] += va * LD(P, HS_BLK * (HS_KC + 1) + (pj0 + u) * (HS_KC + 1) + k, PN);
-                    ph[u] += va * LD(P, 2 * HS_BLK * (HS_KC + 1) + (pj0 + u) * (HS_KC + 1) + k, PN);
+                    va[u] = LD(PA, (ti + 16 * u) * HS_LD + k, PN);
+                    vb[u] = LD(PB, (tj + 16 * u) * HS_LD + k, PN - HS_BLK * HS_LD);
+                    vq[u] = LD(PQ, (tj + 16 * u) * HS_LD + k, PN - 2 * HS_BLK * HS_LD);
                 }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        sacc[u][v] += va[u] * vb[v];
+                        hacc[u][v] += va[u] * vq[v];
+                    }
+            }
+        } else {
+            T ps[4][4], ph[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) ps[u][v] = 0, ph[u][v] = 0;
+            for (int k = 0; k < kcount; ++k) {
+                T va[4], vb[4], vq[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    va[u] = LD(PA, (ti + 16 * u) * HS_LD + k, PN);
+                    vb[u] = LD(PB, (tj + 16 * u) * HS_LD + k, PN - HS_BLK * HS_LD);
+                    vq[u] = LD(PQ, (tj + 16 * u) * HS_LD + k, PN - 2 * HS_BLK * HS_LD);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        ps[u][v] += va[u] * vb[v];
+                        ph[u][v] += va[u] * vq[v];
+                    }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                sacc[u] += static_cast<double>(ps[u]);
-                hacc[u] += static_cast<double>(ph[u]);
-            }
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    sacc[u][v] += static_cast<double>(ps[u][v]);
+                    hacc[u][v] += static_cast<double>(ph[u][v]);
+                }
         }
         __syncthreads();
     }
-    if (pi >= w.na) return;
-    const int fa = LD(a.listA, w.a0 + pi, a.listA_n);
-    const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int j = pj0 + u;
-        if (j >= w.nb) continue;
-        const int fb = LD(a.listB, w.b0 + j, a.listB_n);
-        int64_t lo = r0, hi = r1 - 1;
-        int64_t pos = -1;
-        while (lo <= hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            const int cm = LD(a.col, mid, a.nnz);
-            if (cm == fb) {
-                pos = mid;
-                break;
+        const int i = ti + 16 * u;
+        if (i >= w.na) continue;
+        const int fa = LD(a.listA, w.a0 + i, a.listA_n);
+        const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = tj + 16 * v;
+            if (j >= w.nb) continue;
+            const int fb = LD(a.listB, w.b0 + j, a.listB_n);
+            int64_t lo = r0, hi = r1 - 1, pos = -1;
+            while (lo <= hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int cm = LD(a.col, mid, a.nnz);
+                if (cm == fb) {
+                    pos = mid;
+                    break;
+                }
+                if (cm < fb)
+                    lo = mid + 1;
+                else
+                    hi = mid - 1;
             }
-            if (cm < fb)
-                lo = mid + 1;
-            else
-                hi = mid - 1;
+            if (pos < 0) continue;
+            if (hacc[u][v] != 0.0) atomicAdd(a.H + pos, hacc[u][v]);
+            if (sacc[u][v] != 0.0) atomicAdd(a.S + pos, sacc[u][v]);
         }
-        if (pos < 0) continue;
-        if (pos >= a.nnz) {
-            lsw_report(ST_, KID, __LINE__, pos, a.nnz);
-            continue;
-        }
-        if (hacc[u] != 0.0) atomicAdd(a.H + pos, hacc[u]);
-        if (sacc[u] != 0.0) atomicAdd(a.S + pos, sacc[u]);
     }
 }
 
@@ -832,7 +905,7 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
     TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
     TRACED(a.tr, TK_KINETIC, s,
-           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsP + 127) / 128), nf), 128, 0, s>>>(a)));
+           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf), 128, 0, s>>>(a)));
     TRACED(a.tr, TK_COMPRESS, s, (k_compress<T><<<dim3((a.max_segP + 7) / 8, nf), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }
@@ -843,7 +916,7 @@ cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s) {
 
 cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s) {
     const size_t es = a.prec == 0 ? sizeof(double) : sizeof(float);
-    const size_t smem = 3 * HS_BLK * (HS_KC + 1) * es;
+    const size_t smem = 3 * HS_BLK * HS_LD * es;
     if (a.prec == 0)
         TRACED(a.tr, TK_HS, s, (k_hs<double><<<a.nwork, 256, smem, s>>>(a)));
     else

@@ -300,3 +300,71 @@ def phi_values(wl: Workload, f: int, atom: int, g_coarse, g_fine, xp=np, device=
         parts.append(counter_normal(wl.seed, f, t, gf, xp) * ef)
     v = xp.cat(parts)
     return v / xp.sqrt(xp.sum(v * v))
+
+
+def fill_phi(wl: Workload, phi, off_L, sf_atom, coarse_g, fine_g, chunk_coefs=1 << 25):
+    """Write every support function's compressed coefficients into the torch tensor
+    ``phi`` (layout ``off_L``) in a few large vectorized passes, with the same values
+    as ``phi_values`` for each function.  ``coarse_g[a]`` / ``fine_g[a]`` are the grid
+    indices of atom a's coarse and fine members (layout order)."""
+    import torch
+    dev = phi.device
+    N = wl.N
+    h = wl.h
+    n_sf = len(sf_atom)
+    nc = np.array([len(coarse_g[int(a)]) for a in sf_atom], dtype=np.int64)
+    nf = np.array([len(fine_g[int(a)]) for a in sf_atom], dtype=np.int64)
+    ncoef = nc + 7 * nf
+    # per-atom concatenated g lists on the device
+    atoms = sorted(set(int(a) for a in sf_atom))
+    gc_off, gf_off = {}, {}
+    gcs, gfs = [], []
+    oc = of = 0
+    for a in atoms:
+        gc_off[a] = oc
+        gf_off[a] = of
+        gcs.append(np.asarray(coarse_g[a], np.int64))
+        gfs.append(np.asarray(fine_g[a], np.int64))
+        oc += len(gcs[-1])
+        of += len(gfs[-1])
+    GC = torch.as_tensor(np.concatenate(gcs), device=dev)
+    GF = torch.as_tensor(np.concatenate(gfs) if of else np.zeros(0, np.int64), device=dev)
+    pos = torch.as_tensor(np.asarray(wl.pos, np.float64), device=dev)
+    f = 0
+    while f < n_sf:
+        f1 = f
+        tot = 0
+        while f1 < n_sf and (f1 == f or tot + ncoef[f1] <= chunk_coefs):
+            tot += ncoef[f1]
+            f1 += 1
+        fs = np.arange(f, f1)
+        cnt = torch.as_tensor(ncoef[fs], device=dev)
+        fid = torch.repeat_interleave(torch.as_tensor(fs, device=dev), cnt)        # function of each coef
+        start = torch.cumsum(cnt, 0) - cnt
+        k = torch.arange(int(tot), device=dev) - torch.repeat_interleave(start, cnt)  # index within function
+        ncf = torch.as_tensor(nc[fs], device=dev)
+        nff = torch.as_tensor(nf[fs], device=dev)
+        ncr = torch.repeat_interleave(ncf, cnt)
+        nfr = torch.repeat_interleave(nff, cnt)
+        is_c = k < ncr
+        kf = torch.where(is_c, torch.zeros_like(k), k - ncr)
+        t = torch.where(is_c, torch.zeros_like(k), kf // torch.clamp(nfr, min=1) + 1)
+        j = torch.where(is_c, k, kf - (t - 1) * nfr)
+        atom = torch.as_tensor(np.asarray(sf_atom)[fs], device=dev)
+        atom_r = torch.repeat_interleave(atom, cnt)
+        oc_a = torch.as_tensor(np.array([gc_off[int(a)] for a in np.asarray(sf_atom)[fs]]), device=dev)
+        of_a = torch.as_tensor(np.array([gf_off[int(a)] for a in np.asarray(sf_atom)[fs]]), device=dev)
+        gidx = torch.where(is_c, torch.repeat_interleave(oc_a, cnt) + j, torch.repeat_interleave(of_a, cnt) + j)
+        g = torch.where(is_c, GC[torch.clamp(gidx, max=max(0, GC.numel() - 1))],
+                        GF[torch.clamp(gidx, max=max(0, GF.numel() - 1))] if GF.numel() else torch.zeros_like(gidx))
+        z = counter_normal(wl.seed, fid, t, g, xp=torch)
+        c = pos[atom_r]
+        x = (g % N[0]).to(torch.float64) * h - c[:, 0]
+        y = ((g // N[0]) % N[1]).to(torch.float64) * h - c[:, 1]
+        zz = (g // (N[0] * N[1])).to(torch.float64) * h - c[:, 2]
+        v = z * torch.exp(-(x * x + y * y + zz * zz) / (2.0 * wl.sigma ** 2))
+        nrm = torch.zeros(len(fs), dtype=torch.float64, device=dev).index_add_(0, fid - f, v * v)
+        v = v / torch.sqrt(nrm)[fid - f]
+        dest = torch.as_tensor(np.asarray(off_L)[fs], device=dev)
+        phi[torch.repeat_interleave(dest, cnt) + k] = v.to(phi.dtype)
+        f = f1
