@@ -53,13 +53,17 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="atoms64")
+    p.add_argument("--workload", default="atoms10k")
     p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="step", choices=["step", "serving"],
+                   help="serving: Poisson request stream through the continuous-batching server")
+    p.add_argument("--requests", type=int, default=60)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--tile", type=int, default=0)
+    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--sync-each", action="store_true",
                    help="warm-up only: wait for the device and check its status after every call")
     return p.parse_args()
@@ -73,6 +77,30 @@ def workload(name):
     if name.startswith("atoms64_n"):
         return I.scaled("atoms64", int(name.split("_n")[1]))
     raise SystemExit("unknown workload " + name)
+
+
+def kernels_source_hash():
+    """SHA-256 of the kernel source: ties a stored ncu traffic figure to the kernels
+    it was measured on."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1401_7441_gb300", "csrc", "lsw_kernels.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+def stored_traffic(kernel, workload, prec, batch):
+    """DRAM bytes per launch of ``kernel`` from profiles/roofline_traffic.json, if that
+    file was written from an ncu capture of the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("kernels_sha256") != kernels_source_hash():
+        return None
+    ent = rec.get("kernels", {}).get(kernel)
+    if not ent or ent.get("precision") != prec or ent.get("batch") != batch:
+        return None
+    return ent.get("dram_bytes_per_launch")
 
 
 def keys_to_g(keys):
@@ -325,7 +353,7 @@ def gpu_main(args):
     cg = {a: keys_to_g(S.keys(a, 0, 0)) for a in atoms}
     fg = {a: keys_to_g(S.keys(a, 0, 1)) for a in atoms}
     I.fill_phi(wl, phi, S.off_L, S.sf_atom, cg, fg)
-    V = I.potential(wl, xp=torch, device="cuda").to(dt)
+    V = I.potential_fast(wl, "cuda").to(dt)
     lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
     hphi = torch.zeros(S.total_Lp, dtype=dt, device="cuda")
     ek = torch.zeros(S.n_sf, dtype=torch.float64, device="cuda")
@@ -340,6 +368,11 @@ def gpu_main(args):
     def step():
         lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
         lsw.lsw_build_matrices(S.sys, phi, hphi, Hm, Sm)
+
+    tune = None
+    if not args.no_autotune and not args.batch and not args.tile:
+        from paper_1401_7441_gb300 import autotune
+        tune = autotune.autotune(S, phi, hphi, Hm, Sm, ek, ep, stream)
 
     for _ in range(args.warmup):
         if args.sync_each:
@@ -411,7 +444,8 @@ def gpu_main(args):
             peak = (FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS)
             ach = work_per_launch / (per_launch_ms / 1000.0) / 1e12
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
+                    "frac": ach / peak,
+                    "traffic": stored_traffic(dom, wl.name, prec, (tune or {}).get("chosen", {}).get("batch")),
                     "peak_source": "derived: %s CUDA-core FMA rate (see DESIGN.md)" % prec}
         else:
             roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
@@ -432,7 +466,9 @@ def gpu_main(args):
                 "config": {"workload": wl.name, "atoms": len(wl.pos), "support_functions": S.n_sf,
                            "pattern_nnz": nnz, "grid": list(wl.N), "h_bohr": wl.h,
                            "precision": prec, "l2": "flushed (512 MB write) before every timed step",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "options": (tune or {}).get("chosen", {"batch": args.batch or None, "tile": args.tile or None}),
+                           "autotune_ms": {k: v for k, v in (tune or {}).items() if k != "chosen"}},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
                 "kernel_share": kshare,
@@ -447,10 +483,55 @@ def gpu_main(args):
     return 0
 
 
+def serving_main(args):
+    """p50/p99 latency and support functions/s of the served (FP32, batched, streams)
+    form on a Poisson stream (20 req/s, 50-5,000 atoms, 30 % reuse), against each
+    request run alone on the plain form (FP64, one function per batch, no graphs)."""
+    import torch
+    from paper_1401_7441_gb300 import serving as SV
+    from paper_1401_7441_gb300 import lsw
+    reqs = SV.request_stream(args.requests, rate=20.0, atoms=(50, 5000), reuse_frac=0.3, seed=5005)
+    srv = SV.Server(budget_bytes=150e9, precision=lsw.LSW_FP32, streams=4, host_threads=8)
+    t0 = time.perf_counter()
+    with ClockSampler(os.path.join(tempfile.gettempdir(), "lsw_clk_srv_%d.csv" % os.getpid())) as clk:
+        res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    srv.close()
+    served = SV.summarize(res)
+    # plain form, each request alone (bounded sample: the first few requests)
+    k = min(len(reqs), 6)
+    lat = []
+    nsf = 0
+    t1 = time.perf_counter()
+    for r in reqs[:k]:
+        sub = [r] if r.parent is None else [q for q in reqs if q.rid == r.parent] + [r]
+        p = SV.Server(budget_bytes=150e9, precision=lsw.LSW_FP64, streams=1, host_threads=1, graphs=False)
+        out = {x.rid: x for x in p.run(sub, realtime=False, max_inflight=1)}
+        p.close()
+        lat.append(out[r.rid].t_done - out[r.rid].t_admit)
+        nsf += out[r.rid].n_sf
+    plain_s = time.perf_counter() - t1
+    line = {"metric": METRIC + " (serving)", "value": served["support_functions_per_s"],
+            "unit": "support_functions/s", "n_gpus": 1, "steps": len(res), "warmup": 0,
+            "ms_per_step": 1000.0 * served["span_s"] / max(1, len(res)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson 20 req/s, 50-5,000 atoms log-uniform, 30% reuse",
+                       "requests": len(res), "budget_gb": 150},
+            "serving": served, "wall_s": wall,
+            "plain_alone": {"requests": k, "support_functions_per_s": nsf / plain_s,
+                            "p50_latency_s": float(np.percentile(lat, 50)),
+                            "note": "FP64, one function per batch, no graphs, one request at a time"},
+            "clocks": clk.summary(0)}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.mode == "serving":
+        return serving_main(args)
     return gpu_main(args)
 
 

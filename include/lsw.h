@@ -194,6 +194,21 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi_dev, vo
 lsw_status lsw_build_matrices(lsw_system sys, const void* phi_dev, const void* hphi_dev,
                               double* H_dev, double* S_dev);
 
+/* Reuse support functions on a changed geometry (the paper moves them with the atoms
+ * between geometry steps, section "Flexibility of the minimal basis formalism",
+ * subsection "Geometry optimization", with an interpolation scheme it does not
+ * specify; this library's reading: integer grid shifts only, no sub-grid interpolation).  `dst` and `src`
+ * have the same atoms (in the same order, same functions per atom, same precision,
+ * same device); dst's atom a is src's atom a moved by shift[3a..3a+2] grid points
+ * (host array, typically the change of the atom's nearest grid point).  For every
+ * function f and every member p of L_dst(f): phi_dst = phi_src at p - shift if that
+ * point is a member of L_src(f) (coarse part for s, fine part for d^1..d^7), else 0.
+ * phi_src uses src's layout, phi_dst dst's; they must not overlap.  Enqueued on dst's
+ * stream after the work already enqueued on src's stream.
+ * Errors: LSW_ERR_ARG (mismatched systems, NULL), LSW_ERR_STATE, LSW_ERR_CUDA. */
+lsw_status lsw_reformat(lsw_system dst, lsw_system src, const int32_t* shift, const void* phi_src_dev,
+                        void* phi_dst_dev);
+
 /* Device workspace held by the system, bytes. */
 lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes);
 
@@ -208,6 +223,12 @@ lsw_status lsw_sync(lsw_system sys, double timeout_s);
 lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host,
                          double* H_host, double* S_host, double* e_kin_host,
                          double* e_pot_host);
+
+/* Enqueue this system's future work on `stream` (a cudaStream_t of the system's
+ * device; NULL = the legacy default stream) instead of its context's stream.  Waits
+ * for the work already enqueued on the old stream.  Lets a server build systems on one
+ * stream (creation waits for its uploads) and run each request on its own stream. */
+lsw_status lsw_system_set_stream(lsw_system sys, void* stream);
 
 /* Device trace of the enqueued kernels.  enable = 1 records a CUDA event pair around
  * every launch the system enqueues from now on (inside CUDA graphs as event-record

@@ -11,6 +11,7 @@
 // Membership tests are done in IEEE FP64 without contraction (this file is compiled
 // with -ffp-contract=off): d2 = ((x-X)*(x-X) + (y-Y)*(y-Y)) + (z-Z)*(z-Z), x = i*h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -141,7 +142,7 @@ struct lsw_ctx_s {
     FilterSet filters;
     size_t max_smem = 0;
     int n_sm = 0;
-    int live_systems = 0;
+    std::atomic<int> live_systems{0};
 };
 
 struct GraphKey {
@@ -164,6 +165,7 @@ struct Batch {
 
 struct lsw_system_s {
     lsw_ctx ctx = nullptr;
+    cudaStream_t stream = nullptr;   // where this system's work is enqueued (ctx's by default)
     int32_t N[3];
     double h;
     int prec;
@@ -182,10 +184,11 @@ struct lsw_system_s {
     // device state
     DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
     DeviceBuf d_tile_org, d_tile_fine, d_listA, d_listB, d_work, d_ws, d_status, d_escratch;
+    DeviceBuf d_shift, d_fn_all;   // reformat: per-atom shifts, records of every function
     std::vector<Batch> batches;
     int64_t ws_elems = 0;
     int batch_size = 0;
-    int tile = 8;
+    int tile = 4;
     int use_graph = 1;
     int nwork = 0;
     // potential
@@ -456,13 +459,13 @@ lsw_status build_plans(lsw_system_s* s) {
             p.smem_z = std::max(p.smem_z, a2);
             p.smem_bwd = std::max(p.smem_bwd, a3);
         }
-        if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd > s->ctx->max_smem)
+        if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem)
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles (%zu/%zu/%zu > %zu bytes)",
                         p.smem_fwd, p.smem_z, p.smem_bwd, s->ctx->max_smem);
         s->batches.push_back(b);
     }
     s->ws_elems = ws_max;
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->stream;
     CUDA_TRY(s->d_fn.upload(recs, st));
     for (auto& b : s->batches) b.proto.fn = static_cast<const FnRec*>(s->d_fn.p) + b.fn0;
     CUDA_TRY(s->d_ws.alloc(static_cast<size_t>(ws_max) * s->esize));
@@ -550,7 +553,7 @@ lsw_status build_hs_plan(lsw_system_s* s) {
     org.push_back(0);
     org.push_back(0);
     org.push_back(static_cast<int32_t>(fine.size()));  // sentinel: end of the last fine list
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->stream;
     CUDA_TRY(s->d_tile_org.upload(org, st));
     CUDA_TRY(s->d_tile_fine.upload(fine, st));
     CUDA_TRY(s->d_listA.upload(fA, st));
@@ -583,7 +586,7 @@ lsw_status upload_geometry(lsw_system_s* s) {
         emit_segments(s->N, P, P.c, &seg, &rowptr, &r.segPc, &r.nsegPc, &r.rowPc);
         emit_segments(s->N, P, P.f, &seg, &rowptr, &r.segPf, &r.nsegPf, &r.rowPf);
     }
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->stream;
     CUDA_TRY(s->d_atoms.upload(recs, st));
     CUDA_TRY(s->d_seg.upload(seg, st));
     CUDA_TRY(s->d_rowptr.upload(rowptr, st));
@@ -616,7 +619,7 @@ void harvest(lsw_system_s* s, Tracer* tr) {
 }
 
 lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hphi, double* ek, double* ep) {
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->stream;
     const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
     CUDA_TRY(cudaMemsetAsync(ek, 0, nf * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(ep, 0, nf * sizeof(double), st));
@@ -651,7 +654,7 @@ lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hph
 }
 
 lsw_status enqueue_matrices(lsw_system_s* s, Tracer* tr, const void* phi, const void* hphi, double* H, double* S) {
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->stream;
     const int64_t nnz = static_cast<int64_t>(s->col.size());
     CUDA_TRY(cudaMemsetAsync(H, 0, nnz * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(S, 0, nnz * sizeof(double), st));
@@ -701,7 +704,7 @@ lsw_status enqueue_matrices(lsw_system_s* s, Tracer* tr, const void* phi, const 
 template <class Enq>
 lsw_status run_maybe_graph(lsw_system_s* s, std::map<GraphKey, lsw_system_s::GraphEntry>* cache, GraphKey key,
                            Enq enq) {
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->stream;
     if (!s->use_graph || st == nullptr) {
         Tracer* tr = nullptr;
         if (s->profiling) {
@@ -787,7 +790,7 @@ lsw_status lsw_ctx_create(int device, void* stream, lsw_ctx* out) {
 lsw_status lsw_ctx_destroy(lsw_ctx ctx) {
     g_err.clear();
     if (!ctx) return LSW_OK;
-    if (ctx->live_systems != 0) return fail(LSW_ERR_STATE, "lsw_ctx_destroy: %d systems alive", ctx->live_systems);
+    if (ctx->live_systems != 0) return fail(LSW_ERR_STATE, "lsw_ctx_destroy: %d systems alive", ctx->live_systems.load());
     if (!ctx->host_only && ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LSW_OK;
@@ -849,6 +852,7 @@ lsw_status lsw_system_create(lsw_ctx ctx, const lsw_system_desc* d, lsw_system* 
     std::unique_ptr<lsw_system_s> s(new (std::nothrow) lsw_system_s());
     if (!s) return fail(LSW_ERR_OOM, "lsw_system_create: host allocation");
     s->ctx = ctx;
+    s->stream = ctx->stream;
     for (int k = 0; k < 3; ++k) s->N[k] = d->N[k];
     s->h = d->h;
     s->prec = d->precision;
@@ -1037,7 +1041,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
     const size_t head = (NOALLOC_MAX_BATCH * sizeof(FnRec) + 255) / 256 * 256;
     const int64_t cap = static_cast<int64_t>((NOALLOC_SCRATCH_BYTES - head) / sys->esize);
     const int zcols = sys->prec == LSW_FP64 ? 64 : 128;
-    cudaStream_t st = sys->ctx->stream;
+    cudaStream_t st = sys->stream;
     const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
     double* e0 = static_cast<double*>(sys->d_escratch.p);
     if (!ek) ek = e0;
@@ -1118,7 +1122,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             p.smem_z = std::max(p.smem_z, a2);
             p.smem_bwd = std::max(p.smem_bwd, a3);
         }
-        if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd > sys->ctx->max_smem)
+        if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > sys->ctx->max_smem)
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
         // records into the head of the scratch (pageable source: reusable on return)
         CUDA_TRY(cudaMemcpyAsync(scratch, recs, nb * sizeof(FnRec), cudaMemcpyHostToDevice, st));
@@ -1151,6 +1155,67 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
     return LSW_OK;
 }
 
+lsw_status lsw_reformat(lsw_system dst, lsw_system src, const int32_t* shift, const void* phi_src, void* phi_dst) {
+    g_err.clear();
+    if (!dst || !src || !shift || !phi_src || !phi_dst) return fail(LSW_ERR_ARG, "lsw_reformat: NULL argument");
+    if (dst->ctx->host_only || src->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (dst->ctx->device != src->ctx->device) return fail(LSW_ERR_ARG, "lsw_reformat: systems on different devices");
+    if (dst->prec != src->prec) return fail(LSW_ERR_ARG, "lsw_reformat: precisions differ");
+    if (dst->n_atoms != src->n_atoms || dst->nsf != src->nsf)
+        return fail(LSW_ERR_ARG, "lsw_reformat: atoms or support functions per atom differ");
+    if (phi_src == phi_dst) return fail(LSW_ERR_ARG, "lsw_reformat: source and destination overlap");
+    CUDA_TRY(cudaSetDevice(dst->ctx->device));
+    cudaStream_t st = dst->stream;
+    const int64_t nf = static_cast<int64_t>(dst->sf_atom.size());
+    // the source's stream must have finished writing phi_src: order the two streams
+    if (src->stream != st) {
+        CUDA_TRY(cudaEventRecord(src->done, src->stream));
+        CUDA_TRY(cudaStreamWaitEvent(st, src->done, 0));
+    }
+    std::vector<int32_t> sh(shift, shift + 3 * dst->n_atoms);
+    CUDA_TRY(dst->d_shift.upload(sh, st));
+    if (!dst->d_fn_all.p) {
+        std::vector<FnRec> recs(nf);
+        for (int64_t f = 0; f < nf; ++f) {
+            FnRec& r = recs[f];
+            std::memset(&r, 0, sizeof(r));
+            r.f = static_cast<int32_t>(f);
+            r.atom = dst->sf_atom[f];
+            for (int d = 0; d < 3; ++d) {
+                r.lo[d] = dst->L[r.atom].lo[d];
+                r.n[d] = dst->L[r.atom].n[d];
+            }
+            r.off_phi = dst->off_L[f];
+        }
+        CUDA_TRY(dst->d_fn_all.upload(recs, st));
+    }
+    ReformatLaunch p;
+    std::memset(&p, 0, sizeof(p));
+    p.fn = static_cast<const FnRec*>(dst->d_fn_all.p);
+    p.nfn = static_cast<int>(nf);
+    for (int a = 0; a < dst->n_atoms; ++a)
+        p.max_seg = std::max<int>(p.max_seg, static_cast<int>((dst->L[a].c.keys.size() + dst->L[a].f.keys.size()) / 3));
+    p.atoms_dst = static_cast<const AtomRec*>(dst->d_atoms.p);
+    p.atoms_src = static_cast<const AtomRec*>(src->d_atoms.p);
+    p.seg_dst = static_cast<const Seg*>(dst->d_seg.p);
+    p.seg_src = static_cast<const Seg*>(src->d_seg.p);
+    p.rowptr_src = static_cast<const int32_t*>(src->d_rowptr.p);
+    p.shift = static_cast<const int32_t*>(dst->d_shift.p);
+    p.off_src = static_cast<const int64_t*>(src->d_offL.p);
+    p.phi_src = phi_src;
+    p.phi_dst = phi_dst;
+    p.prec = dst->prec;
+    p.status = static_cast<int*>(dst->d_status.p);
+    p.seg_dst_n = static_cast<int64_t>(dst->d_seg.bytes / sizeof(Seg));
+    p.seg_src_n = static_cast<int64_t>(src->d_seg.bytes / sizeof(Seg));
+    p.rowptr_src_n = static_cast<int64_t>(src->d_rowptr.bytes / sizeof(int32_t));
+    p.src_n = src->off_L.back();
+    p.dst_n = dst->off_L.back();
+    CUDA_TRY(cudaMemsetAsync(phi_dst, 0, static_cast<size_t>(dst->off_L.back()) * dst->esize, st));
+    CUDA_TRY(enqueue_reformat(p, st));
+    return LSW_OK;
+}
+
 lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
     g_err.clear();
     if (!sys || !bytes) return fail(LSW_ERR_ARG, "lsw_workspace_bytes: NULL argument");
@@ -1158,7 +1223,7 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
                                &sys->d_sfatom, &sys->d_rowp, &sys->d_col, &sys->d_tile_org, &sys->d_tile_fine,
                                &sys->d_listA, &sys->d_listB, &sys->d_work, &sys->d_ws, &sys->d_status,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
-                               &sys->d_ep};
+                               &sys->d_ep, &sys->d_shift, &sys->d_fn_all};
     int64_t b = 0;
     for (auto* p : bufs) b += static_cast<int64_t>(p->bytes);
     *bytes = b;
@@ -1170,7 +1235,7 @@ lsw_status lsw_sync(lsw_system sys, double timeout_s) {
     if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys) return fail(LSW_ERR_ARG, "lsw_sync: NULL system");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
-    CUDA_TRY(cudaEventRecord(sys->done, sys->ctx->stream));
+    CUDA_TRY(cudaEventRecord(sys->done, sys->stream));
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaEventQuery(sys->done);
@@ -1211,7 +1276,7 @@ lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host, 
         CUDA_TRY(sys->d_ek.alloc(nf * sizeof(double)));
         CUDA_TRY(sys->d_ep.alloc(nf * sizeof(double)));
     }
-    cudaStream_t st = sys->ctx->stream;
+    cudaStream_t st = sys->stream;
     CUDA_TRY(cudaMemcpyAsync(sys->d_phi.p, phi_host, bphi, cudaMemcpyHostToDevice, st));
     lsw_status r = lsw_apply_hamiltonian(sys, sys->d_phi.p, sys->d_hphi.p, static_cast<double*>(sys->d_ek.p),
                                          static_cast<double*>(sys->d_ep.p));
@@ -1227,13 +1292,23 @@ lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host, 
     return lsw_sync(sys, 600.0);
 }
 
+lsw_status lsw_system_set_stream(lsw_system sys, void* stream) {
+    g_err.clear();
+    if (!sys) return fail(LSW_ERR_ARG, "lsw_system_set_stream: NULL system");
+    if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(sys->stream));
+    sys->stream = static_cast<cudaStream_t>(stream);
+    return LSW_OK;
+}
+
 lsw_status lsw_profile(lsw_system sys, int32_t enable) {
     g_err.clear();
     if (!sys) return fail(LSW_ERR_ARG, "lsw_profile: NULL system");
     if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (enable != 0 && enable != 1) return fail(LSW_ERR_ARG, "lsw_profile: enable %d", enable);
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
-    CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(sys->stream));
     drop_graphs(sys);
     sys->direct_tr.reset();
     sys->profiling = enable;
@@ -1246,7 +1321,7 @@ lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds,
     if (!sys || !n_kinds || !ms || !launches) return fail(LSW_ERR_ARG, "lsw_profile_read: NULL argument");
     if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
-    CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(sys->stream));
     harvest(sys, sys->direct_tr.get());
     for (auto* c : {&sys->graphs_h, &sys->graphs_m})
         for (auto& kv : *c) harvest(sys, kv.second.tr.get());
@@ -1267,7 +1342,7 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
     if (std::strcmp(name, "batch") == 0) {
         if (value < 1 || value > 4096) return fail(LSW_ERR_ARG, "lsw_set_option: batch %lld", static_cast<long long>(value));
-        CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
         drop_graphs(sys);
         sys->batch_size = static_cast<int>(value);
         return build_plans(sys);
@@ -1279,7 +1354,7 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
     }
     if (std::strcmp(name, "tile") == 0) {
         if (value < 2 || value > 8) return fail(LSW_ERR_ARG, "lsw_set_option: tile %lld", static_cast<long long>(value));
-        CUDA_TRY(cudaStreamSynchronize(sys->ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
         drop_graphs(sys);
         sys->tile = static_cast<int>(value);
         return build_hs_plan(sys);

@@ -18,6 +18,7 @@ constexpr int FWD_LO = -14;      // combined filters (w * h), (w * g): m = -14..
 constexpr int FWD_TAPS = 31;
 constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [2lo-14, 2hi+16]
 constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
+constexpr size_t BWD_STATIC_SMEM = 12 * 1024;   // upper bound of k_bwd_xy's static shared memory
 
 // Filter tables, FP64 (rounded once from double-double).
 struct FilterSet {
@@ -135,6 +136,26 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(32) << 20;   // 32 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 constexpr int NOALLOC_MAX_BATCH = 64;      // functions per batch (records kept in the scratch)
 cudaError_t noalloc_scratch(int device, void** ptr);
+
+// Support-function reuse across geometries (lsw_reformat).
+struct ReformatLaunch {
+    const FnRec* fn;             // destination records (boxes, offsets); unused ws fields
+    int nfn;
+    int max_seg;                 // largest coarse+fine segment count of a destination L
+    const AtomRec* atoms_dst;
+    const AtomRec* atoms_src;
+    const Seg* seg_dst;
+    const Seg* seg_src;
+    const int32_t* rowptr_src;
+    const int32_t* shift;        // [n_atoms][3] grid shift of each atom (dst = src + shift)
+    const int64_t* off_src;      // source function offsets
+    const void* phi_src;
+    void* phi_dst;
+    int prec;
+    int* status;
+    int64_t seg_dst_n, seg_src_n, rowptr_src_n, src_n, dst_n;
+};
+cudaError_t enqueue_reformat(const ReformatLaunch& a, cudaStream_t s);
 
 // Device entry points (lsw_kernels.cu).
 cudaError_t upload_filters(const FilterSet& fs, int device);

@@ -162,6 +162,18 @@ __global__ void k_compress(HphiLaunch a) {
     }
 }
 
+// Division by a loop-invariant divisor d (1 <= d < 2^16) for dividends n < 2^16:
+// q = umulhi(n, ceil(2^32 / d)) is exact there (the error term n / 2^32 < 2^-16 cannot
+// reach the next integer).  Replaces the ~20-instruction integer division in index math.
+struct FastDiv {
+    uint32_t m;
+    int d;
+    __device__ __forceinline__ explicit FastDiv(int dd) : m(dd > 1 ? 0xFFFFFFFFu / static_cast<uint32_t>(dd) + 1u : 0u), d(dd) {}
+    __device__ __forceinline__ int div(int n) const {
+        return d > 1 ? static_cast<int>(__umulhi(static_cast<uint32_t>(n), m)) : n;
+    }
+};
+
 // ---------------------------------------------------------------- register-blocked 1D blocks
 //
 // Forward (synthesis + magic filter, upsampling by 2): u[2p+e] = sum_{k} F_b[2k+e] in_b[p-k],
@@ -250,9 +262,10 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
     const T* D = static_cast<const T*>(a.ws) + r.ws_D;
     const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
     const int pn = nx * ny;
+    const FastDiv fd_pn(pn), fd_nx(nx), fd_ny(ny), fd_2ny(2 * ny), fd_X(X);
     for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
-        const int tb = i / pn, rem = i - tb * pn;
-        const int y = rem / nx, x = rem - y * nx;
+        const int tb = fd_pn.div(i), rem = i - tb * pn;
+        const int y = fd_nx.div(rem), x = rem - y * nx;
         ST(in, (tb * ny + y) * RS + x, smem_n,
            LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(z) * pn + rem, 8 * plane));
     }
@@ -260,8 +273,8 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
     // x pass: rows (by, y), blocks of 8 outputs along x'
     const int nbx = (nx + 15 + FB - 1) / FB;
     for (int task = threadIdx.x; task < 2 * ny * nbx; task += blockDim.x) {
-        const int row = task % (2 * ny), blk = task / (2 * ny);
-        const int by = row / ny, y = row - by * ny;
+        const int blk = fd_2ny.div(task), row = task - blk * 2 * ny;
+        const int by = fd_ny.div(row), y = row - by * ny;
         const int p0 = blk * FB;
         const int s0 = ((2 * by) * ny + y) * RS, d0 = s0 + ny * RS;
         T w0[FW], w1[FW], u[2 * FB];
@@ -285,7 +298,7 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
     const int64_t bf_room = 2LL * nz * Y * X - (static_cast<int64_t>(bz) * nz + z) * Y * X;
     const int nby = (ny + 15 + FB - 1) / FB;
     for (int task = threadIdx.x; task < X * nby; task += blockDim.x) {
-        const int xo = task % X, blk = task / X;
+        const int blk = fd_X.div(task), xo = task - blk * X;
         const int p0 = blk * FB;
         T w0[FW], w1[FW], u[2 * FB];
 #pragma unroll
@@ -387,16 +400,28 @@ __global__ void k_z(HphiLaunch a) {
 // ---------------------------------------------------------------- backward y, x + kinetic x, y
 
 // Per plane (z'', bz) of the L' box: transposed filters along y then x (potential part)
-// plus the kinetic arms along x and y of the four output types with z bit bz.
+// plus the kinetic arms along x and y of the four output types with z bit bz.  Only
+// what the compress step reads is computed: rows of the plane holding members of L'
+// and, in each row, the x range of its member segment (L' is a sphere clipped by the
+// box, so one segment per row); kinetic type pairs whose input rows or columns of D
+// are all zero (wavelet types off the fine region) are skipped.  Each phase first
+// lists its tasks in shared memory, so skipped work frees whole rounds.
+constexpr int BWD_MAX_TASKS = 2048;
+
 template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int16_t rx0[256], rx1[256];         // member x range per row (L' plane), -1: none
+    __shared__ int task[BWD_MAX_TASKS];
+    __shared__ int ntask, ylo, yhi, xlo, xhi;
+    __shared__ unsigned char rowf[4][128], colf[4][128];   // D plane: nonzero per (type, row / column)
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[blockIdx.y];
     const int zb = blockIdx.x >> 1, bz = blockIdx.x & 1;
     if (zb >= r.np[2]) return;
+    const AtomRec& at = a.atoms[r.atom];
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int X = 2 * nx + 29, Y = 2 * ny + 29;
     const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
@@ -410,142 +435,217 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
     const int64_t smem_n = static_cast<int64_t>(a.smem_bwd / sizeof(T));
     const int zL = zb + dz;
     const bool dplane = zL >= 0 && zL < nz;
+    if (threadIdx.x == 0) {
+        ylo = nyp;
+        yhi = -1;
+        xlo = nxp;
+        xhi = -1;
+    }
+    for (int i = threadIdx.x; i < 4 * 128; i += blockDim.x) {
+        rowf[i >> 7][i & 127] = 0;
+        colf[i >> 7][i & 127] = 0;
+    }
+    __syncthreads();
+    // member x range of each row of this plane (coarse part of L')
+    for (int y = threadIdx.x; y < nyp; y += blockDim.x) {
+        const int64_t row = at.rowPc + y + static_cast<int64_t>(nyp) * zb;
+        const int s0 = LD(a.rowptr, row, a.rowptr_n), s1 = LD(a.rowptr, row + 1, a.rowptr_n);
+        int lo = -1, hi = -1;
+        if (s1 > s0) {
+            lo = LD(a.seg, at.segPc + s0, a.seg_n).x0;
+            hi = LD(a.seg, at.segPc + s1 - 1, a.seg_n).x1;
+            atomicMin(&ylo, y);
+            atomicMax(&yhi, y);
+            atomicMin(&xlo, lo);
+            atomicMax(&xhi, hi);
+        }
+        rx0[y] = static_cast<int16_t>(lo);
+        rx1[y] = static_cast<int16_t>(hi);
+    }
     const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
     const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
     for (int i = threadIdx.x; i < Y * X; i += blockDim.x) ST(pl, i, smem_n, LD(Bb, i, bb_room));
     const T* D = static_cast<const T*>(a.ws) + r.ws_D;
     const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
     const int pn = nx * ny;
-    if (dplane)
+    const int64_t dp_n = smem_n - plA - 2LL * nyp * X;
+    if (dplane) {
+        const FastDiv fd_pn(pn), fd_nx(nx);
         for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
-            const int tb = i / pn, rem = i - tb * pn;
-            const int y = rem / nx, x = rem - y * nx;
-            ST(Dp, (tb * ny + y) * RS + x, smem_n - plA - 2 * nyp * X,
-               LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem, 8 * plane));
+            const int tb = fd_pn.div(i), rem = i - tb * pn;
+            const int y = fd_nx.div(rem), x = rem - y * nx;
+            const T v = LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem, 8 * plane);
+            ST(Dp, (tb * ny + y) * RS + x, dp_n, v);
+            if (v != T(0)) {
+                rowf[tb][y & 127] = 1;
+                colf[tb][x & 127] = 1;
+            }
         }
+    }
+    if (threadIdx.x == 0) ntask = 0;
     __syncthreads();
     const int64_t mid_n = 2LL * nyp * X;
-    const int64_t dp_n = smem_n - plA - mid_n;
-    // y pass (transposed filters, decimating): columns x', blocks of BB outputs b
-    const int nbb = (nyp + BB - 1) / BB;
-    for (int task = threadIdx.x; task < X * nbb; task += blockDim.x) {
-        const int xo = task % X, b0 = (task / X) * BB;
-        const int base = 2 * (b0 + dy);
-        T w[BW], s[BB], d[BB];
-#pragma unroll
-        for (int i = 0; i < BW; ++i) {
-            const int yo = base + i;
-            w[i] = (yo >= 0 && yo < Y) ? LD(pl, yo * X + xo, smem_n) : T(0);
-        }
-        bwd_block(w, s, d);
-#pragma unroll
-        for (int j = 0; j < BB; ++j) {
-            const int b = b0 + j;
-            if (b < nyp) {
-                ST(mid, static_cast<int64_t>(b) * X + xo, mid_n, s[j]);
-                ST(mid, static_cast<int64_t>(nyp + b) * X + xo, mid_n, d[j]);
-            }
-        }
-    }
-    __syncthreads();   // pl is dead from here on: Gs reuses it
-    const T ks = static_cast<T>(a.kin_scale);
-    T ekin_t = 0;     // per-thread partial in the kernel's precision
-    // x pass (transposed filters): rows (by, b), blocks of BB outputs along x''
-    const int nbx = (nxp + BB - 1) / BB;
     const int64_t gs_n = 4LL * nyp * nxp;
-    for (int task = threadIdx.x; task < 2 * nyp * nbx; task += blockDim.x) {
-        const int row = task % (2 * nyp), x0 = (task / (2 * nyp)) * BB;
-        const int by = row / nyp, b = row - by * nyp;
-        const int base = 2 * (x0 + dx);
-        T w[BW], s[BB], d[BB];
+    const T ks = static_cast<T>(a.kin_scale);
+    T ekin_t = 0;
+    const int ylo_ = ylo, yhi_ = yhi;
+    if (yhi_ >= 0) {
+        // ---- y pass: columns x', blocks of BB rows b within [ylo, yhi]
+        const int nbb = (yhi_ - ylo_ + BB) / BB;
+        {
+            const FastDiv fd_X(X);
+            for (int tk = threadIdx.x; tk < X * nbb; tk += blockDim.x) {
+                const int q = fd_X.div(tk), xo = tk - q * X, b0 = ylo_ + q * BB;
+                const int base = 2 * (b0 + dy);
+                T w[BW], s[BB], d[BB];
 #pragma unroll
-        for (int i = 0; i < BW; ++i) {
-            const int xo = base + i;
-            w[i] = (xo >= 0 && xo < X) ? LD(mid, row * X + xo, mid_n) : T(0);
-        }
-        bwd_block(w, s, d);
+                for (int i = 0; i < BW; ++i) {
+                    const int yo = base + i;
+                    w[i] = (yo >= 0 && yo < Y) ? LD(pl, yo * X + xo, smem_n) : T(0);
+                }
+                bwd_block(w, s, d);
 #pragma unroll
-        for (int j = 0; j < BB; ++j) {
-            const int xb = x0 + j;
-            if (xb < nxp) {
-                ST(Gs, ((0 + 2 * by) * nyp + b) * nxp + xb, gs_n, s[j]);
-                ST(Gs, ((1 + 2 * by) * nyp + b) * nxp + xb, gs_n, d[j]);
+                for (int j = 0; j < BB; ++j) {
+                    const int b = b0 + j;
+                    if (b <= yhi_) {
+                        ST(mid, static_cast<int64_t>(b) * X + xo, mid_n, s[j]);
+                        ST(mid, static_cast<int64_t>(nyp + b) * X + xo, mid_n, d[j]);
+                    }
+                }
             }
         }
-    }
-    if (dplane) {
+        __syncthreads();   // pl is dead from here on: Gs reuses it
+        // ---- task list: (by, row b, x block) intersecting the row's member range
+        for (int b = ylo_ + threadIdx.x; b <= yhi_; b += blockDim.x) {
+            if (rx0[b] < 0) continue;
+            const int k0 = rx0[b] / BB, k1 = rx1[b] / BB;
+            for (int by = 0; by < 2; ++by) {
+                const int base = atomicAdd(&ntask, k1 - k0 + 1);
+                for (int k = k0; k <= k1; ++k)
+                    if (base + k - k0 < BWD_MAX_TASKS) task[base + k - k0] = (by << 24) | (b << 12) | k;
+            }
+        }
         __syncthreads();
-        // kinetic x arm: rows (by, y''), blocks of BB outputs along x''; pair (bx = 0, 1)
-        for (int task = threadIdx.x; task < 2 * nyp * nbx; task += blockDim.x) {
-            const int row = task % (2 * nyp), x0 = (task / (2 * nyp)) * BB;
-            const int by = row / nyp, b = row - by * nyp;
-            const int y = b + dy;
-            if (y < 0 || y >= ny) continue;
-            T k0[KW], k1[KW], o0[BB], o1[BB];
-            const int r0 = ((2 * by) * ny + y) * RS, r1 = r0 + ny * RS;
+        const int nt_x = min(ntask, BWD_MAX_TASKS);
+        if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
+        // ---- x pass (transposed filters) on the listed row blocks
+        for (int it = threadIdx.x; it < nt_x; it += blockDim.x) {
+            const int code = task[it];
+            const int by = code >> 24, b = (code >> 12) & 4095, x0 = (code & 4095) * BB;
+            const int row = by * nyp + b;
+            const int base = 2 * (x0 + dx);
+            T w[BW], s[BB], d[BB];
 #pragma unroll
-            for (int i = 0; i < KW; ++i) {
-                const int x = x0 + dx - KIN_HALF + i;
-                const bool ok = x >= 0 && x < nx;
-                k0[i] = ok ? LD(Dp, r0 + x, dp_n) : T(0);
-                k1[i] = ok ? LD(Dp, r1 + x, dp_n) : T(0);
+            for (int i = 0; i < BW; ++i) {
+                const int xo = base + i;
+                w[i] = (xo >= 0 && xo < X) ? LD(mid, row * X + xo, mid_n) : T(0);
             }
-            kin_block(k0, k1, o0, o1);
+            bwd_block(w, s, d);
 #pragma unroll
             for (int j = 0; j < BB; ++j) {
                 const int xb = x0 + j;
                 if (xb < nxp) {
-                    o0[j] *= ks;
-                    o1[j] *= ks;
-                    const int64_t g0 = ((0 + 2 * by) * nyp + b) * nxp + xb;
-                    const int64_t g1 = ((1 + 2 * by) * nyp + b) * nxp + xb;
-                    ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
-                    ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
-                    const int x = x0 + dx + j;
-                    if (x >= 0 && x < nx) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
+                    ST(Gs, ((0 + 2 * by) * nyp + b) * nxp + xb, gs_n, s[j]);
+                    ST(Gs, ((1 + 2 * by) * nyp + b) * nxp + xb, gs_n, d[j]);
                 }
             }
         }
-        __syncthreads();
-        // kinetic y arm: columns (bx, x''), blocks of BB outputs along y''; pair (by = 0, 1)
-        const int nbyk = (nyp + BB - 1) / BB;
-        for (int task = threadIdx.x; task < 2 * nxp * nbyk; task += blockDim.x) {
-            const int colx = task % (2 * nxp), b0 = (task / (2 * nxp)) * BB;
-            const int bx = colx / nxp, xb = colx - bx * nxp;
-            const int x = xb + dx;
-            if (x < 0 || x >= nx) continue;
-            T k0[KW], k1[KW], o0[BB], o1[BB];
+        if (dplane) {
+            __syncthreads();
+            // ---- kinetic x arm on the same row blocks, pair (bx = 0, 1) of each by
+            for (int it = threadIdx.x; it < nt_x; it += blockDim.x) {
+                const int code = task[it];
+                const int by = code >> 24, b = (code >> 12) & 4095, x0 = (code & 4095) * BB;
+                const int y = b + dy;
+                if (y < 0 || y >= ny) continue;
+                if (!rowf[2 * by][y & 127] && !rowf[2 * by + 1][y & 127]) continue;   // both inputs zero
+                T k0[KW], k1[KW], o0[BB], o1[BB];
+                const int r0 = ((2 * by) * ny + y) * RS, r1 = r0 + ny * RS;
 #pragma unroll
-            for (int i = 0; i < KW; ++i) {
-                const int y = b0 + dy - KIN_HALF + i;
-                const bool ok = y >= 0 && y < ny;
-                k0[i] = ok ? LD(Dp, ((bx + 0) * ny + y) * RS + x, dp_n) : T(0);
-                k1[i] = ok ? LD(Dp, ((bx + 2) * ny + y) * RS + x, dp_n) : T(0);
+                for (int i = 0; i < KW; ++i) {
+                    const int x = x0 + dx - KIN_HALF + i;
+                    const bool ok = x >= 0 && x < nx;
+                    k0[i] = ok ? LD(Dp, r0 + x, dp_n) : T(0);
+                    k1[i] = ok ? LD(Dp, r1 + x, dp_n) : T(0);
+                }
+                kin_block(k0, k1, o0, o1);
+#pragma unroll
+                for (int j = 0; j < BB; ++j) {
+                    const int xb = x0 + j;
+                    if (xb < nxp) {
+                        o0[j] *= ks;
+                        o1[j] *= ks;
+                        const int64_t g0 = ((0 + 2 * by) * nyp + b) * nxp + xb;
+                        const int64_t g1 = ((1 + 2 * by) * nyp + b) * nxp + xb;
+                        ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
+                        ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
+                        const int x = x0 + dx + j;
+                        if (x >= 0 && x < nx) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
+                    }
+                }
             }
-            kin_block(k0, k1, o0, o1);
+            __syncthreads();
+            if (threadIdx.x == 0) ntask = 0;
+            __syncthreads();
+            // ---- kinetic y arm: (bx, column x'' in [xlo, xhi], block of rows in [ylo, yhi])
+            const int nbyk = (yhi_ - ylo_ + BB) / BB;
+            const int ncols = xhi - xlo + 1;
+            for (int c = threadIdx.x; c < 2 * ncols; c += blockDim.x) {
+                const int bx = c >= ncols, xb = xlo + (c - bx * ncols);
+                const int x = xb + dx;
+                if (x < 0 || x >= nx) continue;
+                if (!colf[bx][x & 127] && !colf[bx + 2][x & 127]) continue;
+                const int base = atomicAdd(&ntask, nbyk);
+                for (int k = 0; k < nbyk; ++k)
+                    if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | k;
+            }
+            __syncthreads();
+            const int nt_y = min(ntask, BWD_MAX_TASKS);
+            if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
+            for (int it = threadIdx.x; it < nt_y; it += blockDim.x) {
+                const int code = task[it];
+                const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = ylo_ + (code & 4095) * BB;
+                const int x = xb + dx;
+                T k0[KW], k1[KW], o0[BB], o1[BB];
 #pragma unroll
-            for (int j = 0; j < BB; ++j) {
-                const int b = b0 + j;
-                if (b < nyp) {
-                    o0[j] *= ks;
-                    o1[j] *= ks;
-                    const int64_t g0 = (static_cast<int64_t>(bx + 0) * nyp + b) * nxp + xb;
-                    const int64_t g1 = (static_cast<int64_t>(bx + 2) * nyp + b) * nxp + xb;
-                    ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
-                    ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
-                    const int y = b + dy;
-                    if (y >= 0 && y < ny) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
+                for (int i = 0; i < KW; ++i) {
+                    const int y = b0 + dy - KIN_HALF + i;
+                    const bool ok = y >= 0 && y < ny;
+                    k0[i] = ok ? LD(Dp, ((bx + 0) * ny + y) * RS + x, dp_n) : T(0);
+                    k1[i] = ok ? LD(Dp, ((bx + 2) * ny + y) * RS + x, dp_n) : T(0);
+                }
+                kin_block(k0, k1, o0, o1);
+#pragma unroll
+                for (int j = 0; j < BB; ++j) {
+                    const int b = b0 + j;
+                    if (b <= yhi_) {
+                        o0[j] *= ks;
+                        o1[j] *= ks;
+                        const int64_t g0 = (static_cast<int64_t>(bx + 0) * nyp + b) * nxp + xb;
+                        const int64_t g1 = (static_cast<int64_t>(bx + 2) * nyp + b) * nxp + xb;
+                        ST(Gs, g0, gs_n, LD(Gs, g0, gs_n) + o0[j]);
+                        ST(Gs, g1, gs_n, LD(Gs, g1, gs_n) + o1[j]);
+                        const int y = b + dy;
+                        if (y >= 0 && y < ny) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
+                    }
                 }
             }
         }
     }
     __syncthreads();
+    // write the member rows of the four type planes (values off the members are never read)
     T* G = static_cast<T*>(a.ws) + r.ws_G;
     const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
-    const int pnp = nxp * nyp;
-    for (int i = threadIdx.x; i < 4 * pnp; i += blockDim.x) {
-        const int tb = i / pnp, rem = i - tb * pnp;
-        ST(G, (tb + 4 * bz) * gplane + static_cast<int64_t>(zb) * pnp + rem, 8 * gplane, LD(Gs, i, gs_n));
+    if (yhi_ >= 0) {
+        const int nrows = yhi_ - ylo_ + 1;
+        const int n = 4 * nrows * nxp;
+        const FastDiv fd_row(nrows * nxp), fd_nxp(nxp);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int tb = fd_row.div(i), rem = i - tb * nrows * nxp;
+            const int b = ylo_ + fd_nxp.div(rem), xb = rem - (b - ylo_) * nxp;
+            ST(G, (tb + 4 * bz) * gplane + (static_cast<int64_t>(zb) * nyp + b) * nxp + xb, 8 * gplane,
+               LD(Gs, (tb * nyp + b) * nxp + xb, gs_n));
+        }
     }
     const double ekin = warp_sum(static_cast<double>(ekin_t));
     if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
@@ -564,6 +664,7 @@ __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
     const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
     const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;   // column (x, y) of the L box
+    const int tb = blockIdx.z;                             // type pair (tb, tb + 4)
     T ekin_t = 0;
     if (c < nx * ny) {
         const int y = c / nx, x = c - y * nx;
@@ -577,7 +678,7 @@ __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
             const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
             const int64_t gcol = static_cast<int64_t>(yb) * nxp + xb;
             const T ks = static_cast<T>(a.kin_scale);
-            for (int tb = 0; tb < 4; ++tb) {
+            {
                 for (int b0 = 0; b0 < nzp; b0 += BB) {
                     T k0[KW], k1[KW], o0[BB], o1[BB];
 #pragma unroll
@@ -660,7 +761,7 @@ __device__ __forceinline__ void row_gather(const HSLaunch& a, int64_t seg0, int6
 // chunk by chunk and accumulates S_ab (phi_a . phi_b) and H_ab (phi_a . H phi_b) for
 // all 64 x 64 pairs, 4 x 4 per thread; pattern pairs are added to the CSR in FP64.
 template <class T>
-__global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 7;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -684,14 +785,17 @@ __global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
     const int n_fine_chunks = (nfine + fpc - 1) / fpc;
     const int tid = threadIdx.x;
     const int ti = tid >> 4, tj = tid & 15;                // pairs (ti + 16u, tj + 16v)
-    double sacc[4][4], hacc[4][4];
+    // per-work-item sums in the panel precision (<= T^3 + 7 * fine points terms);
+    // the sums over tiles are FP64 (the atomic adds into the CSR values)
+    T sacc[4][4], hacc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) sacc[u][v] = 0.0, hacc[u][v] = 0.0;
+        for (int v = 0; v < 4; ++v) sacc[u][v] = T(0), hacc[u][v] = T(0);
     const T* phi = static_cast<const T*>(a.phi);
     const T* hphi = static_cast<const T*>(a.hphi);
     const int nslot = w.na + w.nb;
+    const int UA = (w.na + 15) >> 4, UB = (w.nb + 15) >> 4;   // 16-row groups in use
     for (int ch = 0; ch < n_coarse_chunks + n_fine_chunks; ++ch) {
         const bool coarse = ch < n_coarse_chunks;
         int kcount;
@@ -700,9 +804,11 @@ __global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
             const int nr = min(rows_per_chunk, n_rows - r0);
             kcount = nr * TL;
             // task = (slot, tile row)
+            const FastDiv fd_nr(nr), fd_TL(TL);
             for (int task = tid; task < nslot * nr; task += blockDim.x) {
-                const int slot = task / nr, rr = r0 + (task - slot * nr);
-                const int gy = oy + rr % TL, gz = oz + rr / TL;
+                const int slot = fd_nr.div(task), rr = r0 + (task - slot * nr);
+                const int rz = fd_TL.div(rr);
+                const int gy = oy + (rr - rz * TL), gz = oz + rz;
                 const int col0 = (rr - r0) * TL;
                 const bool isA = slot < w.na;
                 const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
@@ -724,8 +830,9 @@ __global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
             const int q0 = (ch - n_coarse_chunks) * fpc;
             const int npts = min(fpc, nfine - q0);
             kcount = 7 * npts;
+            const FastDiv fd_np(npts);
             for (int task = tid; task < nslot * npts; task += blockDim.x) {
-                const int slot = task / npts, kp = task - slot * npts;
+                const int slot = fd_np.div(task), kp = task - slot * npts;
                 const int code = LD(a.tile_fine, f0 + q0 + kp, a.fine_n);
                 const int gx = ox + (code & 255), gy = oy + ((code >> 8) & 255), gz = oz + (code >> 16);
                 const bool isA = slot < w.na;
@@ -751,53 +858,25 @@ __global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
         }
         __syncthreads();
         // 4 x 4 pairs per thread over this chunk (rows ti + 16u of A, tj + 16v of B);
-        // FP32 panels: per-chunk partial sums (<= 64 terms) in FP32, then FP64
-        if constexpr (sizeof(T) == 8) {
-            for (int k = 0; k < kcount; ++k) {
-                T va[4], vb[4], vq[4];
+        // only the 16-row groups holding functions (u < UA, v < UB, block-uniform)
+        for (int k = 0; k < kcount; ++k) {
+            T va[4], vb[4], vq[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    va[u] = LD(PA, (ti + 16 * u) * HS_LD + k, PN);
+            for (int u = 0; u < 4; ++u) {
+                if (u < UA) va[u] = LD(PA, (ti + 16 * u) * HS_LD + k, PN);
+                if (u < UB) {
                     vb[u] = LD(PB, (tj + 16 * u) * HS_LD + k, PN - HS_BLK * HS_LD);
                     vq[u] = LD(PQ, (tj + 16 * u) * HS_LD + k, PN - 2 * HS_BLK * HS_LD);
                 }
+            }
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
+                for (int v = 0; v < 4; ++v)
+                    if (u < UA && v < UB) {
                         sacc[u][v] += va[u] * vb[v];
                         hacc[u][v] += va[u] * vq[v];
                     }
-            }
-        } else {
-            T ps[4][4], ph[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) ps[u][v] = 0, ph[u][v] = 0;
-            for (int k = 0; k < kcount; ++k) {
-                T va[4], vb[4], vq[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    va[u] = LD(PA, (ti + 16 * u) * HS_LD + k, PN);
-                    vb[u] = LD(PB, (tj + 16 * u) * HS_LD + k, PN - HS_BLK * HS_LD);
-                    vq[u] = LD(PQ, (tj + 16 * u) * HS_LD + k, PN - 2 * HS_BLK * HS_LD);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        ps[u][v] += va[u] * vb[v];
-                        ph[u][v] += va[u] * vq[v];
-                    }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    sacc[u][v] += static_cast<double>(ps[u][v]);
-                    hacc[u][v] += static_cast<double>(ph[u][v]);
-                }
         }
         __syncthreads();
     }
@@ -826,10 +905,74 @@ __global__ void __launch_bounds__(256, 1) k_hs(HSLaunch a) {
                     hi = mid - 1;
             }
             if (pos < 0) continue;
-            if (hacc[u][v] != 0.0) atomicAdd(a.H + pos, hacc[u][v]);
-            if (sacc[u][v] != 0.0) atomicAdd(a.S + pos, sacc[u][v]);
+            if (hacc[u][v] != T(0)) atomicAdd(a.H + pos, static_cast<double>(hacc[u][v]));
+            if (sacc[u][v] != T(0)) atomicAdd(a.S + pos, static_cast<double>(sacc[u][v]));
         }
     }
+}
+
+// ---------------------------------------------------------------- reformat
+
+// Reuse of support functions on a shifted geometry: warp per destination segment of
+// L_dst(f); each member point p takes the source value at p - shift(atom) if that point
+// is a member of L_src(f) (coarse part for s, fine part for d^1..d^7), else 0.
+template <class T>
+__global__ void k_reformat(ReformatLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 10;
+    const FnRec r = a.fn[blockIdx.y];
+    const AtomRec& ad = a.atoms_dst[r.atom];
+    const AtomRec& as = a.atoms_src[r.atom];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sidx = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nseg = ad.nsegLc + ad.nsegLf;
+    if (sidx >= nseg) return;
+    const bool fine = sidx >= ad.nsegLc;
+    const Seg sg = LD(a.seg_dst, fine ? ad.segLf + (sidx - ad.nsegLc) : ad.segLc + sidx, a.seg_dst_n);
+    const int sx = a.shift[3 * r.atom], sy = a.shift[3 * r.atom + 1], sz = a.shift[3 * r.atom + 2];
+    // destination row -> global (y, z)
+    const int yl = sg.row % ad.n[1], zl = sg.row / ad.n[1];
+    const int gy = ad.lo[1] + yl - sy, gz = ad.lo[2] + zl - sz;     // source row
+    const int ys = gy - as.lo[1], zs = gz - as.lo[2];
+    const bool row_in = ys >= 0 && zs >= 0 && ys < as.n[1] && zs < as.n[2];
+    int s0 = 0, s1 = 0;
+    if (row_in) {
+        const int64_t rrow = (fine ? as.rowLf : as.rowLc) + ys + static_cast<int64_t>(as.n[1]) * zs;
+        s0 = LD(a.rowptr_src, rrow, a.rowptr_src_n);
+        s1 = LD(a.rowptr_src, rrow + 1, a.rowptr_src_n);
+    }
+    const T* src = static_cast<const T*>(a.phi_src) + LD(a.off_src, r.f, a.nfn + 1);
+    T* dst = static_cast<T*>(a.phi_dst) + r.off_phi;
+    const int64_t src_room = a.src_n - LD(a.off_src, r.f, a.nfn + 1);
+    const int64_t dst_room = a.dst_n - r.off_phi;
+    const int64_t seg0 = fine ? as.segLf : as.segLc;
+    const int len = sg.x1 - sg.x0 + 1;
+    for (int k = lane; k < len; k += 32) {
+        const int xs = ad.lo[0] + sg.x0 + k - sx - as.lo[0];          // source box-local x
+        int64_t off = -1;
+        for (int q = s0; q < s1; ++q) {
+            const Seg ss = LD(a.seg_src, seg0 + q, a.seg_src_n);
+            if (xs >= ss.x0 && xs <= ss.x1) off = ss.off + (xs - ss.x0);
+        }
+        if (!fine) {
+            ST(dst, sg.off + k, dst_room, off >= 0 ? LD(src, off, src_room) : T(0));
+        } else {
+#pragma unroll
+            for (int t = 0; t < 7; ++t)
+                ST(dst, ad.ncL + static_cast<int64_t>(t) * ad.nfL + sg.off + k, dst_room,
+                   off >= 0 ? LD(src, as.ncL + static_cast<int64_t>(t) * as.nfL + off, src_room) : T(0));
+        }
+    }
+}
+
+cudaError_t enqueue_reformat(const ReformatLaunch& a, cudaStream_t s) {
+    if (a.nfn == 0) return cudaSuccess;
+    const dim3 grid((a.max_seg + 7) / 8, a.nfn);
+    if (a.prec == 0)
+        k_reformat<double><<<grid, 256, 0, s>>>(a);
+    else
+        k_reformat<float><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- fixed device scratch
@@ -874,11 +1017,16 @@ cudaError_t upload_filters(const FilterSet& fs, int device) {
 }
 
 cudaError_t configure_kernels(size_t max_smem) {
+    // dynamic shared memory may use what the kernel's static shared memory leaves
     cudaError_t e;
-    const int m = static_cast<int>(max_smem);
-#define SETMAX(K)                                                                             \
-    if ((e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, m)) != cudaSuccess) \
-        return e;
+#define SETMAX(K)                                                                               \
+    {                                                                                           \
+        cudaFuncAttributes fa;                                                                  \
+        if ((e = cudaFuncGetAttributes(&fa, K)) != cudaSuccess) return e;                       \
+        const int m = static_cast<int>(max_smem - fa.sharedSizeBytes);                          \
+        if ((e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, m)) != cudaSuccess) \
+            return e;                                                                           \
+    }
     SETMAX(k_fwd_xy<double>) SETMAX(k_fwd_xy<float>)
     SETMAX(k_z<double>) SETMAX(k_z<float>)
     SETMAX(k_bwd_xy<double>) SETMAX(k_bwd_xy<float>)
@@ -905,7 +1053,7 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
     TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
     TRACED(a.tr, TK_KINETIC, s,
-           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf), 128, 0, s>>>(a)));
+           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf, 4), 128, 0, s>>>(a)));
     TRACED(a.tr, TK_COMPRESS, s, (k_compress<T><<<dim3((a.max_segP + 7) / 8, nf), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }

@@ -257,6 +257,39 @@ def potential_block(wl: Workload, lo, shape, xp=np, device=None):
     return V
 
 
+def potential_fast(wl: Workload, device, chunk=64):
+    """The same V as ``potential`` (up to the order of the additions), built on a torch
+    device with one scatter-add per chunk of wells instead of one per well."""
+    import torch
+    lo = np.asarray(wl.V_lo, np.int64)
+    shape = np.asarray(wl.V_shape, np.int64)
+    V = torch.zeros(int(np.prod(shape)), dtype=torch.float64, device=device)
+    h2 = wl.h / 2.0
+    wells = np.asarray(wl.wells, np.float64)
+    wmax = float(wells[:, 4].max()) if len(wells) else 1.0
+    W = int(math.ceil(2 * 6.0 * wmax / h2)) + 3               # padded block edge (fine points)
+    ar = torch.arange(W, device=device, dtype=torch.int64)
+    for c0 in range(0, len(wells), chunk):
+        wc = torch.as_tensor(wells[c0:c0 + chunk], device=device)
+        n = wc.shape[0]
+        cut = 6.0 * wc[:, 4]
+        E, I0 = [], []
+        for d in range(3):
+            j0 = torch.clamp(torch.floor((wc[:, d] - cut) / h2).to(torch.int64), min=int(lo[d]))
+            j1 = torch.clamp(torch.ceil((wc[:, d] + cut) / h2).to(torch.int64), max=int(lo[d] + shape[d] - 1))
+            j = j0[:, None] + ar[None, :]                      # (n, W) fine indices
+            ok = j <= j1[:, None]
+            x = j.to(torch.float64) * h2
+            e = torch.exp(-((x - wc[:, d:d + 1]) ** 2) / (2.0 * wc[:, 4:5] ** 2))
+            E.append(torch.where(ok, e, torch.zeros_like(e)))
+            I0.append(torch.clamp(j - int(lo[d]), 0, int(shape[d] - 1)))
+        blk = (-wc[:, 3])[:, None, None, None] * E[2][:, :, None, None] * E[1][:, None, :, None] \
+            * E[0][:, None, None, :]
+        idx = (I0[2][:, :, None, None] * shape[1] + I0[1][:, None, :, None]) * shape[0] + I0[0][:, None, None, :]
+        V.index_add_(0, idx.reshape(-1), blk.reshape(-1))
+    return V.reshape(int(shape[2]), int(shape[1]), int(shape[0]))
+
+
 def potential(wl: Workload, xp=np, device=None):
     """V on the whole fine grid the method can touch, array [z, y, x] from index -14."""
     return potential_block(wl, wl.V_lo, wl.V_shape, xp, device)

@@ -65,11 +65,13 @@ _SIGS = {
     "lsw_apply_hamiltonian": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_build_matrices": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_apply_hamiltonian_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lsw_reformat": (C.c_int, [_P, _P, _I32P, _P, _P]),
     "lsw_workspace_bytes": (C.c_int, [_P, _I64P]),
     "lsw_sync": (C.c_int, [_P, C.c_double]),
     "lsw_step_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "lsw_set_option": (C.c_int, [_P, C.c_char_p, C.c_int64]),
     "lsw_profile": (C.c_int, [_P, C.c_int32]),
+    "lsw_system_set_stream": (C.c_int, [_P, _P]),
     "lsw_profile_read": (C.c_int, [_P, C.c_int32, _I32P, _DP, _I64P]),
 }
 
@@ -190,6 +192,12 @@ def lsw_build_matrices(sys, phi, hphi, H, S):
     check(lib().lsw_build_matrices(sys, _ptr(phi), _ptr(hphi), _ptr(H), _ptr(S)))
 
 
+def lsw_reformat(dst, src, shift, phi_src, phi_dst):
+    """Move compressed support functions onto shifted atoms (shift: [n_atoms, 3] ints)."""
+    sh = np.ascontiguousarray(np.asarray(shift, dtype=np.int32).reshape(-1))
+    check(lib().lsw_reformat(dst, src, sh.ctypes.data_as(_I32P), _ptr(phi_src), _ptr(phi_dst)))
+
+
 def lsw_workspace_bytes(sys):
     b = C.c_int64()
     check(lib().lsw_workspace_bytes(sys, C.byref(b)))
@@ -207,6 +215,10 @@ def lsw_step_host(sys, phi_host, hphi_host, H_host, S_host, e_kin_host=None, e_p
 
 def lsw_set_option(sys, name, value):
     check(lib().lsw_set_option(sys, name.encode(), int(value)))
+
+
+def lsw_system_set_stream(sys, stream):
+    check(lib().lsw_system_set_stream(sys, stream))
 
 
 def lsw_profile(sys, enable):
