@@ -260,7 +260,7 @@ class ClockSampler:
 
 def kernel_work(S, wl, prec):
     """Algorithmic FLOPs per kernel kind for one full step: the in-range taps of each
-    separable filter (zero padding and out-of-box taps are not counted; see DESIGN.md),
+    separable filter (zero padding and out-of-box taps are not counted),
     and the compulsory bytes of a step (phi in, H phi out, H and S values out)."""
     es = 8 if prec == "fp64" else 4
     fl = {"fwd_xy": 0.0, "z_stage": 0.0, "bwd_xy": 0.0, "kinetic": 0.0}
@@ -446,7 +446,8 @@ def gpu_main(args):
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak,
                     "traffic": stored_traffic(dom, wl.name, prec, (tune or {}).get("chosen", {}).get("batch")),
-                    "peak_source": "derived: %s CUDA-core FMA rate (see DESIGN.md)" % prec}
+                    "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec == "fp32"
+                                    else "nominal GB300 FP64 rate (1.25 TFLOP/s)")}
         else:
             roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
                     "frac": None, "traffic": None}

@@ -52,7 +52,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", ARCH, "-lineinfo",
-               "-Xcompiler", host_flags, "--fmad=true", "-diag-suppress=177"] + inc + (["-DLSW_CHECKED"] if CHECKED else [])
+               "-Xcompiler", host_flags, "--fmad=true", "-diag-suppress=177"] + inc + (["-DLSW_CHECKED"] if CHECKED else []) \
+            + os.environ.get("LSW_NVCC_DEFINES", "").split()
         if src.endswith(".cpp"):
             cmd = [nvcc, "-x", "c++", "-c", src, "-o", obj, "-std=c++17", "-Xcompiler", host_flags] + inc
         if verbose:

@@ -396,7 +396,7 @@ void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, siz
 
 lsw_status build_plans(lsw_system_s* s) {
     const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
-    const int zcols = s->prec == LSW_FP64 ? 64 : 128;
+    const int zcols = s->prec == LSW_FP64 ? ZCOLS_F64 : ZCOLS_F32;
     std::vector<FnRec> recs(nf);
     for (int64_t f = 0; f < nf; ++f) {
         FnRec& r = recs[f];
@@ -1040,7 +1040,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
     CUDA_TRY(noalloc_scratch(sys->ctx->device, &scratch));
     const size_t head = (NOALLOC_MAX_BATCH * sizeof(FnRec) + 255) / 256 * 256;
     const int64_t cap = static_cast<int64_t>((NOALLOC_SCRATCH_BYTES - head) / sys->esize);
-    const int zcols = sys->prec == LSW_FP64 ? 64 : 128;
+    const int zcols = sys->prec == LSW_FP64 ? ZCOLS_F64 : ZCOLS_F32;
     cudaStream_t st = sys->stream;
     const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
     double* e0 = static_cast<double*>(sys->d_escratch.p);

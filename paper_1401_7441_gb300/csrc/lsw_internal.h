@@ -18,6 +18,8 @@ constexpr int FWD_LO = -14;      // combined filters (w * h), (w * g): m = -14..
 constexpr int FWD_TAPS = 31;
 constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [2lo-14, 2hi+16]
 constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
+constexpr int ZCOLS_F64 = 64;    // real-space columns per block of the z stage (FP64)
+constexpr int ZCOLS_F32 = 128;   // (FP32)
 constexpr size_t BWD_STATIC_SMEM = 12 * 1024;   // upper bound of k_bwd_xy's static shared memory
 
 // Filter tables, FP64 (rounded once from double-double).
@@ -62,7 +64,7 @@ struct HSWork {
 
 // Kernel kinds of the per-launch device trace (lsw_profile / lsw_profile_read).
 enum TraceKind : int {
-    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_COMPRESS, TK_HS, TK_COUNT
+    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_RESERVED, TK_HS, TK_COUNT
 };
 
 // Host-side recorder of CUDA event pairs around launches; NULL = no tracing.

@@ -8,11 +8,11 @@
 //   k_z           per (x', y') column: the same along z -> real-space u; v = V u
 //                 (E_pot += V u^2); then the transposed filters back to coarse z on
 //                 the L' box
+//   k_kin_z       per (x, y) column of L: kinetic arm along z (T = -1/(2h^2) sum_d
+//                 T_{b_d b'_d} along d, Galerkin blocks of the two-level basis) -> G
 //   k_bwd_xy      per coarse z plane of L': transposed filters along y then x, plus
-//                 the kinetic arms along x and y (T = -1/(2h^2) sum_d T_{b_d b'_d} along
-//                 d, Galerkin blocks of the two-level basis) -> G; E_kin partials
-//   k_kin_z       per (x'', y'') column: kinetic arm along z, G += ...; E_kin partials
-//   k_compress    G on the members of L' -> compressed H phi
+//                 the kinetic arms along x and y, plus G; written straight into the
+//                 compressed H phi on the members of L'; E_kin partials
 //   k_hs          per grid tile (App. D "transposed" layout): panels of phi and
 //                 H phi of the functions touching the tile; S_ab += <phi_a|phi_b>,
 //                 H_ab += <phi_a|H phi_b> over the tile; FP64 accumulation
@@ -92,6 +92,26 @@ __device__ __forceinline__ void st_chk(T* p, int64_t i, int64_t n, V v, int* st,
 #define FWD(b, m) (((m) >= 0 && (m) < FWD_TAPS) ? Tab<T>::fwd(b, m) : (lsw_report(ST_, KID, __LINE__, (m), FWD_TAPS), T(0)))
 #endif
 
+// Element copy global -> shared without a register round trip (cp.async, 4 or 8 bytes):
+// a staging loop issues all its copies back to back, so every load of a plane is in
+// flight at once; cp_wait() completes this thread's copies (a barrier then publishes
+// them to the block).  The checked build copies through the bounds-checked accessors.
+#ifdef LSW_CHECKED
+#define CPA(dst, di, dn, src, si, sn) ST(dst, di, dn, LD(src, si, sn))
+#else
+#define CPA(dst, di, dn, src, si, sn) cp_async(&(dst)[di], &(src)[si])
+#endif
+template <class T>
+__device__ __forceinline__ void cp_async(T* dst, const T* src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element of 4 or 8 bytes");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- uncompress / compress
 
 template <class T>
@@ -128,40 +148,6 @@ __global__ void k_uncompress(HphiLaunch a) {
     }
 }
 
-template <class T>
-__global__ void k_compress(HphiLaunch a) {
-    [[maybe_unused]] int* ST_ = a.status;
-    [[maybe_unused]] constexpr int KID = 6;
-    const FnRec r = a.fn[blockIdx.y];
-    const AtomRec& at = a.atoms[r.atom];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sidx = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int nseg = at.nsegPc + at.nsegPf;
-    if (sidx >= nseg) return;
-    const bool fine = sidx >= at.nsegPc;
-    const Seg sg = LD(a.seg, fine ? at.segPf + (sidx - at.nsegPc) : at.segPc + sidx, a.seg_n);
-    const int64_t plane = static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2];
-    const T* G = static_cast<const T*>(a.ws) + r.ws_G;
-    T* out = static_cast<T*>(a.hphi) + r.off_hphi;
-    const int64_t out_room = a.hphi_n - r.off_hphi;
-    const int len = sg.x1 - sg.x0 + 1;
-    if (sg.x0 < 0 || sg.x1 >= r.np[0] || sg.row < 0 || sg.row >= r.np[1] * r.np[2]) {
-        if (lane == 0) atomicOr(a.status, ST_BAD_SEG);
-        return;
-    }
-    const int64_t base = static_cast<int64_t>(sg.row) * r.np[0] + sg.x0;
-    for (int k = lane; k < len; k += 32) {
-        if (!fine) {
-            ST(out, sg.off + k, out_room, LD(G, base + k, 8 * plane));
-        } else {
-#pragma unroll
-            for (int t = 1; t < 8; ++t)
-                ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + sg.off + k, out_room,
-                   LD(G, t * plane + base + k, 8 * plane));
-        }
-    }
-}
-
 // Division by a loop-invariant divisor d (1 <= d < 2^16) for dividends n < 2^16:
 // q = umulhi(n, ceil(2^32 / d)) is exact there (the error term n / 2^32 < 2^-16 cannot
 // reach the next integer).  Replaces the ~20-instruction integer division in index math.
@@ -182,9 +168,63 @@ struct FastDiv {
 // values per type) held in registers; taps are compile-time immediates.
 constexpr int FB = 4;                 // coarse steps per forward block (8 outputs)
 constexpr int FW = FB + 15;           // forward window
-constexpr int BB = 4;                 // outputs per backward / kinetic block
-constexpr int BW = 2 * BB + 29;       // backward window (fine points)
+constexpr int BB = 4;                 // outputs per kinetic block
 constexpr int KW = BB + 2 * KIN_HALF; // kinetic window
+#ifndef LSW_Z_NB
+#define LSW_Z_NB 4                    // outputs per backward block in the z stage (FP32)
+#endif
+#ifndef LSW_BWD_NB
+#define LSW_BWD_NB 8                  // outputs per backward block in the plane kernel (FP32)
+#endif
+template <class T, int Stage>         // Stage 0: z stage, 1: backward plane kernel
+struct Blk {                          // outputs per backward (decimating) block
+    static constexpr int NB = sizeof(T) == 4 ? (Stage == 0 ? LSW_Z_NB : LSW_BWD_NB) : 4;
+    static constexpr int W = 2 * NB + 29;
+};
+template <class T>
+struct ZCols { static constexpr int C = sizeof(T) == 8 ? ZCOLS_F64 : ZCOLS_F32; };
+
+// Window w[i] = p[off + (first + i) * stride] for positions first + i in [0, n), 0 outside.
+// When the whole window is inside (the common, warp-uniform case) the loads carry no
+// bounds test.
+#ifdef LSW_CHECKED
+#define WLD(p, i, room) ld_chk(p, static_cast<int64_t>(i), static_cast<int64_t>(room), st, 11, __LINE__)
+#else
+#define WLD(p, i, room) ((p)[i])
+#endif
+template <int N, class T>
+__device__ __forceinline__ void win(T (&w)[N], const T* p, int64_t off, int stride, int first, int n,
+                                    [[maybe_unused]] int64_t room, [[maybe_unused]] int* st) {
+    if (first >= 0 && first + N <= n) {
+        const T* q = p + off + static_cast<int64_t>(first) * stride;
+#pragma unroll
+        for (int i = 0; i < N; ++i) w[i] = WLD(q, static_cast<int64_t>(i) * stride, room - off - static_cast<int64_t>(first) * stride);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int pos = first + i;
+            w[i] = (pos >= 0 && pos < n) ? WLD(p, off + static_cast<int64_t>(pos) * stride, room) : T(0);
+        }
+    }
+}
+
+// The same for a window in shared memory, with 32-bit offsets (shared addresses are
+// 32-bit; keeping the index math in int lets loads fold their offsets).
+template <int N, class T>
+__device__ __forceinline__ void swin(T (&w)[N], const T* p, int off, int stride, int first, int n,
+                                     [[maybe_unused]] int64_t room, [[maybe_unused]] int* st) {
+    if (first >= 0 && first + N <= n) {
+        const int b = off + first * stride;
+#pragma unroll
+        for (int i = 0; i < N; ++i) w[i] = WLD(p, b + i * stride, room);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int pos = first + i;
+            w[i] = (pos >= 0 && pos < n) ? WLD(p, off + pos * stride, room) : T(0);
+        }
+    }
+}
 
 template <class T>
 __device__ __forceinline__ void fwd_block(const T (&w0)[FW], const T (&w1)[FW], T (&u)[2 * FB]) {
@@ -206,11 +246,11 @@ __device__ __forceinline__ void fwd_block(const T (&w0)[FW], const T (&w1)[FW], 
 }
 
 // Backward (transposed filters, decimation by 2): s_j = sum_m F_0[m] v[2j+m],
-// d_j = sum_m F_1[m] v[2j+m], m = 0..30, from the window v[0 .. 2*BB+28].
-template <class T>
-__device__ __forceinline__ void bwd_block(const T (&w)[BW], T (&s)[BB], T (&d)[BB]) {
+// d_j = sum_m F_1[m] v[2j+m], m = 0..30, from the window v[0 .. 2*NB+28].
+template <class T, int NB>
+__device__ __forceinline__ void bwd_block(const T (&w)[2 * NB + 29], T (&s)[NB], T (&d)[NB]) {
 #pragma unroll
-    for (int j = 0; j < BB; ++j) {
+    for (int j = 0; j < NB; ++j) {
         T a0 = 0, a1 = 0;
 #pragma unroll
         for (int m = 0; m < FWD_TAPS; ++m) {
@@ -247,6 +287,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 2;
+    int* st = a.status;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[blockIdx.y];
@@ -262,34 +303,35 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
     const T* D = static_cast<const T*>(a.ws) + r.ws_D;
     const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
     const int pn = nx * ny;
-    const FastDiv fd_pn(pn), fd_nx(nx), fd_ny(ny), fd_2ny(2 * ny), fd_X(X);
-    for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
-        const int tb = fd_pn.div(i), rem = i - tb * pn;
-        const int y = fd_nx.div(rem), x = rem - y * nx;
-        ST(in, (tb * ny + y) * RS + x, smem_n,
-           LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(z) * pn + rem, 8 * plane));
+    {
+        const FastDiv fd_pn(pn), fd_nx(nx);
+        for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
+            const int tb = fd_pn.div(i), rem = i - tb * pn;
+            const int y = fd_nx.div(rem), x = rem - y * nx;
+            CPA(in, (tb * ny + y) * RS + x, smem_n, D, (tb + 4 * bz) * plane + static_cast<int64_t>(z) * pn + rem,
+                8 * plane);
+        }
     }
+    cp_wait();
     __syncthreads();
     // x pass: rows (by, y), blocks of 8 outputs along x'
     const int nbx = (nx + 15 + FB - 1) / FB;
-    for (int task = threadIdx.x; task < 2 * ny * nbx; task += blockDim.x) {
-        const int blk = fd_2ny.div(task), row = task - blk * 2 * ny;
-        const int by = fd_ny.div(row), y = row - by * ny;
-        const int p0 = blk * FB;
-        const int s0 = ((2 * by) * ny + y) * RS, d0 = s0 + ny * RS;
-        T w0[FW], w1[FW], u[2 * FB];
+    {
+        const FastDiv fd_2ny(2 * ny), fd_ny(ny);
+        for (int task = threadIdx.x; task < 2 * ny * nbx; task += blockDim.x) {
+            const int blk = fd_2ny.div(task), row = task - blk * 2 * ny;
+            const int by = fd_ny.div(row), y = row - by * ny;
+            const int p0 = blk * FB;
+            const int s0 = ((2 * by) * ny + y) * RS, d0 = s0 + ny * RS;
+            T w0[FW], w1[FW], u[2 * FB];
+            swin(w0, in, s0, 1, p0 - 15, nx, smem_n, st);
+            swin(w1, in, d0, 1, p0 - 15, nx, smem_n, st);
+            fwd_block(w0, w1, u);
 #pragma unroll
-        for (int i = 0; i < FW; ++i) {
-            const int q = p0 - 15 + i;
-            const bool ok = q >= 0 && q < nx;
-            w0[i] = ok ? LD(in, s0 + q, smem_n) : T(0);
-            w1[i] = ok ? LD(in, d0 + q, smem_n) : T(0);
-        }
-        fwd_block(w0, w1, u);
-#pragma unroll
-        for (int k = 0; k < 2 * FB; ++k) {
-            const int xo = 2 * p0 + k;
-            if (xo < X) ST(mid, row * X + xo, mid_n, u[k]);
+            for (int k = 0; k < 2 * FB; ++k) {
+                const int xo = 2 * p0 + k;
+                if (xo < X) ST(mid, row * X + xo, mid_n, u[k]);
+            }
         }
     }
     __syncthreads();
@@ -297,17 +339,13 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
     T* Bf = static_cast<T*>(a.ws) + r.ws_Bf + (static_cast<int64_t>(bz) * nz + z) * Y * X;
     const int64_t bf_room = 2LL * nz * Y * X - (static_cast<int64_t>(bz) * nz + z) * Y * X;
     const int nby = (ny + 15 + FB - 1) / FB;
+    const FastDiv fd_X(X);
     for (int task = threadIdx.x; task < X * nby; task += blockDim.x) {
         const int blk = fd_X.div(task), xo = task - blk * X;
         const int p0 = blk * FB;
         T w0[FW], w1[FW], u[2 * FB];
-#pragma unroll
-        for (int i = 0; i < FW; ++i) {
-            const int q = p0 - 15 + i;
-            const bool ok = q >= 0 && q < ny;
-            w0[i] = ok ? LD(mid, q * X + xo, mid_n) : T(0);
-            w1[i] = ok ? LD(mid, (ny + q) * X + xo, mid_n) : T(0);
-        }
+        swin(w0, mid, xo, X, p0 - 15, ny, mid_n, st);
+        swin(w1, mid, ny * X + xo, X, p0 - 15, ny, mid_n, st);
         fwd_block(w0, w1, u);
 #pragma unroll
         for (int k = 0; k < 2 * FB; ++k) {
@@ -320,29 +358,32 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
 // ---------------------------------------------------------------- z stage with V
 
 template <class T>
-__global__ void k_z(HphiLaunch a) {
+__global__ void __launch_bounds__(ZCols<T>::C) k_z(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 3;
+    constexpr int NB = Blk<T, 0>::NB;
+    constexpr int W = Blk<T, 0>::W;
+    constexpr int C = ZCols<T>::C;       // columns per block = threads; a compile-time
+                                         // stride turns window offsets into immediates
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[blockIdx.y];
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int X = 2 * nx + 29, Y = 2 * ny + 29, Z = 2 * nz + 29;
     const int cols = X * Y;
-    const int C = a.zcols;
     const int c = blockIdx.x * C + threadIdx.x;
     if (blockIdx.x * C >= cols) return;
     const bool valid = c < cols;
     const int t = threadIdx.x;
     T* cin = sm;                  // [2][nz][C]  (each thread owns its column)
     T* vs = sm + 2 * nz * C;      // [Z][C]
-    const int64_t smem_n = static_cast<int64_t>(a.smem_z / sizeof(T));
-    const int64_t vs_n = smem_n - 2 * nz * C;
+    [[maybe_unused]] const int64_t smem_n = static_cast<int64_t>(a.smem_z / sizeof(T));
+    [[maybe_unused]] const int64_t vs_n = smem_n - 2 * nz * C;
     const T* Bf = static_cast<const T*>(a.ws) + r.ws_Bf;
-    for (int q = 0; q < 2 * nz; ++q)
-        ST(cin, q * C + t, smem_n, valid ? LD(Bf, static_cast<int64_t>(q) * cols + c, 2LL * nz * cols) : T(0));
     T epot_t = 0;   // per-thread partial in the kernel's precision (no FP64 in FP32 loops)
     if (valid) {
+        // Stage the column's input and its slice of V first: all loads independent and
+        // in flight together (the multiply below then reads V from shared memory).
         const int xo = c % X, yo = c / X;
         const int64_t jx = 2LL * r.lo[0] - V_REACH + xo - a.vlo[0];
         const int64_t jy = 2LL * r.lo[1] - V_REACH + yo - a.vlo[1];
@@ -350,21 +391,35 @@ __global__ void k_z(HphiLaunch a) {
         const T* V = static_cast<const T*>(a.V);
         const int64_t vrow = jy * a.vn[0] + jx;
         const int64_t vstride = a.vn[0] * a.vn[1];
+        for (int q = 0; q < 2 * nz; ++q)
+            CPA(cin, q * C + t, smem_n, Bf, static_cast<int64_t>(q) * cols + c, 2LL * nz * cols);
+        for (int zo = 0; zo < Z; ++zo)
+            CPA(vs, zo * C + t, vs_n, V, (jz0 + zo) * vstride + vrow, a.v_n);
+        cp_wait();   // each thread reads only its own column: no barrier needed
         for (int p0 = 0; 2 * p0 < Z; p0 += FB) {
             T w0[FW], w1[FW], u[2 * FB];
+            const int q0 = p0 - 15;
+            if (q0 >= 0 && q0 + FW <= nz) {
 #pragma unroll
-            for (int i = 0; i < FW; ++i) {
-                const int q = p0 - 15 + i;
-                const bool ok = q >= 0 && q < nz;
-                w0[i] = ok ? LD(cin, q * C + t, smem_n) : T(0);
-                w1[i] = ok ? LD(cin, (nz + q) * C + t, smem_n) : T(0);
+                for (int i = 0; i < FW; ++i) {
+                    w0[i] = LD(cin, (q0 + i) * C + t, smem_n);
+                    w1[i] = LD(cin, (nz + q0 + i) * C + t, smem_n);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < FW; ++i) {
+                    const int q = q0 + i;
+                    const bool ok = q >= 0 && q < nz;
+                    w0[i] = ok ? LD(cin, q * C + t, smem_n) : T(0);
+                    w1[i] = ok ? LD(cin, (nz + q) * C + t, smem_n) : T(0);
+                }
             }
             fwd_block(w0, w1, u);
 #pragma unroll
             for (int k = 0; k < 2 * FB; ++k) {
                 const int zo = 2 * p0 + k;
                 if (zo < Z) {
-                    const T vv = LD(V, (jz0 + zo) * vstride + vrow, a.v_n);
+                    const T vv = LD(vs, zo * C + t, vs_n);
                     const T v = vv * u[k];
                     epot_t += v * u[k];
                     ST(vs, zo * C + t, vs_n, v);
@@ -374,17 +429,22 @@ __global__ void k_z(HphiLaunch a) {
         const int nzp = r.np[2];
         const int dz = r.lop[2] - r.lo[2];
         T* Bb = static_cast<T*>(a.ws) + r.ws_Bb;
-        for (int b0 = 0; b0 < nzp; b0 += BB) {
-            const int base = 2 * (b0 + dz);
-            T w[BW], s[BB], d[BB];
+        for (int b0 = 0; b0 < nzp; b0 += NB) {
+            T w[W], s[NB], d[NB];
+            const int z0 = 2 * (b0 + dz);
+            if (z0 >= 0 && z0 + W <= Z) {
 #pragma unroll
-            for (int i = 0; i < BW; ++i) {
-                const int zo = base + i;
-                w[i] = (zo >= 0 && zo < Z) ? LD(vs, zo * C + t, vs_n) : T(0);
+                for (int i = 0; i < W; ++i) w[i] = LD(vs, (z0 + i) * C + t, vs_n);
+            } else {
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    const int zo = z0 + i;
+                    w[i] = (zo >= 0 && zo < Z) ? LD(vs, zo * C + t, vs_n) : T(0);
+                }
             }
-            bwd_block(w, s, d);
+            bwd_block<T, NB>(w, s, d);
 #pragma unroll
-            for (int j = 0; j < BB; ++j) {
+            for (int j = 0; j < NB; ++j) {
                 const int b = b0 + j;
                 if (b < nzp) {
                     ST(Bb, static_cast<int64_t>(b) * cols + c, 2LL * nzp * cols, s[j]);
@@ -397,23 +457,83 @@ __global__ void k_z(HphiLaunch a) {
     if ((threadIdx.x & 31) == 0 && epot != 0.0) atomicAdd(a.e_pot + r.f, epot);
 }
 
-// ---------------------------------------------------------------- backward y, x + kinetic x, y
+// ---------------------------------------------------------------- kinetic z arm
+
+// Per (x, y) column of the L box and type pair (t, t + 4): the kinetic arm along z,
+// written to G on the L' box column (G holds only this arm; the backward plane kernel
+// adds the rest).  Runs before the backward plane kernel.
+template <class T>
+__global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 5;
+    int* st = a.status;
+    const FnRec r = a.fn[blockIdx.y];
+    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
+    const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
+    const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;   // column (x, y) of the L box
+    const int tb = blockIdx.z;                             // type pair (tb, tb + 4)
+    T ekin_t = 0;
+    if (c < nx * ny) {
+        const int y = c / nx, x = c - y * nx;
+        const int xb = x - dx, yb = y - dy;             // the same column in the L' box
+        if (xb >= 0 && xb < nxp && yb >= 0 && yb < nyp) {
+            const T* D = static_cast<const T*>(a.ws) + r.ws_D;
+            T* G = static_cast<T*>(a.ws) + r.ws_G;
+            const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
+            const int pn = nx * ny;
+            const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
+            const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
+            const int64_t gcol = static_cast<int64_t>(yb) * nxp + xb;
+            const T ks = static_cast<T>(a.kin_scale);
+            for (int b0 = 0; b0 < nzp; b0 += BB) {
+                T k0[KW], k1[KW], o0[BB], o1[BB];
+                win(k0, D, tb * plane + c, pn, b0 + dz - KIN_HALF, nz, 8 * plane, st);
+                win(k1, D, (tb + 4) * plane + c, pn, b0 + dz - KIN_HALF, nz, 8 * plane, st);
+                kin_block(k0, k1, o0, o1);
+#pragma unroll
+                for (int j = 0; j < BB; ++j) {
+                    const int b = b0 + j;
+                    if (b < nzp) {
+                        o0[j] *= ks;
+                        o1[j] *= ks;
+                        ST(G, tb * gplane + b * pnp + gcol, 8 * gplane, o0[j]);
+                        ST(G, (tb + 4) * gplane + b * pnp + gcol, 8 * gplane, o1[j]);
+                        const int zz = b + dz;
+                        if (zz >= 0 && zz < nz) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
+                    }
+                }
+            }
+        }
+    }
+    const double ekin = warp_sum(static_cast<double>(ekin_t));
+    if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
+}
+
+// ---------------------------------------------------------------- backward y, x + kinetic x, y + compress
 
 // Per plane (z'', bz) of the L' box: transposed filters along y then x (potential part)
-// plus the kinetic arms along x and y of the four output types with z bit bz.  Only
-// what the compress step reads is computed: rows of the plane holding members of L'
-// and, in each row, the x range of its member segment (L' is a sphere clipped by the
-// box, so one segment per row); kinetic type pairs whose input rows or columns of D
-// are all zero (wavelet types off the fine region) are skipped.  Each phase first
-// lists its tasks in shared memory, so skipped work frees whole rounds.
+// plus the kinetic arms along x and y of the four output types with z bit bz, plus the
+// z arm that k_kin_z left in G; the sum is written straight into the compressed H phi
+// on the members of L' in this plane.  Only member rows (and, per row, the x range of
+// its member segment: L' is a sphere clipped by the box) are computed; kinetic type
+// pairs whose input rows or columns of D are all zero (wavelet types off the fine
+// region) are skipped.  Each phase first lists its tasks in shared memory, so skipped
+// work frees whole rounds.
 constexpr int BWD_MAX_TASKS = 2048;
+#ifndef LSW_BWD_MIN_BLOCKS
+#define LSW_BWD_MIN_BLOCKS 2      // resident blocks per SM the FP32 version is compiled for
+#endif
 
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaunch a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) k_bwd_xy(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 4;
+    int* st = a.status;
+    constexpr int NB = Blk<T, 1>::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int16_t rx0[256], rx1[256];         // member x range per row (L' plane), -1: none
+    __shared__ int roff[256];                      // coefficient offset of the row's coarse segment
     __shared__ int task[BWD_MAX_TASKS];
     __shared__ int ntask, ylo, yhi, xlo, xhi;
     __shared__ unsigned char rowf[4][128], colf[4][128];   // D plane: nonzero per (type, row / column)
@@ -450,9 +570,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
     for (int y = threadIdx.x; y < nyp; y += blockDim.x) {
         const int64_t row = at.rowPc + y + static_cast<int64_t>(nyp) * zb;
         const int s0 = LD(a.rowptr, row, a.rowptr_n), s1 = LD(a.rowptr, row + 1, a.rowptr_n);
-        int lo = -1, hi = -1;
+        int lo = -1, hi = -1, off = 0;
         if (s1 > s0) {
-            lo = LD(a.seg, at.segPc + s0, a.seg_n).x0;
+            const Seg sg = LD(a.seg, at.segPc + s0, a.seg_n);
+            lo = sg.x0;
+            off = sg.off;
             hi = LD(a.seg, at.segPc + s1 - 1, a.seg_n).x1;
             atomicMin(&ylo, y);
             atomicMax(&yhi, y);
@@ -461,10 +583,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
         }
         rx0[y] = static_cast<int16_t>(lo);
         rx1[y] = static_cast<int16_t>(hi);
+        roff[y] = off;
     }
     const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
     const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
-    for (int i = threadIdx.x; i < Y * X; i += blockDim.x) ST(pl, i, smem_n, LD(Bb, i, bb_room));
+    for (int i = threadIdx.x; i < Y * X; i += blockDim.x) CPA(pl, i, smem_n, Bb, i, bb_room);
     const T* D = static_cast<const T*>(a.ws) + r.ws_D;
     const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
     const int pn = nx * ny;
@@ -474,9 +597,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
         for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
             const int tb = fd_pn.div(i), rem = i - tb * pn;
             const int y = fd_nx.div(rem), x = rem - y * nx;
-            const T v = LD(D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem, 8 * plane);
-            ST(Dp, (tb * ny + y) * RS + x, dp_n, v);
-            if (v != T(0)) {
+            CPA(Dp, (tb * ny + y) * RS + x, dp_n, D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem,
+                8 * plane);
+        }
+    }
+    cp_wait();
+    __syncthreads();
+    if (dplane) {   // zero flags of the staged D plane
+        const FastDiv fd_pn(pn), fd_nx(nx);
+        for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
+            const int tb = fd_pn.div(i), rem = i - tb * pn;
+            const int y = fd_nx.div(rem), x = rem - y * nx;
+            if (LD(Dp, (tb * ny + y) * RS + x, dp_n) != T(0)) {
                 rowf[tb][y & 127] = 1;
                 colf[tb][x & 127] = 1;
             }
@@ -490,22 +622,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
     T ekin_t = 0;
     const int ylo_ = ylo, yhi_ = yhi;
     if (yhi_ >= 0) {
-        // ---- y pass: columns x', blocks of BB rows b within [ylo, yhi]
-        const int nbb = (yhi_ - ylo_ + BB) / BB;
+        // ---- y pass: columns x', blocks of NB rows b within [ylo, yhi]
+        const int nbb = (yhi_ - ylo_ + NB) / NB;
         {
             const FastDiv fd_X(X);
             for (int tk = threadIdx.x; tk < X * nbb; tk += blockDim.x) {
-                const int q = fd_X.div(tk), xo = tk - q * X, b0 = ylo_ + q * BB;
-                const int base = 2 * (b0 + dy);
-                T w[BW], s[BB], d[BB];
+                const int q = fd_X.div(tk), xo = tk - q * X, b0 = ylo_ + q * NB;
+                T w[2 * NB + 29], s[NB], d[NB];
+                swin(w, pl, xo, X, 2 * (b0 + dy), Y, smem_n, st);
+                bwd_block<T, NB>(w, s, d);
 #pragma unroll
-                for (int i = 0; i < BW; ++i) {
-                    const int yo = base + i;
-                    w[i] = (yo >= 0 && yo < Y) ? LD(pl, yo * X + xo, smem_n) : T(0);
-                }
-                bwd_block(w, s, d);
-#pragma unroll
-                for (int j = 0; j < BB; ++j) {
+                for (int j = 0; j < NB; ++j) {
                     const int b = b0 + j;
                     if (b <= yhi_) {
                         ST(mid, static_cast<int64_t>(b) * X + xo, mid_n, s[j]);
@@ -515,10 +642,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
             }
         }
         __syncthreads();   // pl is dead from here on: Gs reuses it
-        // ---- task list: (by, row b, x block) intersecting the row's member range
+        // ---- task list: (by, row b, x block of NB) intersecting the row's member range
         for (int b = ylo_ + threadIdx.x; b <= yhi_; b += blockDim.x) {
             if (rx0[b] < 0) continue;
-            const int k0 = rx0[b] / BB, k1 = rx1[b] / BB;
+            const int k0 = rx0[b] / NB, k1 = rx1[b] / NB;
             for (int by = 0; by < 2; ++by) {
                 const int base = atomicAdd(&ntask, k1 - k0 + 1);
                 for (int k = k0; k <= k1; ++k)
@@ -526,23 +653,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
             }
         }
         __syncthreads();
-        const int nt_x = min(ntask, BWD_MAX_TASKS);
+        int nt = min(ntask, BWD_MAX_TASKS);
         if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
         // ---- x pass (transposed filters) on the listed row blocks
-        for (int it = threadIdx.x; it < nt_x; it += blockDim.x) {
+        for (int it = threadIdx.x; it < nt; it += blockDim.x) {
             const int code = task[it];
-            const int by = code >> 24, b = (code >> 12) & 4095, x0 = (code & 4095) * BB;
+            const int by = code >> 24, b = (code >> 12) & 4095, x0 = (code & 4095) * NB;
             const int row = by * nyp + b;
-            const int base = 2 * (x0 + dx);
-            T w[BW], s[BB], d[BB];
+            T w[2 * NB + 29], s[NB], d[NB];
+            swin(w, mid, row * X, 1, 2 * (x0 + dx), X, mid_n, st);
+            bwd_block<T, NB>(w, s, d);
 #pragma unroll
-            for (int i = 0; i < BW; ++i) {
-                const int xo = base + i;
-                w[i] = (xo >= 0 && xo < X) ? LD(mid, row * X + xo, mid_n) : T(0);
-            }
-            bwd_block(w, s, d);
-#pragma unroll
-            for (int j = 0; j < BB; ++j) {
+            for (int j = 0; j < NB; ++j) {
                 const int xb = x0 + j;
                 if (xb < nxp) {
                     ST(Gs, ((0 + 2 * by) * nyp + b) * nxp + xb, gs_n, s[j]);
@@ -552,22 +674,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
         }
         if (dplane) {
             __syncthreads();
-            // ---- kinetic x arm on the same row blocks, pair (bx = 0, 1) of each by
-            for (int it = threadIdx.x; it < nt_x; it += blockDim.x) {
+            if (threadIdx.x == 0) ntask = 0;
+            __syncthreads();
+            // ---- kinetic x arm: (by, row b, x block of BB) of member rows whose D rows are nonzero
+            for (int b = ylo_ + threadIdx.x; b <= yhi_; b += blockDim.x) {
+                const int y = b + dy;
+                if (rx0[b] < 0 || y < 0 || y >= ny) continue;
+                const int k0 = rx0[b] / BB, k1 = rx1[b] / BB;
+                for (int by = 0; by < 2; ++by) {
+                    if (!rowf[2 * by][y & 127] && !rowf[2 * by + 1][y & 127]) continue;
+                    const int base = atomicAdd(&ntask, k1 - k0 + 1);
+                    for (int k = k0; k <= k1; ++k)
+                        if (base + k - k0 < BWD_MAX_TASKS) task[base + k - k0] = (by << 24) | (b << 12) | k;
+                }
+            }
+            __syncthreads();
+            nt = min(ntask, BWD_MAX_TASKS);
+            if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
+            for (int it = threadIdx.x; it < nt; it += blockDim.x) {
                 const int code = task[it];
                 const int by = code >> 24, b = (code >> 12) & 4095, x0 = (code & 4095) * BB;
                 const int y = b + dy;
-                if (y < 0 || y >= ny) continue;
-                if (!rowf[2 * by][y & 127] && !rowf[2 * by + 1][y & 127]) continue;   // both inputs zero
                 T k0[KW], k1[KW], o0[BB], o1[BB];
                 const int r0 = ((2 * by) * ny + y) * RS, r1 = r0 + ny * RS;
-#pragma unroll
-                for (int i = 0; i < KW; ++i) {
-                    const int x = x0 + dx - KIN_HALF + i;
-                    const bool ok = x >= 0 && x < nx;
-                    k0[i] = ok ? LD(Dp, r0 + x, dp_n) : T(0);
-                    k1[i] = ok ? LD(Dp, r1 + x, dp_n) : T(0);
-                }
+                swin(k0, Dp, r0, 1, x0 + dx - KIN_HALF, nx, dp_n, st);
+                swin(k1, Dp, r1, 1, x0 + dx - KIN_HALF, nx, dp_n, st);
                 kin_block(k0, k1, o0, o1);
 #pragma unroll
                 for (int j = 0; j < BB; ++j) {
@@ -600,20 +731,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
                     if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | k;
             }
             __syncthreads();
-            const int nt_y = min(ntask, BWD_MAX_TASKS);
+            nt = min(ntask, BWD_MAX_TASKS);
             if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
-            for (int it = threadIdx.x; it < nt_y; it += blockDim.x) {
+            for (int it = threadIdx.x; it < nt; it += blockDim.x) {
                 const int code = task[it];
                 const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = ylo_ + (code & 4095) * BB;
                 const int x = xb + dx;
                 T k0[KW], k1[KW], o0[BB], o1[BB];
-#pragma unroll
-                for (int i = 0; i < KW; ++i) {
-                    const int y = b0 + dy - KIN_HALF + i;
-                    const bool ok = y >= 0 && y < ny;
-                    k0[i] = ok ? LD(Dp, ((bx + 0) * ny + y) * RS + x, dp_n) : T(0);
-                    k1[i] = ok ? LD(Dp, ((bx + 2) * ny + y) * RS + x, dp_n) : T(0);
-                }
+                swin(k0, Dp, bx * ny * RS + x, RS, b0 + dy - KIN_HALF, ny, dp_n, st);
+                swin(k1, Dp, (bx + 2) * ny * RS + x, RS, b0 + dy - KIN_HALF, ny, dp_n, st);
                 kin_block(k0, k1, o0, o1);
 #pragma unroll
                 for (int j = 0; j < BB; ++j) {
@@ -633,75 +759,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd_xy(HphiLaun
         }
     }
     __syncthreads();
-    // write the member rows of the four type planes (values off the members are never read)
-    T* G = static_cast<T*>(a.ws) + r.ws_G;
-    const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
+    // ---- compress: members of this plane -> H phi (plus the z arm left in G by k_kin_z)
     if (yhi_ >= 0) {
-        const int nrows = yhi_ - ylo_ + 1;
-        const int n = 4 * nrows * nxp;
-        const FastDiv fd_row(nrows * nxp), fd_nxp(nxp);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int tb = fd_row.div(i), rem = i - tb * nrows * nxp;
-            const int b = ylo_ + fd_nxp.div(rem), xb = rem - (b - ylo_) * nxp;
-            ST(G, (tb + 4 * bz) * gplane + (static_cast<int64_t>(zb) * nyp + b) * nxp + xb, 8 * gplane,
-               LD(Gs, (tb * nyp + b) * nxp + xb, gs_n));
-        }
-    }
-    const double ekin = warp_sum(static_cast<double>(ekin_t));
-    if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
-}
-
-// ---------------------------------------------------------------- kinetic z arm
-
-// Per (x'', y'') column of the L' box inside the L box's x, y range: the kinetic arm
-// along z of the four type pairs (t, t + 4), added to G.
-template <class T>
-__global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
-    [[maybe_unused]] int* ST_ = a.status;
-    [[maybe_unused]] constexpr int KID = 5;
-    const FnRec r = a.fn[blockIdx.y];
-    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
-    const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
-    const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;   // column (x, y) of the L box
-    const int tb = blockIdx.z;                             // type pair (tb, tb + 4)
-    T ekin_t = 0;
-    if (c < nx * ny) {
-        const int y = c / nx, x = c - y * nx;
-        const int xb = x - dx, yb = y - dy;             // the same column in the L' box
-        if (xb >= 0 && xb < nxp && yb >= 0 && yb < nyp) {
-            const T* D = static_cast<const T*>(a.ws) + r.ws_D;
-            T* G = static_cast<T*>(a.ws) + r.ws_G;
-            const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
-            const int64_t pn = static_cast<int64_t>(nx) * ny;
-            const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
-            const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
-            const int64_t gcol = static_cast<int64_t>(yb) * nxp + xb;
-            const T ks = static_cast<T>(a.kin_scale);
-            {
-                for (int b0 = 0; b0 < nzp; b0 += BB) {
-                    T k0[KW], k1[KW], o0[BB], o1[BB];
+        const T* G = static_cast<const T*>(a.ws) + r.ws_G;
+        const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
+        T* out = static_cast<T*>(a.hphi) + r.off_hphi;
+        const int64_t out_room = a.hphi_n - r.off_hphi;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int b = ylo_ + warp; b <= yhi_; b += (blockDim.x >> 5)) {
+            if (rx0[b] < 0) continue;
+            const int y = b + dy;
+            const bool yin = y >= 0 && y < ny;
+            const int64_t grow = (static_cast<int64_t>(zb) * nyp + b) * nxp;
+            if (bz == 0) {   // scaling part s (type 0) on the coarse members
+                for (int xb = rx0[b] + lane; xb <= rx1[b]; xb += 32) {
+                    const int x = xb + dx;
+                    T v = LD(Gs, static_cast<int64_t>(b) * nxp + xb, gs_n);
+                    if (yin && x >= 0 && x < nx) v += LD(G, grow + xb, 8 * gplane);
+                    ST(out, roff[b] + (xb - rx0[b]), out_room, v);
+                }
+            }
+            // wavelet parts on the fine members of this row
+            const int64_t frow = at.rowPf + b + static_cast<int64_t>(nyp) * zb;
+            const int f0 = LD(a.rowptr, frow, a.rowptr_n), f1 = LD(a.rowptr, frow + 1, a.rowptr_n);
+            for (int q = f0; q < f1; ++q) {
+                const Seg fs = LD(a.seg, at.segPf + q, a.seg_n);
+                for (int xb = fs.x0 + lane; xb <= fs.x1; xb += 32) {
+                    const int x = xb + dx;
+                    const bool zin = yin && x >= 0 && x < nx;
 #pragma unroll
-                    for (int i = 0; i < KW; ++i) {
-                        const int z = b0 + dz - KIN_HALF + i;
-                        const bool ok = z >= 0 && z < nz;
-                        k0[i] = ok ? LD(D, tb * plane + z * pn + c, 8 * plane) : T(0);
-                        k1[i] = ok ? LD(D, (tb + 4) * plane + z * pn + c, 8 * plane) : T(0);
-                    }
-                    kin_block(k0, k1, o0, o1);
-#pragma unroll
-                    for (int j = 0; j < BB; ++j) {
-                        const int b = b0 + j;
-                        if (b < nzp) {
-                            o0[j] *= ks;
-                            o1[j] *= ks;
-                            const int64_t g0 = tb * gplane + b * pnp + gcol;
-                            const int64_t g1 = (tb + 4) * gplane + b * pnp + gcol;
-                            ST(G, g0, 8 * gplane, LD(G, g0, 8 * gplane) + o0[j]);
-                            ST(G, g1, 8 * gplane, LD(G, g1, 8 * gplane) + o1[j]);
-                            const int z = b + dz;
-                            if (z >= 0 && z < nz) ekin_t += k0[KIN_HALF + j] * o0[j] + k1[KIN_HALF + j] * o1[j];
-                        }
+                    for (int tb = 0; tb < 4; ++tb) {
+                        const int t = tb + 4 * bz;
+                        if (t == 0) continue;
+                        T v = LD(Gs, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, gs_n);
+                        if (zin) v += LD(G, t * gplane + grow + xb, 8 * gplane);
+                        ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + fs.off + (xb - fs.x0), out_room, v);
                     }
                 }
             }
@@ -1051,10 +1143,9 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_segL + 7) / 8, nf), 256, 0, s>>>(a)));
     TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
     TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
-    TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
     TRACED(a.tr, TK_KINETIC, s,
            (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf, 4), 128, 0, s>>>(a)));
-    TRACED(a.tr, TK_COMPRESS, s, (k_compress<T><<<dim3((a.max_segP + 7) / 8, nf), 256, 0, s>>>(a)));
+    TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
     return cudaGetLastError();
 }
 
