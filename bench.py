@@ -2,7 +2,7 @@
 locreg workloads shaped like the paper's (arXiv 1401.7441), on one or more GPUs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--precision fp32|fp64] [--impl ours|reference]
+                  [--precision fp32|fp64|bf16x] [--impl ours|reference]
 
 One step = lsw_apply_hamiltonian (every support function) + lsw_build_matrices (the
 whole CSR pattern) on inputs resident in HBM.  The L2 is flushed (a 512 MB write)
@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--workload", default="atoms10k")
-    p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
+    p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64", "bf16x"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="step", choices=["step", "serving"],
                    help="serving: Poisson request stream through the continuous-batching server")
@@ -113,9 +113,10 @@ def keys_to_g(keys):
 
 # ---------------------------------------------------------------- oracle (CPU) leg
 
-def oracle_sample(wl, budget_s=20.0, max_fn=None):
+def oracle_sample(wl, budget_s=20.0, max_fn=None, keep=None):
     """Time the oracle on a bounded sample: H phi of the first functions, then the S/H
-    entries between them.  Returns (functions/s, cores, description)."""
+    entries between them.  Returns (functions/s, cores, description); with ``keep`` (a
+    dict) also stores the sample's results there for the error report."""
     from oracle import geometry as G
     from oracle import hamiltonian as Hm
     from oracle import matrices as Mx
@@ -138,15 +139,20 @@ def oracle_sample(wl, budget_s=20.0, max_fn=None):
         lo = [2 * int(L.lo[d]) - 14 for d in range(3)]
         shape = [2 * int(L.hi[d] - L.lo[d] + 1) + 29 for d in range(3)]
         Vb = I.potential_block(wl, lo, shape)
-        hphi[f] = Hm.apply_hamiltonian(geo, f, phi[f], Vb, lo)[0]
+        hphi[f], ek_f, ep_f = Hm.apply_hamiltonian(geo, f, phi[f], Vb, lo)
+        if keep is not None:
+            keep.setdefault("energies", {})[f] = (ek_f, ep_f)
         done.append(f)
         if time.perf_counter() - tf > budget_s:
             break
+    ents = {}
     for a in done:
         for b in done:
-            Mx.overlap_entry(geo, a, b, phi[a], phi[b])
-            Mx.hamiltonian_entry(geo, a, b, phi[a], hphi[b])
+            ents[(a, b)] = (Mx.overlap_entry(geo, a, b, phi[a], phi[b]),
+                            Mx.hamiltonian_entry(geo, a, b, phi[a], hphi[b]))
     dt = time.perf_counter() - tf
+    if keep is not None:
+        keep.update(done=done, phi=phi, hphi=hphi, entries=ents)
     cores = 1
     try:
         import threadpoolctl  # noqa: F401
@@ -156,6 +162,37 @@ def oracle_sample(wl, budget_s=20.0, max_fn=None):
               "H phi each, then S and H entries among them; %.1f s" % (os.cpu_count() or 1, len(done), nsf, dt))
     _ = t0
     return len(done) / dt, cores, sample
+
+
+def error_report(ref, S, hphi_dev, ek_dev, ep_dev, H_dev, S_dev, cutoff_pairs):
+    """Errors of the GPU results against the oracle sample (scaled as in the parity
+    tests: H phi normwise per function, energies and H/S entries by Cauchy-Schwarz
+    bounds)."""
+    done = ref["done"]
+    hp = hphi_dev.double().cpu().numpy()
+    ek, ep = ek_dev.cpu().numpy(), ep_dev.cpu().numpy()
+    e_h, e_en = [], []
+    for f in done:
+        h = ref["hphi"][f]
+        o = int(S.off_Lp[f])
+        g = hp[o:o + len(h)]
+        e_h.append(float(np.linalg.norm(g - h) / np.linalg.norm(h)))
+        scale = np.linalg.norm(ref["phi"][f]) * np.linalg.norm(h)
+        rk, rp_ = ref["energies"][f]
+        e_en.append(float(max(abs(ek[f] - rk), abs(ep[f] - rp_)) / scale))
+    Hh, Sh = H_dev.cpu().numpy(), S_dev.cpu().numpy()
+    e_s, e_hh = [], []
+    for (a, b), (sv, hv) in ref["entries"].items():
+        row = S.col[S.row_ptr[a]:S.row_ptr[a + 1]]
+        k = np.searchsorted(row, b)
+        if k < len(row) and row[k] == b:
+            kk = int(S.row_ptr[a] + k)
+            e_s.append(abs(Sh[kk] - sv) / (np.linalg.norm(ref["phi"][a]) * np.linalg.norm(ref["phi"][b])))
+            e_hh.append(abs(Hh[kk] - hv) / (np.linalg.norm(ref["phi"][a]) * np.linalg.norm(ref["hphi"][b])))
+    return {"against": "FP64 CPU oracle", "functions": len(done), "entries": len(e_s),
+            "hphi_rel_max": max(e_h), "hphi_rel_mean": float(np.mean(e_h)),
+            "energy_scaled_max": max(e_en),
+            "S_scaled_max": float(max(e_s)) if e_s else None, "H_scaled_max": float(max(e_hh)) if e_hh else None}
 
 
 def reference_main(args):
@@ -336,7 +373,7 @@ def gpu_main(args):
     B.build()
     wl = workload(args.workload)
     prec = args.precision or wl.precision
-    P = lsw.LSW_FP64 if prec == "fp64" else lsw.LSW_FP32
+    P = {"fp64": lsw.LSW_FP64, "fp32": lsw.LSW_FP32, "bf16x": lsw.LSW_FP32_BF16X}[prec]
     dt = torch.float64 if prec == "fp64" else torch.float32
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -446,8 +483,8 @@ def gpu_main(args):
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak,
                     "traffic": stored_traffic(dom, wl.name, prec, (tune or {}).get("chosen", {}).get("batch")),
-                    "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if prec == "fp32"
-                                    else "nominal GB300 FP64 rate (1.25 TFLOP/s)")}
+                    "peak_source": ("nominal GB300 FP64 rate (1.25 TFLOP/s)" if prec == "fp64"
+                                    else "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")}
         else:
             roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
                     "frac": None, "traffic": None}
@@ -455,22 +492,27 @@ def gpu_main(args):
     launches_per_step = int(sum(v[1] for v in kinds.values()) / args.steps) if kinds else None
 
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sample = oracle_sample(wl, budget_s=20.0)
+        ref = {}
+        v, cores, sample = oracle_sample(wl, budget_s=20.0, keep=ref)
         cpu = {"value": v, "unit": "support_functions/s", "cores": cores, "kind": "oracle", "sample": sample}
+        step()
+        torch.cuda.synchronize()
+        err = error_report(ref, S, hphi, ek, ep, Hm, Sm, None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "support_functions/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16x": "f32+bf16x3"}[prec], "data": "synthetic",
                 "config": {"workload": wl.name, "atoms": len(wl.pos), "support_functions": S.n_sf,
                            "pattern_nnz": nnz, "grid": list(wl.N), "h_bohr": wl.h,
                            "precision": prec, "l2": "flushed (512 MB write) before every timed step",
                            "parallelism": "replicas" if world > 1 else "single",
                            "options": (tune or {}).get("chosen", {"batch": args.batch or None, "tile": args.tile or None}),
                            "autotune_ms": {k: v for k, v in (tune or {}).items() if k != "chosen"}},
-                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "error_vs_oracle": err, "clocks": clocks,
                 "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
                 "kernel_share": kshare,
                 "algorithmic_tflop_per_step": {k: v / 1e12 for k, v in flops.items()},

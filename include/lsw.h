@@ -52,12 +52,20 @@ typedef enum {
     LSW_ERR_CUDA = 3,         /* a CUDA runtime call failed                      */
     LSW_ERR_TIMEOUT = 4,      /* lsw_sync: the device did not finish in time     */
     LSW_ERR_STATE = 5,        /* wrong call order (e.g. no potential set)        */
-    LSW_ERR_UNSUPPORTED = 6   /* valid but outside what this build handles       */
+    LSW_ERR_UNSUPPORTED = 6,  /* valid but outside what this build handles       */
+    LSW_ERR_IO = 7            /* lsw_save / lsw_load: file cannot be written/read */
 } lsw_status;
 
 #define LSW_HOST_ONLY (-1)
 
-typedef enum { LSW_FP64 = 0, LSW_FP32 = 1 } lsw_precision;
+/* Arithmetic of a system.  LSW_FP64 and LSW_FP32: phi, H phi, V and every convolution
+ * in that type.  LSW_FP32_BF16X: FP32 storage and arithmetic, except the z-direction
+ * combined synthesis + magic filter and its transpose (the band-Toeplitz passes of the
+ * z stage, Sec. II.B), which run as split-bfloat16 products on the tensor cores with
+ * FP32 accumulation: each FP32 operand is split into 2 bfloat16 parts and the 3
+ * products of order <= 1 are summed (option "zsplit" = 3: 3 parts, 6 products, FP32
+ * rounding level).  H, S and energies are FP64 accumulations in every mode. */
+typedef enum { LSW_FP64 = 0, LSW_FP32 = 1, LSW_FP32_BF16X = 2 } lsw_precision;
 typedef enum { LSW_REGION_L = 0, LSW_REGION_LP = 1 } lsw_region;
 typedef enum { LSW_PART_COARSE = 0, LSW_PART_FINE = 1 } lsw_part;
 typedef enum { LSW_FINE_UNION = 0, LSW_FINE_OWN = 1 } lsw_fine_mode;
@@ -237,14 +245,40 @@ lsw_status lsw_profile(lsw_system sys, int32_t enable);
 
 /* Summed device milliseconds and launch counts per kernel kind since the last read,
  * kinds in this order: 0 memset, 1 uncompress, 2 forward xy, 3 z stage with V,
- * 4 backward xy, 5 kinetic, 6 compress, 7 H/S tiles.  Waits for the stream.  Writes
+ * 4 backward xy (with the compressed write), 5 kinetic z arm, 6 (unused), 7 H/S tiles.  Waits for the stream.  Writes
  * min(max_kinds, *n_kinds) entries of ms[] and launches[]; resets the totals. */
 lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds, double* ms,
                             int64_t* launches);
 
+/* Checkpoint (no counterpart in the paper, which restarts from its own files): write
+ * the system description and, if phi_dev is not NULL, the compressed support functions
+ * (total_L values of the system precision, device) to `path`.  Waits for the system's
+ * stream.  File: "LSWSAVE1", int32 version 1, then the lsw_system_desc fields, the
+ * atom arrays, the "zsplit" value, int64 total_L, int64 has_phi, phi; little-endian.
+ * Errors: LSW_ERR_ARG (NULL), LSW_ERR_IO, LSW_ERR_CUDA. */
+lsw_status lsw_save(lsw_system sys, const void* phi_dev, const char* path);
+
+/* Rebuild a saved system on `ctx` (same arithmetic as lsw_system_create, so keys,
+ * layout and pattern are identical) and, if phi_dev is not NULL, copy the saved
+ * support functions into it (device, total_L values; the file must hold them).  Pass
+ * NULL first to learn total_L from lsw_system_layout, then lsw_load_phi.  Synchronous.
+ * Errors: LSW_ERR_ARG, LSW_ERR_IO (unreadable or not a checkpoint), LSW_ERR_STATE (no
+ * support functions in the file), and those of lsw_system_create. */
+lsw_status lsw_load(lsw_ctx ctx, const char* path, lsw_system* out, void* phi_dev);
+
+/* Copy the support functions saved in `path` into phi_dev (device, total_L values of
+ * sys, which must have been built from that file).  Synchronous.
+ * Errors: LSW_ERR_ARG, LSW_ERR_IO, LSW_ERR_STATE (file without support functions or of
+ * another layout). */
+lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev);
+
 /* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
- * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8).
- * Errors: LSW_ERR_ARG (unknown name or value). */
+ * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8),
+ * "zsplit" (LSW_FP32_BF16X systems only: 2 or 3 bfloat16 parts per FP32 operand of the
+ * tensor-core z stage).
+ * Errors: LSW_ERR_ARG (unknown name or value), LSW_ERR_STATE ("zsplit" on another
+ * precision), LSW_ERR_UNSUPPORTED (3 parts do not fit a locreg's tile in shared memory;
+ * the previous value stays). */
 lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value);
 
 #ifdef __cplusplus

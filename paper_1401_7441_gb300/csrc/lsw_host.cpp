@@ -168,7 +168,8 @@ struct lsw_system_s {
     cudaStream_t stream = nullptr;   // where this system's work is enqueued (ctx's by default)
     int32_t N[3];
     double h;
-    int prec;
+    int prec;              // storage / arithmetic type: LSW_FP64 or LSW_FP32
+    int zsplit = 0;        // LSW_FP32_BF16X: bfloat16 parts of the tensor-core z stage
     size_t esize;
     int32_t n_atoms;
     std::vector<double> pos, r_loc, r_fine;
@@ -394,6 +395,20 @@ void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, siz
     *bwd = es * static_cast<size_t>(plA + 2 * r.np[1] * X + 4 * r.n[1] * RS);
 }
 
+// Dynamic shared memory of the tensor-core z stage for a function record and `parts`
+// bfloat16 parts (mirror of the layout in k_z_tc: 512-byte header, data operand parts
+// 128 x max(K1, K2), filter operand parts N1 x K1 and N2 x K2, V tile Z x 128 FP32).
+size_t ztc_smem(const FnRec& r, int parts) {
+    auto up16 = [](int64_t v) { return (v + 15) / 16 * 16; };
+    const int64_t Z = 2 * r.n[2] + 29;
+    const int64_t K1 = up16(2 * r.n[2]), N1 = up16(Z), K2 = N1, N2 = up16(2 * r.np[2]);
+    const int64_t KA = std::max(K1, K2);
+    return static_cast<size_t>(512 + parts * (128 * KA * 2 + N1 * K1 * 2 + N2 * K2 * 2) + Z * 128 * 4);
+}
+// Largest extents the tensor-core z stage takes (register window of half of K1 <= 64,
+// MMA N <= 256).
+bool ztc_fits(const FnRec& r) { return r.n[2] <= 64 && 2 * r.np[2] <= 256; }
+
 lsw_status build_plans(lsw_system_s* s) {
     const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
     const int zcols = s->prec == LSW_FP64 ? ZCOLS_F64 : ZCOLS_F32;
@@ -458,10 +473,18 @@ lsw_status build_plans(lsw_system_s* s) {
             p.smem_fwd = std::max(p.smem_fwd, a1);
             p.smem_z = std::max(p.smem_z, a2);
             p.smem_bwd = std::max(p.smem_bwd, a3);
+            if (s->zsplit) {
+                if (!ztc_fits(r))
+                    return fail(LSW_ERR_UNSUPPORTED, "locreg z extent %d / %d too large for the tensor-core z stage",
+                                r.n[2], r.np[2]);
+                p.smem_ztc = std::max(p.smem_ztc, ztc_smem(r, s->zsplit));
+            }
         }
-        if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem)
-            return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles (%zu/%zu/%zu > %zu bytes)",
-                        p.smem_fwd, p.smem_z, p.smem_bwd, s->ctx->max_smem);
+        p.zsplit = s->zsplit;
+        if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem ||
+            p.smem_ztc > s->ctx->max_smem)
+            return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles (%zu/%zu/%zu/%zu > %zu bytes)",
+                        p.smem_fwd, p.smem_z, p.smem_bwd, p.smem_ztc, s->ctx->max_smem);
         s->batches.push_back(b);
     }
     s->ws_elems = ws_max;
@@ -831,7 +854,7 @@ lsw_status lsw_system_create(lsw_ctx ctx, const lsw_system_desc* d, lsw_system* 
     if (!(d->h > 0) || !std::isfinite(d->h)) return fail(LSW_ERR_ARG, "lsw_system_create: h must be > 0");
     if (d->n_atoms < 1 || !d->pos || !d->r_loc || !d->r_fine || !d->n_sf)
         return fail(LSW_ERR_ARG, "lsw_system_create: no atoms or NULL atom arrays");
-    if (d->precision != LSW_FP64 && d->precision != LSW_FP32)
+    if (d->precision != LSW_FP64 && d->precision != LSW_FP32 && d->precision != LSW_FP32_BF16X)
         return fail(LSW_ERR_ARG, "lsw_system_create: precision %d", d->precision);
     if (d->fine_mode != LSW_FINE_UNION && d->fine_mode != LSW_FINE_OWN)
         return fail(LSW_ERR_ARG, "lsw_system_create: fine_mode %d", d->fine_mode);
@@ -855,7 +878,8 @@ lsw_status lsw_system_create(lsw_ctx ctx, const lsw_system_desc* d, lsw_system* 
     s->stream = ctx->stream;
     for (int k = 0; k < 3; ++k) s->N[k] = d->N[k];
     s->h = d->h;
-    s->prec = d->precision;
+    s->prec = d->precision == LSW_FP64 ? LSW_FP64 : LSW_FP32;
+    s->zsplit = d->precision == LSW_FP32_BF16X ? 2 : 0;
     s->esize = s->prec == LSW_FP64 ? 8 : 4;
     s->n_atoms = d->n_atoms;
     s->pos.assign(d->pos, d->pos + 3 * d->n_atoms);
@@ -1121,8 +1145,15 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             p.smem_fwd = std::max(p.smem_fwd, a1);
             p.smem_z = std::max(p.smem_z, a2);
             p.smem_bwd = std::max(p.smem_bwd, a3);
+            if (sys->zsplit) {
+                if (!ztc_fits(r))
+                    return fail(LSW_ERR_UNSUPPORTED, "locreg z extent too large for the tensor-core z stage");
+                p.smem_ztc = std::max(p.smem_ztc, ztc_smem(r, sys->zsplit));
+            }
         }
-        if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > sys->ctx->max_smem)
+        p.zsplit = sys->zsplit;
+        if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > sys->ctx->max_smem ||
+            p.smem_ztc > sys->ctx->max_smem)
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
         // records into the head of the scratch (pageable source: reusable on return)
         CUDA_TRY(cudaMemcpyAsync(scratch, recs, nb * sizeof(FnRec), cudaMemcpyHostToDevice, st));
@@ -1352,6 +1383,22 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         sys->use_graph = static_cast<int>(value);
         return LSW_OK;
     }
+    if (std::strcmp(name, "zsplit") == 0) {
+        if (value != 2 && value != 3) return fail(LSW_ERR_ARG, "lsw_set_option: zsplit %lld", static_cast<long long>(value));
+        if (!sys->zsplit) return fail(LSW_ERR_STATE, "lsw_set_option: zsplit needs an LSW_FP32_BF16X system");
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        const int old = sys->zsplit;
+        sys->zsplit = static_cast<int>(value);
+        lsw_status e = build_plans(sys);
+        if (e != LSW_OK) {
+            const std::string msg = g_err;
+            sys->zsplit = old;
+            if (build_plans(sys) != LSW_OK) return fail(LSW_ERR_STATE, "lsw_set_option: zsplit: cannot restore plans");
+            return fail(e, "%s", msg.c_str());
+        }
+        return LSW_OK;
+    }
     if (std::strcmp(name, "tile") == 0) {
         if (value < 2 || value > 8) return fail(LSW_ERR_ARG, "lsw_set_option: tile %lld", static_cast<long long>(value));
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
@@ -1360,6 +1407,145 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         return build_hs_plan(sys);
     }
     return fail(LSW_ERR_ARG, "lsw_set_option: unknown option '%s'", name);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+const char kSaveMagic[8] = {'L', 'S', 'W', 'S', 'A', 'V', 'E', '1'};
+
+struct FileCloser {
+    FILE* f;
+    ~FileCloser() {
+        if (f) std::fclose(f);
+    }
+};
+
+template <class V>
+bool put(FILE* f, const V* p, size_t n) { return n == 0 || std::fwrite(p, sizeof(V), n, f) == n; }
+template <class V>
+bool get(FILE* f, V* p, size_t n) { return n == 0 || std::fread(p, sizeof(V), n, f) == n; }
+
+// Reads the description part of a checkpoint; leaves the file at total_L.
+lsw_status read_desc(FILE* f, const char* path, lsw_system_desc* d, std::vector<double>& pos, std::vector<double>& rl,
+                     std::vector<double>& rf, std::vector<int32_t>& nsf, int32_t* zsplit) {
+    char magic[8];
+    int32_t version = 0;
+    if (!get(f, magic, 8) || std::memcmp(magic, kSaveMagic, 8) != 0 || !get(f, &version, 1) || version != 1)
+        return fail(LSW_ERR_IO, "lsw_load: %s is not a checkpoint of this library", path);
+    std::memset(d, 0, sizeof(*d));
+    bool ok = get(f, d->N, 3) && get(f, &d->h, 1) && get(f, &d->n_atoms, 1) && get(f, &d->lprime_margin, 1) &&
+              get(f, &d->pair_cutoff, 1) && get(f, &d->pair_mode, 1) && get(f, &d->fine_mode, 1) &&
+              get(f, &d->precision, 1) && get(f, zsplit, 1);
+    if (!ok || d->n_atoms < 1 || d->n_atoms > (1 << 26)) return fail(LSW_ERR_IO, "lsw_load: %s: truncated header", path);
+    const size_t n = static_cast<size_t>(d->n_atoms);
+    pos.resize(3 * n);
+    rl.resize(n);
+    rf.resize(n);
+    nsf.resize(n);
+    if (!get(f, pos.data(), 3 * n) || !get(f, rl.data(), n) || !get(f, rf.data(), n) || !get(f, nsf.data(), n))
+        return fail(LSW_ERR_IO, "lsw_load: %s: truncated atom arrays", path);
+    d->pos = pos.data();
+    d->r_loc = rl.data();
+    d->r_fine = rf.data();
+    d->n_sf = nsf.data();
+    return LSW_OK;
+}
+
+// Reads total_L, has_phi and (if phi_dev) the values into phi_dev.
+lsw_status read_phi(FILE* f, const char* path, lsw_system_s* s, void* phi_dev) {
+    int64_t total = -1, has = 0;
+    if (!get(f, &total, 1) || !get(f, &has, 1)) return fail(LSW_ERR_IO, "lsw_load: %s: truncated", path);
+    if (total != s->off_L.back()) return fail(LSW_ERR_STATE, "lsw_load: %s holds another layout", path);
+    if (!phi_dev) return LSW_OK;
+    if (!has) return fail(LSW_ERR_STATE, "lsw_load: %s holds no support functions", path);
+    if (s->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    std::vector<unsigned char> buf(static_cast<size_t>(total) * s->esize);
+    if (!get(f, buf.data(), buf.size())) return fail(LSW_ERR_IO, "lsw_load: %s: truncated values", path);
+    CUDA_TRY(cudaSetDevice(s->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    CUDA_TRY(cudaMemcpy(phi_dev, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    return LSW_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lsw_status lsw_save(lsw_system sys, const void* phi_dev, const char* path) {
+    g_err.clear();
+    if (!sys || !path) return fail(LSW_ERR_ARG, "lsw_save: NULL argument");
+    if (phi_dev && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    const int64_t total = sys->off_L.back();
+    std::vector<unsigned char> buf;
+    if (phi_dev) {
+        buf.resize(static_cast<size_t>(total) * sys->esize);
+        CUDA_TRY(cudaSetDevice(sys->ctx->device));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        CUDA_TRY(cudaMemcpy(buf.data(), phi_dev, buf.size(), cudaMemcpyDeviceToHost));
+    }
+    FileCloser fc{std::fopen(path, "wb")};
+    if (!fc.f) return fail(LSW_ERR_IO, "lsw_save: cannot open %s", path);
+    const int32_t version = 1, na = sys->n_atoms;
+    const int32_t prec = sys->zsplit ? LSW_FP32_BF16X : sys->prec, zs = sys->zsplit;
+    const double h = sys->h, margin = sys->margin, cutoff = sys->cutoff;
+    const int32_t pm = sys->pair_mode, fm = sys->fine_mode;
+    const int64_t has = phi_dev ? 1 : 0;
+    const bool ok = put(fc.f, kSaveMagic, 8) && put(fc.f, &version, 1) && put(fc.f, sys->N, 3) && put(fc.f, &h, 1) &&
+                    put(fc.f, &na, 1) && put(fc.f, &margin, 1) && put(fc.f, &cutoff, 1) && put(fc.f, &pm, 1) &&
+                    put(fc.f, &fm, 1) && put(fc.f, &prec, 1) && put(fc.f, &zs, 1) &&
+                    put(fc.f, sys->pos.data(), sys->pos.size()) && put(fc.f, sys->r_loc.data(), sys->r_loc.size()) &&
+                    put(fc.f, sys->r_fine.data(), sys->r_fine.size()) && put(fc.f, sys->nsf.data(), sys->nsf.size()) &&
+                    put(fc.f, &total, 1) && put(fc.f, &has, 1) && put(fc.f, buf.data(), buf.size());
+    if (!ok || std::fflush(fc.f) != 0) return fail(LSW_ERR_IO, "lsw_save: write to %s failed", path);
+    return LSW_OK;
+}
+
+lsw_status lsw_load(lsw_ctx ctx, const char* path, lsw_system* out, void* phi_dev) {
+    g_err.clear();
+    if (!ctx || !path || !out) return fail(LSW_ERR_ARG, "lsw_load: NULL argument");
+    *out = nullptr;
+    FileCloser fc{std::fopen(path, "rb")};
+    if (!fc.f) return fail(LSW_ERR_IO, "lsw_load: cannot open %s", path);
+    lsw_system_desc d;
+    std::vector<double> pos, rl, rf;
+    std::vector<int32_t> nsf;
+    int32_t zs = 0;
+    lsw_status e = read_desc(fc.f, path, &d, pos, rl, rf, nsf, &zs);
+    if (e != LSW_OK) return e;
+    lsw_system s = nullptr;
+    if ((e = lsw_system_create(ctx, &d, &s)) != LSW_OK) return e;
+    if (zs == 3 && s->zsplit && !ctx->host_only) {
+        if ((e = lsw_set_option(s, "zsplit", 3)) != LSW_OK) {
+            lsw_system_destroy(s);
+            return e;
+        }
+    } else if (zs == 3) {
+        s->zsplit = 3;
+    }
+    if ((e = read_phi(fc.f, path, s, phi_dev)) != LSW_OK) {
+        const std::string msg = g_err;
+        lsw_system_destroy(s);
+        return fail(e, "%s", msg.c_str());
+    }
+    *out = s;
+    return LSW_OK;
+}
+
+lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev) {
+    g_err.clear();
+    if (!sys || !path || !phi_dev) return fail(LSW_ERR_ARG, "lsw_load_phi: NULL argument");
+    FileCloser fc{std::fopen(path, "rb")};
+    if (!fc.f) return fail(LSW_ERR_IO, "lsw_load: cannot open %s", path);
+    lsw_system_desc d;
+    std::vector<double> pos, rl, rf;
+    std::vector<int32_t> nsf;
+    int32_t zs = 0;
+    lsw_status e = read_desc(fc.f, path, &d, pos, rl, rf, nsf, &zs);
+    if (e != LSW_OK) return e;
+    if (d.n_atoms != sys->n_atoms) return fail(LSW_ERR_STATE, "lsw_load_phi: %s holds another system", path);
+    return read_phi(fc.f, path, sys, phi_dev);
 }
 
 }  // extern "C"

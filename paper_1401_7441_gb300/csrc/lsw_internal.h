@@ -87,6 +87,9 @@ struct HphiLaunch {
     int max_segP;
     size_t smem_fwd, smem_z, smem_bwd;
     int zcols;                   // columns per CTA of the z stage
+    int zsplit;                  // 0: z stage on FMA units; 2 or 3: bfloat16 parts per
+                                 // FP32 operand of the tensor-core z stage
+    size_t smem_ztc;             // dynamic shared memory of the tensor-core z stage
     const AtomRec* atoms;
     const Seg* seg;
     const int32_t* rowptr;
@@ -171,6 +174,7 @@ enum : int {
     ST_BAD_SEG = 2,
     ST_BAD_PAIR = 4,
     ST_BAD_INDEX = 8,   // self-checking build: an index fell outside its buffer
+    ST_WAIT_TIMEOUT = 16,   // a bounded wait for tensor-core completion ran out
 };
 
 // Layout of the device status block (int32 words): [0] status bits, [1] first bad

@@ -20,6 +20,8 @@
 // All kernels are templated on the storage/compute type T (double or float); energy
 // and matrix accumulations are FP64.  Device-side checks set bits of a status word
 // (never trap).
+#include <cuda_bf16.h>
+
 #include <cstdint>
 #include <mutex>
 
@@ -455,6 +457,360 @@ __global__ void __launch_bounds__(ZCols<T>::C) k_z(HphiLaunch a) {
     }
     const double epot = warp_sum(static_cast<double>(epot_t));
     if ((threadIdx.x & 31) == 0 && epot != 0.0) atomicAdd(a.e_pot + r.f, epot);
+}
+
+// ---------------------------------------------------------------- z stage on tensor cores
+//
+// The z stage of k_z cast as two band-Toeplitz products per tile of 128 real-space
+// columns c (the MMA rows, M = 128), with the filter matrices as the N x K operand:
+//   U[c][o]  = sum_k A1[c][k] F1[o][k],   k = b nz + q,      F1[o][k] = F_b[o - 2q]
+//   v[c][o]  = V(o, c) U[c][o]            (E_pot += v U)
+//   Bb[c][j] = sum_o v[c][o] F2[j][o],    j = b' nz' + b,     F2[j][o] = F_b'[o - 2(b + dz)]
+// F_b are the combined synthesis + magic filters (w*h), (w*g) of k_z.  Every FP32
+// operand x is split into NS bfloat16 parts x = x_0 + x_1 (+ x_2) (each part the
+// rounding of what the previous ones leave); the products of parts whose orders add up
+// to at most NS - 1 are accumulated in FP32 in tensor memory: NS = 2 takes 3 products
+// (relative error of a product about 2^-17), NS = 3 takes 6 (about 2^-24).
+//
+// One CTA of 8 warps loops over tiles of one function.  Warp w reads tensor-memory
+// lanes 32 (w mod 4) .. + 31 (the hardware's lane quarters), so thread (w, lane) owns
+// column 32 (w mod 4) + lane of the tile and half w / 4 of each K or N range.  Per tile:
+// inputs (prefetched into registers during the previous tile) -> bfloat16 parts in
+// shared memory; V of the tile -> shared memory by cp.async; forward MMAs; U from
+// tensor memory -> v -> parts; backward MMAs; result from tensor memory -> Bb.  Waits on
+// MMA completion are bounded (about 1 s) and end in a status bit, never a hang.
+
+namespace tc {
+
+constexpr int TILE = 128;       // real-space columns per tile (MMA M)
+constexpr int HEAD = 512;       // shared header: mbarrier, tensor-memory address, taps
+constexpr int TILES_PER_CTA = 8;
+constexpr int MAX_KH = 64;      // largest half of K1 = 2 nz rounded up to 16 (nz <= 64)
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Byte offset of element (r, k) of an R x K bfloat16 operand in the canonical K-major
+// layout without swizzle: core matrices of 8 rows x 16 bytes stored contiguously,
+// K-adjacent core matrices 128 bytes apart (leading byte offset), 8-row groups K * 16
+// bytes apart (stride byte offset).
+__device__ __forceinline__ int core_off(int r, int k, int K) {
+    return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// Shared-memory matrix descriptor of that layout (start address >> 4, leading byte
+// offset >> 4 at bit 16, stride byte offset >> 4 at bit 32, descriptor version 1 at
+// bit 46, no swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t start, int K) {
+    return static_cast<uint64_t>((start & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(128 >> 4) << 16) |
+           (static_cast<uint64_t>((K * 16) >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator (bit 4), bfloat16 A and B
+// (bits 7, 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t da, uint64_t db, uint32_t id, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(da), "l"(db), "r"(id), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor cores (async proxy)
+__device__ __forceinline__ void fence_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of the mbarrier; false after about one second.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const uint64_t t0 = gtime();
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (gtime() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, int ncols) {   // one whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, int ncols) {    // one whole warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 8 consecutive FP32 columns of this thread's lane; the wait is in the same statement
+// so no use of the registers can be scheduled before it.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t q[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(q[i]);
+}
+// (x0, x1) = sum of NS packed bfloat16 pairs (low half x0's part, high half x1's); each
+// part rounds (to nearest) what the previous parts leave, and the subtraction is exact
+// in FP32.
+template <int NS>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t (&w)[NS]) {
+    float r0 = x0, r1 = x1;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(r0, r1);
+        w[i] = *reinterpret_cast<const uint32_t*>(&b);
+        if (i + 1 < NS) {
+            r0 -= __low2float(b);
+            r1 -= __high2float(b);
+        }
+    }
+}
+// Split 8 values and store part i as one 16-byte row of a core matrix at
+// base + i * part_bytes + off.
+template <int NS>
+__device__ __forceinline__ void put8(unsigned char* base, int part_bytes, int off, const float (&x)[8],
+                                     [[maybe_unused]] int* st, [[maybe_unused]] int64_t room) {
+    uint32_t w[4][NS];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) split2<NS>(x[2 * e], x[2 * e + 1], w[e]);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const int64_t at = static_cast<int64_t>(i) * part_bytes + off;
+#ifdef LSW_CHECKED
+        if (off < 0 || off + 16 > part_bytes || at + 16 > room) {
+            lsw_report(st, 8, __LINE__, at, room);
+            continue;
+        }
+#endif
+        *reinterpret_cast<uint4*>(base + at) = make_uint4(w[0][i], w[1][i], w[2][i], w[3][i]);
+    }
+}
+// Index pairs (part of the data operand, part of the filter operand) of the products.
+template <int NS>
+struct Terms;
+template <>
+struct Terms<2> {
+    static constexpr int n = 3;
+    __device__ static int a(int t) { return t == 2 ? 1 : 0; }
+    __device__ static int b(int t) { return t == 1 ? 1 : 0; }
+};
+template <>
+struct Terms<3> {
+    static constexpr int n = 6;   // (0,0) (0,1) (1,0) (1,1) (0,2) (2,0)
+    __device__ static int a(int t) { return t == 2 || t == 3 ? 1 : (t == 5 ? 2 : 0); }
+    __device__ static int b(int t) { return t == 1 || t == 3 ? 1 : (t == 4 ? 2 : 0); }
+};
+
+}  // namespace tc
+
+// Dynamic shared memory of k_z_tc for a function with L extent nz, L' extent nzp
+// (host mirror in lsw_host.cpp: ztc_smem).
+template <int NS>
+__global__ void __launch_bounds__(256, 1) k_z_tc(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 8;
+    using tc::TILE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const FnRec r = a.fn[blockIdx.y];
+    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
+    const int X = 2 * nx + 29, Y = 2 * ny + 29, Z = 2 * nz + 29;
+    const int cols = X * Y;
+    const int ntiles = (cols + TILE - 1) / TILE;
+    if (static_cast<int>(blockIdx.x) >= ntiles) return;   // uniform over the CTA
+    const int nzp = r.np[2], dz = r.lop[2] - r.lo[2];
+    const int K1 = (2 * nz + 15) & ~15, N1 = (Z + 15) & ~15, K2 = N1, N2 = (2 * nzp + 15) & ~15;
+    const int KA = max(K1, K2);
+    const int A_PART = TILE * KA * 2, B1_PART = N1 * K1 * 2, B2_PART = N2 * K2 * 2;
+    unsigned char* sA = smem_raw + tc::HEAD;
+    unsigned char* sB1 = sA + NS * A_PART;
+    unsigned char* sB2 = sB1 + NS * B1_PART;
+    float* sV = reinterpret_cast<float*>(sB2 + NS * B2_PART);   // [Z][TILE]
+    const int64_t room = static_cast<int64_t>(a.smem_ztc);
+    [[maybe_unused]] const int64_t sv_n = (room - (reinterpret_cast<unsigned char*>(sV) - smem_raw)) / 4;
+    int* st = a.status;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = (warp & 3) * 32 + lane;    // tile column = tensor-memory lane
+    const int half = warp >> 2;
+    const uint32_t mbar = tc::saddr(smem_raw);
+    const uint32_t tslot = tc::saddr(smem_raw + 8);
+    const int ncols = max(N1, N2) <= 128 ? 128 : 256;
+    float* taps = reinterpret_cast<float*>(smem_raw + 16);     // [2][FWD_TAPS]
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    if (threadIdx.x == 32) tc::mbar_init(mbar);
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + 2 * FWD_TAPS) {
+        const int i = threadIdx.x - 64;
+        taps[i] = Tab<float>::fwd(i / FWD_TAPS, i % FWD_TAPS);
+    }
+    __syncthreads();
+
+    // filter operands F1 (N1 x K1) and F2 (N2 x K2), zero outside the filter support
+    for (int ci = threadIdx.x; ci < N1 * (K1 >> 3); ci += blockDim.x) {
+        const int o = ci / (K1 >> 3), k0 = (ci - o * (K1 >> 3)) * 8;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + e, b = k >= nz ? 1 : 0, q = k - b * nz, m = o - 2 * q;
+            x[e] = (k < 2 * nz && m >= 0 && m < FWD_TAPS) ? taps[b * FWD_TAPS + m] : 0.f;
+        }
+        tc::put8<NS>(sB1, B1_PART, tc::core_off(o, k0, K1), x, st, room - (sB1 - smem_raw));
+    }
+    for (int ci = threadIdx.x; ci < N2 * (K2 >> 3); ci += blockDim.x) {
+        const int j = ci / (K2 >> 3), o0 = (ci - j * (K2 >> 3)) * 8;
+        const int bp = j >= nzp ? 1 : 0, b = j - bp * nzp;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int o = o0 + e, m = o - 2 * (b + dz);
+            x[e] = (j < 2 * nzp && o < Z && m >= 0 && m < FWD_TAPS) ? taps[bp * FWD_TAPS + m] : 0.f;
+        }
+        tc::put8<NS>(sB2, B2_PART, tc::core_off(j, o0, K2), x, st, room - (sB2 - smem_raw));
+    }
+
+    const float* Bf = static_cast<const float*>(a.ws) + r.ws_Bf;
+    float* Bb = static_cast<float*>(a.ws) + r.ws_Bb;
+    const float* V = static_cast<const float*>(a.V);
+    const int64_t vstride = a.vn[0] * a.vn[1];
+    const int64_t jz0 = 2LL * r.lo[2] - V_REACH - a.vlo[2];
+    const int kh = K1 >> 1, k_lo = half * kh;          // this thread's half of K1
+    const int nh1 = N1 >> 1, o_lo = half * nh1;        // its half of N1 (= K2)
+    const int nh2 = N2 >> 1, j_lo = half * nh2;        // its half of N2
+    float xin[tc::MAX_KH];
+    auto load_in = [&](int tile) {
+        const int c = tile * TILE + row;
+        const bool ok = c < cols;
+#pragma unroll
+        for (int i = 0; i < tc::MAX_KH; ++i) {
+            const int k = k_lo + i;
+            xin[i] = (i < kh && ok && k < 2 * nz) ? LD(Bf, static_cast<int64_t>(k) * cols + c, 2LL * nz * cols) : 0.f;
+        }
+    };
+    load_in(blockIdx.x);
+    tc::fence_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + 8);
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    uint32_t phase = 0;
+    float epot_t = 0.f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int c = tile * TILE + row;
+        const bool valid = c < cols;
+        // V(o, c) for o in this thread's half -> sV (cp.async; read back by this thread only)
+        if (valid) {
+            const int xo = c % X, yo = c / X;
+            const int64_t vrow = (2LL * r.lo[1] - V_REACH + yo - a.vlo[1]) * a.vn[0] + (2LL * r.lo[0] - V_REACH + xo - a.vlo[0]);
+            for (int o = o_lo; o < min(o_lo + nh1, Z); ++o)
+                CPA(sV, o * TILE + row, sv_n, V, (jz0 + o) * vstride + vrow, a.v_n);
+        }
+        // inputs -> A1 parts (row `row`, k in this thread's half)
+#pragma unroll
+        for (int i = 0; i < tc::MAX_KH; i += 8) {
+            if (i >= kh) break;
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = xin[i + e];
+            tc::put8<NS>(sA, A_PART, tc::core_off(row, k_lo + i, K1), x, st, room - (sA - smem_raw));
+        }
+        tc::fence_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t id = tc::idesc(TILE, N1);
+            for (int s = 0; s < (K1 >> 4); ++s)
+#pragma unroll
+                for (int t = 0; t < tc::Terms<NS>::n; ++t)
+                    tc::mma(tmem, tc::sdesc(tc::saddr(sA + tc::Terms<NS>::a(t) * A_PART + s * 256), K1),
+                            tc::sdesc(tc::saddr(sB1 + tc::Terms<NS>::b(t) * B1_PART + s * 256), K1), id,
+                            s > 0 || t > 0);
+            tc::commit(mbar);
+        }
+        if (tile + static_cast<int>(gridDim.x) < ntiles) load_in(tile + gridDim.x);   // prefetch
+        bool ok = tc::mbar_wait(mbar, phase);
+        phase ^= 1;
+        cp_wait();
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicOr(st, ST_WAIT_TIMEOUT);
+            break;
+        }
+        tc::fence_after();
+        // U -> v = V U -> A2 parts (row `row`, o in this thread's half of K2 = N1)
+        for (int ch = 0; ch < nh1; ch += 8) {
+            float u[8], x[8];
+            tc::tmem_ld8(tlane + o_lo + ch, u);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int o = o_lo + ch + e;
+                const float v = (valid && o < Z) ? LD(sV, o * TILE + row, sv_n) * u[e] : 0.f;
+                epot_t += v * u[e];
+                x[e] = v;
+            }
+            tc::put8<NS>(sA, A_PART, tc::core_off(row, o_lo + ch, K2), x, st, room - (sA - smem_raw));
+        }
+        tc::fence_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t id = tc::idesc(TILE, N2);
+            for (int s = 0; s < (K2 >> 4); ++s)
+#pragma unroll
+                for (int t = 0; t < tc::Terms<NS>::n; ++t)
+                    tc::mma(tmem, tc::sdesc(tc::saddr(sA + tc::Terms<NS>::a(t) * A_PART + s * 256), K2),
+                            tc::sdesc(tc::saddr(sB2 + tc::Terms<NS>::b(t) * B2_PART + s * 256), K2), id,
+                            s > 0 || t > 0);
+            tc::commit(mbar);
+        }
+        ok = tc::mbar_wait(mbar, phase);
+        phase ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicOr(st, ST_WAIT_TIMEOUT);
+            break;
+        }
+        tc::fence_after();
+        // result -> Bb (row j = b' nz' + b of the coarse z output, column c)
+        for (int ch = 0; ch < nh2; ch += 8) {
+            float d[8];
+            tc::tmem_ld8(tlane + j_lo + ch, d);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j = j_lo + ch + e;
+                if (valid && j < 2 * nzp) ST(Bb, static_cast<int64_t>(j) * cols + c, 2LL * nzp * cols, d[e]);
+            }
+        }
+        tc::fence_before();
+        __syncthreads();   // every read of this tile's tensor memory and V is done
+        tc::fence_after();
+    }
+    const double epot = warp_sum(static_cast<double>(epot_t));
+    if (lane == 0 && epot != 0.0) atomicAdd(a.e_pot + r.f, epot);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_free(tmem, ncols);
 }
 
 // ---------------------------------------------------------------- kinetic z arm
@@ -1121,6 +1477,7 @@ cudaError_t configure_kernels(size_t max_smem) {
     }
     SETMAX(k_fwd_xy<double>) SETMAX(k_fwd_xy<float>)
     SETMAX(k_z<double>) SETMAX(k_z<float>)
+    SETMAX(k_z_tc<2>) SETMAX(k_z_tc<3>)
     SETMAX(k_bwd_xy<double>) SETMAX(k_bwd_xy<float>)
     SETMAX(k_hs<double>) SETMAX(k_hs<float>)
 #undef SETMAX
@@ -1142,7 +1499,20 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     const int nf = a.nfn;
     TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_segL + 7) / 8, nf), 256, 0, s>>>(a)));
     TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
-    TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
+    if constexpr (sizeof(T) == 4) {
+        if (a.zsplit) {
+            // several tiles per CTA: the filter operands are built once per CTA
+            const int gx = ((a.max_cols + tc::TILE - 1) / tc::TILE + tc::TILES_PER_CTA - 1) / tc::TILES_PER_CTA;
+            if (a.zsplit == 3)
+                TRACED(a.tr, TK_Z, s, (k_z_tc<3><<<dim3(gx, nf), 256, a.smem_ztc, s>>>(a)));
+            else
+                TRACED(a.tr, TK_Z, s, (k_z_tc<2><<<dim3(gx, nf), 256, a.smem_ztc, s>>>(a)));
+        } else {
+            TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
+        }
+    } else {
+        TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
+    }
     TRACED(a.tr, TK_KINETIC, s,
            (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf, 4), 128, 0, s>>>(a)));
     TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));

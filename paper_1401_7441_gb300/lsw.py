@@ -16,9 +16,10 @@ import numpy as np
 
 from . import build as _build
 
-LSW_OK, LSW_ERR_ARG, LSW_ERR_OOM, LSW_ERR_CUDA, LSW_ERR_TIMEOUT, LSW_ERR_STATE, LSW_ERR_UNSUPPORTED = range(7)
+(LSW_OK, LSW_ERR_ARG, LSW_ERR_OOM, LSW_ERR_CUDA, LSW_ERR_TIMEOUT, LSW_ERR_STATE, LSW_ERR_UNSUPPORTED,
+ LSW_ERR_IO) = range(8)
 LSW_HOST_ONLY = -1
-LSW_FP64, LSW_FP32 = 0, 1
+LSW_FP64, LSW_FP32, LSW_FP32_BF16X = 0, 1, 2
 LSW_REGION_L, LSW_REGION_LP = 0, 1
 LSW_PART_COARSE, LSW_PART_FINE = 0, 1
 LSW_FINE_UNION, LSW_FINE_OWN = 0, 1
@@ -27,7 +28,7 @@ FILTERS = {"h": 0, "g": 1, "moments": 2, "magic": 3, "kin_r": 4, "kin_hh": 5, "k
            "kin_gh": 7, "kin_gg": 8, "fwd_h": 9, "fwd_g": 10}
 
 _STATUS = {1: "LSW_ERR_ARG", 2: "LSW_ERR_OOM", 3: "LSW_ERR_CUDA", 4: "LSW_ERR_TIMEOUT",
-           5: "LSW_ERR_STATE", 6: "LSW_ERR_UNSUPPORTED"}
+           5: "LSW_ERR_STATE", 6: "LSW_ERR_UNSUPPORTED", 7: "LSW_ERR_IO"}
 
 
 class LswError(RuntimeError):
@@ -73,9 +74,12 @@ _SIGS = {
     "lsw_profile": (C.c_int, [_P, C.c_int32]),
     "lsw_system_set_stream": (C.c_int, [_P, _P]),
     "lsw_profile_read": (C.c_int, [_P, C.c_int32, _I32P, _DP, _I64P]),
+    "lsw_save": (C.c_int, [_P, _P, C.c_char_p]),
+    "lsw_load": (C.c_int, [_P, C.c_char_p, C.POINTER(_P), _P]),
+    "lsw_load_phi": (C.c_int, [_P, C.c_char_p, _P]),
 }
 
-TRACE_KINDS = ["memset", "uncompress", "fwd_xy", "z_stage", "bwd_xy", "kinetic", "compress", "hs_tiles"]
+TRACE_KINDS = ["memset", "uncompress", "fwd_xy", "z_stage", "bwd_xy", "kinetic", "unused", "hs_tiles"]
 
 
 def lib():
@@ -293,3 +297,17 @@ class System:
             self.close()
         except Exception:
             pass
+
+
+def lsw_save(sys, phi, path):
+    check(lib().lsw_save(sys, _ptr(phi), os.fsencode(path)))
+
+
+def lsw_load(ctx, path, phi=None):
+    out = _P()
+    check(lib().lsw_load(ctx, os.fsencode(path), C.byref(out), _ptr(phi)))
+    return out
+
+
+def lsw_load_phi(sys, path, phi):
+    check(lib().lsw_load_phi(sys, os.fsencode(path), _ptr(phi)))

@@ -16,7 +16,7 @@ from tests.oracle_support import desc_of
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lsw.LSW_FP64: 1e-12, lsw.LSW_FP32: 1e-5}
+TOL = {lsw.LSW_FP64: 1e-12, lsw.LSW_FP32: 1e-5, lsw.LSW_FP32_BF16X: 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,7 +71,7 @@ def check_rows(wl, geo, gpu, ref, rows, tol, h_cols=None):
                 assert abs(gpu["H"][k] - h_ref) <= tol * np.linalg.norm(phi_a) * np.linalg.norm(hb), (a, b)
 
 
-@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_single_function_box(prec):
     wl = I.single_sf_24()
     geo = G.build(desc_of(wl))
@@ -85,7 +85,7 @@ def test_single_function_box(prec):
     assert abs(gpu["H"][0] - (gpu["ek"][0] + gpu["ep"][0])) <= TOL[prec] * abs(gpu["ek"][0])
 
 
-@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_small_system_every_function_and_entry(prec):
     wl = I.scaled("atoms64", 8, seed=5)
     geo = G.build(desc_of(wl))
@@ -137,7 +137,7 @@ def test_options_do_not_change_results():
         assert np.max(np.abs(o["H"] - base["H"])) <= 1e-12 * np.max(np.abs(base["H"])), opts
 
 
-@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_atoms64_full_size_sampled(prec):
     wl = I.atoms64()
     geo = G.build(desc_of(wl))
@@ -176,7 +176,7 @@ def test_step_host_equals_device_calls():
         S.close()
 
 
-@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32])
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_graph_path_on_created_stream(prec):
     # on a created (non-default) stream the library replays captured CUDA graphs
     import torch
@@ -190,3 +190,51 @@ def test_graph_path_on_created_stream(prec):
         gpu = gpu_run(wl, phi_fn(wl), prec, repeat=3)
     check_functions(wl, geo, gpu, ref, TOL[prec])
     check_rows(wl, geo, gpu, ref, range(n), TOL[prec])
+
+
+def test_split_bf16_parts_against_fp32_and_oracle():
+    # Tensor-core z stage (split bfloat16, FP32 accumulation): 2 parts (3 products)
+    # are within the reduced-precision tolerance of the oracle; 3 parts (6 products)
+    # sit at the FP32 rounding level, far closer to the FP32 FMA path than 2 parts.
+    wl = I.scaled("atoms64", 6, seed=12)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    n = len(geo.sf_atom)
+    ref = oracle_hphi(wl, geo, range(n), V)
+    f32 = gpu_run(wl, phi_fn(wl), lsw.LSW_FP32)
+    errs = {}
+    for parts in (2, 3):
+        g = gpu_run(wl, phi_fn(wl), lsw.LSW_FP32_BF16X, options={"zsplit": parts})
+        errs[parts] = check_functions(wl, geo, g, ref, 1e-5)
+        check_rows(wl, geo, g, ref, range(n), 1e-5)
+        gap = np.isnan(f32["hphi"])
+        assert np.array_equal(np.isnan(g["hphi"]), gap)
+        d = np.linalg.norm(g["hphi"][~gap] - f32["hphi"][~gap]) / np.linalg.norm(f32["hphi"][~gap])
+        errs[(parts, "f32")] = d
+    assert errs[(3, "f32")] <= 2e-7, errs
+    assert errs[(3, "f32")] < errs[(2, "f32")], errs
+    f32_err = check_functions(wl, geo, f32, ref, 1e-5)
+    assert errs[3] <= 3 * f32_err + 1e-7, errs
+
+
+def test_split_bf16_option_errors():
+    import torch
+    from tests.lib_support import ensure_built
+    ensure_built()
+    wl = I.scaled("atoms64", 3, seed=2)
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   precision=lsw.LSW_FP32, device=0, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        with pytest.raises(lsw.LswError):
+            lsw.lsw_set_option(S.sys, "zsplit", 3)       # not a split-bfloat16 system
+    finally:
+        S.close()
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   precision=lsw.LSW_FP32_BF16X, device=0, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        with pytest.raises(lsw.LswError):
+            lsw.lsw_set_option(S.sys, "zsplit", 4)
+        lsw.lsw_set_option(S.sys, "zsplit", 3)
+        lsw.lsw_set_option(S.sys, "zsplit", 2)
+    finally:
+        S.close()

@@ -114,3 +114,42 @@ def test_atom_without_functions_and_empty_rows(ctx):
         assert np.array_equal(S.row_ptr, geo.row_ptr) and np.array_equal(S.col, geo.col)
     finally:
         S.close()
+
+
+def test_checkpoint_description_roundtrip(ctx, tmp_path):
+    # lsw_save without support functions writes the description; lsw_load rebuilds a
+    # system with the same keys, layout and pattern (same host arithmetic).
+    wl = I.scaled("atoms64", 9, seed=3)
+    S = host_system(wl, ctx, precision=lsw.LSW_FP32_BF16X)
+    path = str(tmp_path / "sys.lsw")
+    try:
+        lsw.lsw_save(S.sys, None, path)
+        T = lsw.lsw_load(ctx, path)
+        try:
+            lay_s = lsw.lsw_system_layout(S.sys)
+            lay_t = lsw.lsw_system_layout(T)
+            for x, y in zip(lay_s, lay_t):
+                assert np.array_equal(np.asarray(x), np.asarray(y))
+            rs, cs = lsw.lsw_pattern(S.sys)
+            rt, ct = lsw.lsw_pattern(T)
+            assert np.array_equal(rs, rt) and np.array_equal(cs, ct)
+            for a in range(len(wl.pos)):
+                for region in (lsw.LSW_REGION_L, lsw.LSW_REGION_LP):
+                    for part in (lsw.LSW_PART_COARSE, lsw.LSW_PART_FINE):
+                        assert np.array_equal(lsw.lsw_system_keys(S.sys, a, region, part),
+                                              lsw.lsw_system_keys(T, a, region, part))
+            with pytest.raises(lsw.LswError) as e:
+                lsw.lsw_load_phi(T, path, 64)               # no support functions saved
+            assert e.value.status == lsw.LSW_ERR_STATE
+        finally:
+            lsw.lsw_system_destroy(T)
+    finally:
+        S.close()
+    bad = tmp_path / "bad.lsw"
+    bad.write_bytes(b"not a checkpoint")
+    with pytest.raises(lsw.LswError) as e:
+        lsw.lsw_load(ctx, str(bad))
+    assert e.value.status == lsw.LSW_ERR_IO
+    with pytest.raises(lsw.LswError) as e:
+        lsw.lsw_load(ctx, str(tmp_path / "missing.lsw"))
+    assert e.value.status == lsw.LSW_ERR_IO
