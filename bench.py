@@ -534,7 +534,7 @@ def serving_main(args):
     from paper_1401_7441_gb300 import serving as SV
     from paper_1401_7441_gb300 import lsw
     reqs = SV.request_stream(args.requests, rate=20.0, atoms=(50, 5000), reuse_frac=0.3, seed=5005)
-    srv = SV.Server(budget_bytes=150e9, precision=lsw.LSW_FP32, streams=4, host_threads=8)
+    srv = SV.Server(budget_bytes=150e9, precision=lsw.LSW_FP32_BF16X, streams=4, host_threads=8)
     t0 = time.perf_counter()
     with ClockSampler(os.path.join(tempfile.gettempdir(), "lsw_clk_srv_%d.csv" % os.getpid())) as clk:
         res = srv.run(reqs, realtime=True)

@@ -701,9 +701,13 @@ __global__ void __launch_bounds__(256, 1) k_z_tc(HphiLaunch a) {
         const int c = tile * TILE + row;
         const bool ok = c < cols;
 #pragma unroll
-        for (int i = 0; i < tc::MAX_KH; ++i) {
-            const int k = k_lo + i;
-            xin[i] = (i < kh && ok && k < 2 * nz) ? LD(Bf, static_cast<int64_t>(k) * cols + c, 2LL * nz * cols) : 0.f;
+        for (int i0 = 0; i0 < tc::MAX_KH; i0 += 8) {
+            if (i0 >= kh) break;            // uniform: whole chunks of 8 past the half are skipped
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = k_lo + i0 + e;
+                xin[i0 + e] = (ok && k < 2 * nz) ? LD(Bf, static_cast<int64_t>(k) * cols + c, 2LL * nz * cols) : 0.f;
+            }
         }
     };
     load_in(blockIdx.x);
@@ -722,8 +726,15 @@ __global__ void __launch_bounds__(256, 1) k_z_tc(HphiLaunch a) {
         if (valid) {
             const int xo = c % X, yo = c / X;
             const int64_t vrow = (2LL * r.lo[1] - V_REACH + yo - a.vlo[1]) * a.vn[0] + (2LL * r.lo[0] - V_REACH + xo - a.vlo[0]);
-            for (int o = o_lo; o < min(o_lo + nh1, Z); ++o)
-                CPA(sV, o * TILE + row, sv_n, V, (jz0 + o) * vstride + vrow, a.v_n);
+            const int o1 = min(o_lo + nh1, Z);
+#ifdef LSW_CHECKED
+            for (int o = o_lo; o < o1; ++o) CPA(sV, o * TILE + row, sv_n, V, (jz0 + o) * vstride + vrow, a.v_n);
+#else
+            const float* vp = V + (jz0 + o_lo) * vstride + vrow;
+            float* sp = sV + o_lo * TILE + row;
+#pragma unroll 4
+            for (int o = o_lo; o < o1; ++o, vp += vstride, sp += TILE) cp_async(sp, vp);
+#endif
         }
         // inputs -> A1 parts (row `row`, k in this thread's half)
 #pragma unroll
@@ -792,13 +803,14 @@ __global__ void __launch_bounds__(256, 1) k_z_tc(HphiLaunch a) {
         }
         tc::fence_after();
         // result -> Bb (row j = b' nz' + b of the coarse z output, column c)
+        const int j1 = valid ? min(j_lo + nh2, 2 * nzp) : j_lo;    // rows this thread stores
         for (int ch = 0; ch < nh2; ch += 8) {
             float d[8];
             tc::tmem_ld8(tlane + j_lo + ch, d);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int j = j_lo + ch + e;
-                if (valid && j < 2 * nzp) ST(Bb, static_cast<int64_t>(j) * cols + c, 2LL * nzp * cols, d[e]);
+                if (j < j1) ST(Bb, static_cast<int64_t>(j) * cols + c, 2LL * nzp * cols, d[e]);
             }
         }
         tc::fence_before();
