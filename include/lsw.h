@@ -259,7 +259,8 @@ lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds,
 lsw_status lsw_save(lsw_system sys, const void* phi_dev, const char* path);
 
 /* Rebuild a saved system on `ctx` (same arithmetic as lsw_system_create, so keys,
- * layout and pattern are identical) and, if phi_dev is not NULL, copy the saved
+ * layout and pattern are identical; "zsplit" is restored, the other options take
+ * their defaults) and, if phi_dev is not NULL, copy the saved
  * support functions into it (device, total_L values; the file must hold them).  Pass
  * NULL first to learn total_L from lsw_system_layout, then lsw_load_phi.  Synchronous.
  * Errors: LSW_ERR_ARG, LSW_ERR_IO (unreadable or not a checkpoint), LSW_ERR_STATE (no
@@ -275,10 +276,12 @@ lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev);
 /* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
  * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8),
  * "zsplit" (LSW_FP32_BF16X systems only: 2 or 3 bfloat16 parts per FP32 operand of the
- * tensor-core z stage).
- * Errors: LSW_ERR_ARG (unknown name or value), LSW_ERR_STATE ("zsplit" on another
- * precision), LSW_ERR_UNSUPPORTED (3 parts do not fit a locreg's tile in shared memory;
- * the previous value stays). */
+ * tensor-core z stage), "xy_tc" (LSW_FP32_BF16X systems only: 1 runs the x and y passes
+ * of the plane kernels as split-bfloat16 tensor-core products as well; 0, the default,
+ * keeps them on the FMA units, which measured faster).
+ * Errors: LSW_ERR_ARG (unknown name or value), LSW_ERR_STATE ("zsplit" or "xy_tc" on
+ * another precision), LSW_ERR_UNSUPPORTED (the locregs do not fit the tensor-core tiles
+ * in shared memory; the previous value stays). */
 lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value);
 
 #ifdef __cplusplus

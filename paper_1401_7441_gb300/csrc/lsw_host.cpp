@@ -170,6 +170,7 @@ struct lsw_system_s {
     double h;
     int prec;              // storage / arithmetic type: LSW_FP64 or LSW_FP32
     int zsplit = 0;        // LSW_FP32_BF16X: bfloat16 parts of the tensor-core z stage
+    int xy_tc = 0;         // option "xy_tc": x, y passes on the tensor-core plane kernels
     size_t esize;
     int32_t n_atoms;
     std::vector<double> pos, r_loc, r_fine;
@@ -392,7 +393,8 @@ void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, siz
     *fwd = es * static_cast<size_t>(4 * r.n[1] * RS + 2 * r.n[1] * X);
     *z = es * static_cast<size_t>((2 * r.n[2] + Z) * zcols);
     const int64_t plA = std::max<int64_t>(Y * X, 4LL * r.np[1] * r.np[0]);
-    *bwd = es * static_cast<size_t>(plA + 2 * r.np[1] * X + 4 * r.n[1] * RS);
+    *bwd = es * static_cast<size_t>(plA + 2 * r.np[1] * X + 4 * r.n[1] * RS) +
+           static_cast<size_t>((4 * r.n[0] * r.n[1] + 15) / 16 * 16);   // + z-arm column flags
 }
 
 // Dynamic shared memory of the tensor-core z stage for a function record and `parts`
@@ -405,9 +407,34 @@ size_t ztc_smem(const FnRec& r, int parts) {
     const int64_t KA = std::max(K1, K2);
     return static_cast<size_t>(512 + parts * (128 * KA * 2 + N1 * K1 * 2 + N2 * K2 * 2) + Z * 128 * 4);
 }
-// Largest extents the tensor-core z stage takes (register window of half of K1 <= 64,
-// MMA N <= 256).
+// Dynamic shared memory of the tensor-core backward plane kernel (mirror of k_bwd_xy's
+// tensor-core layout: 512-byte header, Fy parts 128 x K1, Fx parts N2 x K2, one region
+// for the P operand / M1 operand / Gs, the D plane).
+size_t bwd_tc_smem(const FnRec& r, int parts) {
+    auto up16 = [](int64_t v) { return (v + 15) / 16 * 16; };
+    const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+    const int64_t K1 = up16(Y), N1 = up16(X), K2 = N1, N2 = up16(2 * r.np[0]);
+    const int64_t XR = up16(std::max<int64_t>(std::max<int64_t>(parts * N1 * K1 * 2, parts * 128 * K2 * 2), 16LL * r.np[1] * r.np[0]));
+    const int64_t RS = r.n[0] | 1;
+    return static_cast<size_t>(512 + parts * 128 * K1 * 2 + parts * N2 * K2 * 2 + XR + 4 * r.n[1] * RS * 4 +
+                               (4 * r.n[0] * r.n[1] + 15) / 16 * 16);
+}
+// Dynamic shared memory of the tensor-core forward plane kernel (mirror of k_fwd_xy_tc:
+// 512-byte header, Fy parts 128 x K1, Fx parts N2 x K2, one region for the D-plane
+// operand and then the M1 operand).
+size_t fwd_tc_smem(const FnRec& r, int parts) {
+    auto up16 = [](int64_t v) { return (v + 15) / 16 * 16; };
+    const int64_t X = 2 * r.n[0] + 29;
+    const int64_t K1 = up16(2 * r.n[1]), N1 = up16(2 * r.n[0]), K2 = N1, N2 = up16(X);
+    return static_cast<size_t>(512 + parts * 128 * K1 * 2 + parts * N2 * K2 * 2 +
+                               parts * std::max<int64_t>(N1 * K1 * 2, 128 * K2 * 2));
+}
+// Largest extents the tensor-core kernels take: z stage (register window of half of
+// K1 <= 64, MMA N <= 256); plane kernels (MMA M = 128 rows: 2 n_y' and Y <= 128, N <= 128).
 bool ztc_fits(const FnRec& r) { return r.n[2] <= 64 && 2 * r.np[2] <= 256; }
+bool xytc_fits(const FnRec& r) {
+    return 2 * r.n[0] + 29 <= 128 && 2 * r.n[1] + 29 <= 128 && 2 * r.np[1] <= 128 && 2 * r.np[0] <= 128;
+}
 
 lsw_status build_plans(lsw_system_s* s) {
     const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
@@ -453,6 +480,8 @@ lsw_status build_plans(lsw_system_s* s) {
             o += align64(2LL * r.np[2] * Y * X);
             recs[f].ws_G = o;
             o += align64(8LL * r.np[0] * r.np[1] * r.np[2]);
+            recs[f].ws_Gf = o;
+            o += align64((4LL * r.n[0] * r.n[1] + static_cast<int64_t>(s->esize) - 1) / static_cast<int64_t>(s->esize));
         }
         ws_max = std::max(ws_max, o);
         for (int64_t f = f0; f < f0 + b.nfn; ++f) {
@@ -472,17 +501,25 @@ lsw_status build_plans(lsw_system_s* s) {
             pass_smem(r, s->esize, zcols, &a1, &a2, &a3);
             p.smem_fwd = std::max(p.smem_fwd, a1);
             p.smem_z = std::max(p.smem_z, a2);
+            p.smem_kin = std::max(p.smem_kin, static_cast<size_t>(2 * r.n[2] * 128) * (p.prec == 0 ? 8 : 4));
             p.smem_bwd = std::max(p.smem_bwd, a3);
             if (s->zsplit) {
                 if (!ztc_fits(r))
-                    return fail(LSW_ERR_UNSUPPORTED, "locreg z extent %d / %d too large for the tensor-core z stage",
-                                r.n[2], r.np[2]);
+                    return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core kernels");
                 p.smem_ztc = std::max(p.smem_ztc, ztc_smem(r, s->zsplit));
+                if (s->xy_tc) {
+                    if (!xytc_fits(r))
+                        return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core plane kernels");
+                    p.smem_bwd_tc = std::max(p.smem_bwd_tc, bwd_tc_smem(r, s->zsplit));
+                    p.smem_fwd_tc = std::max(p.smem_fwd_tc, fwd_tc_smem(r, s->zsplit));
+                }
             }
         }
         p.zsplit = s->zsplit;
+        p.xy_tc = s->zsplit ? s->xy_tc : 0;
         if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem ||
-            p.smem_ztc > s->ctx->max_smem)
+            p.smem_ztc > s->ctx->max_smem || p.smem_kin > s->ctx->max_smem || p.smem_bwd_tc + BWD_STATIC_SMEM > s->ctx->max_smem ||
+            p.smem_fwd_tc > s->ctx->max_smem)
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles (%zu/%zu/%zu/%zu > %zu bytes)",
                         p.smem_fwd, p.smem_z, p.smem_bwd, p.smem_ztc, s->ctx->max_smem);
         s->batches.push_back(b);
@@ -1095,7 +1132,9 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
             const int64_t sD = align64(8LL * r.n[0] * r.n[1] * r.n[2]);
             const int64_t sR = align64(2LL * r.n[2] * Y * X) + align64(2LL * r.np[2] * Y * X) +
-                               align64(8LL * r.np[0] * r.np[1] * r.np[2]);
+                               align64(8LL * r.np[0] * r.np[1] * r.np[2]) +
+                               align64((4LL * r.n[0] * r.n[1] + static_cast<int64_t>(sys->esize) - 1) /
+                                       static_cast<int64_t>(sys->esize));
             if (needD + sD + needR + sR > cap) break;
             recs[nb] = r;
             sizeD[nb] = sD;
@@ -1129,6 +1168,8 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             o += align64(2LL * r.np[2] * Y * X);
             recs[k].ws_G = o;
             o += align64(8LL * r.np[0] * r.np[1] * r.np[2]);
+            recs[k].ws_Gf = o;
+            o += align64((4LL * r.n[0] * r.n[1] + static_cast<int64_t>(sys->esize) - 1) / static_cast<int64_t>(sys->esize));
             const LocregHost& Lh = sys->L[r.atom];
             const LocregHost& Ph = sys->Lp[r.atom];
             p.max_nz = std::max(p.max_nz, r.n[2]);
@@ -1144,16 +1185,25 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             pass_smem(r, sys->esize, zcols, &a1, &a2, &a3);
             p.smem_fwd = std::max(p.smem_fwd, a1);
             p.smem_z = std::max(p.smem_z, a2);
+            p.smem_kin = std::max(p.smem_kin, static_cast<size_t>(2 * r.n[2] * 128) * (p.prec == 0 ? 8 : 4));
             p.smem_bwd = std::max(p.smem_bwd, a3);
             if (sys->zsplit) {
                 if (!ztc_fits(r))
-                    return fail(LSW_ERR_UNSUPPORTED, "locreg z extent too large for the tensor-core z stage");
+                    return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core kernels");
                 p.smem_ztc = std::max(p.smem_ztc, ztc_smem(r, sys->zsplit));
+                if (sys->xy_tc) {
+                    if (!xytc_fits(r))
+                        return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core plane kernels");
+                    p.smem_bwd_tc = std::max(p.smem_bwd_tc, bwd_tc_smem(r, sys->zsplit));
+                    p.smem_fwd_tc = std::max(p.smem_fwd_tc, fwd_tc_smem(r, sys->zsplit));
+                }
             }
         }
         p.zsplit = sys->zsplit;
+        p.xy_tc = sys->zsplit ? sys->xy_tc : 0;
         if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > sys->ctx->max_smem ||
-            p.smem_ztc > sys->ctx->max_smem)
+            p.smem_ztc > sys->ctx->max_smem || p.smem_kin > sys->ctx->max_smem || p.smem_bwd_tc + BWD_STATIC_SMEM > sys->ctx->max_smem ||
+            p.smem_fwd_tc > sys->ctx->max_smem)
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
         // records into the head of the scratch (pageable source: reusable on return)
         CUDA_TRY(cudaMemcpyAsync(scratch, recs, nb * sizeof(FnRec), cudaMemcpyHostToDevice, st));
@@ -1395,6 +1445,22 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
             const std::string msg = g_err;
             sys->zsplit = old;
             if (build_plans(sys) != LSW_OK) return fail(LSW_ERR_STATE, "lsw_set_option: zsplit: cannot restore plans");
+            return fail(e, "%s", msg.c_str());
+        }
+        return LSW_OK;
+    }
+    if (std::strcmp(name, "xy_tc") == 0) {
+        if (value != 0 && value != 1) return fail(LSW_ERR_ARG, "lsw_set_option: xy_tc %lld", static_cast<long long>(value));
+        if (!sys->zsplit) return fail(LSW_ERR_STATE, "lsw_set_option: xy_tc needs an LSW_FP32_BF16X system");
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        const int old = sys->xy_tc;
+        sys->xy_tc = static_cast<int>(value);
+        lsw_status e = build_plans(sys);
+        if (e != LSW_OK) {
+            const std::string msg = g_err;
+            sys->xy_tc = old;
+            if (build_plans(sys) != LSW_OK) return fail(LSW_ERR_STATE, "lsw_set_option: xy_tc: cannot restore plans");
             return fail(e, "%s", msg.c_str());
         }
         return LSW_OK;

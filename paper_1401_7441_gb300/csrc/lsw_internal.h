@@ -55,6 +55,8 @@ struct FnRec {
     int32_t lo[3], n[3], lop[3], np[3];
     int64_t off_phi, off_hphi;
     int64_t ws_D, ws_Bf, ws_Bb, ws_G;    // element offsets inside the batch workspace
+    int64_t ws_Gf;                       // element offset of the z-arm column flags (bytes
+                                         // [4][n_x n_y]: 1 where the D column pair is nonzero)
 };
 
 // One H/S work item: tile `tile`, functions listA[a0 .. a0+na) x listB[b0 .. b0+nb).
@@ -89,7 +91,12 @@ struct HphiLaunch {
     int zcols;                   // columns per CTA of the z stage
     int zsplit;                  // 0: z stage on FMA units; 2 or 3: bfloat16 parts per
                                  // FP32 operand of the tensor-core z stage
+    int xy_tc;                   // 1: the x, y passes run on the tensor-core plane kernels too
+                                 // (with zsplit parts); 0: on the FMA plane kernels
     size_t smem_ztc;             // dynamic shared memory of the tensor-core z stage
+    size_t smem_bwd_tc;          // dynamic shared memory of the tensor-core plane kernel
+    size_t smem_fwd_tc;          // dynamic shared memory of the tensor-core forward plane kernel
+    size_t smem_kin;             // dynamic shared memory of the kinetic z-arm kernel
     const AtomRec* atoms;
     const Seg* seg;
     const int32_t* rowptr;

@@ -825,39 +825,194 @@ __global__ void __launch_bounds__(256, 1) k_z_tc(HphiLaunch a) {
     if (warp == 0) tc::tmem_free(tmem, ncols);
 }
 
+// ---------------------------------------------------------------- forward x, y on tensor cores
+//
+// k_fwd_xy as two band-Toeplitz tensor-core products per (z, b_z) plane with split-
+// bfloat16 operands (NS parts) and FP32 accumulation in tensor memory:
+//   M1[y'][i] = sum_k Fy[y'][k] Din[k][i],   k = by n_y + y,  i = bx n_x + q,  Fy[y'][k] = F_by[y' - 2y]
+//   U[y'][x'] = sum_i M1[y'][i] Fx[x'][i],   Fx[x'][i] = F_bx[x' - 2q]
+// with Din[k][i] = D[bx + 2 by][z][y][q] of this plane; U is the plane of Bf.  Thread
+// (warp w, lane l) owns row y' = 32 (w mod 4) + l of both products and half w / 4 of each
+// K or N range.  256 threads; the operands take about 90 KB, so two blocks share an SM.
+template <int NS>
+__global__ void __launch_bounds__(256) k_fwd_xy_tc(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 2;
+    int* st = a.status;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const FnRec r = a.fn[blockIdx.y];
+    const int z = blockIdx.x >> 1, bz = blockIdx.x & 1;
+    if (z >= r.n[2]) return;   // uniform over the CTA, before any allocation
+    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
+    const int X = 2 * nx + 29, Y = 2 * ny + 29;
+    const int K1 = (2 * ny + 15) & ~15, N1 = (2 * nx + 15) & ~15, K2 = N1, N2 = (X + 15) & ~15;
+    const int FY_PART = 128 * K1 * 2, FX_PART = N2 * K2 * 2, P_PART = N1 * K1 * 2, M_PART = 128 * K2 * 2;
+    unsigned char* sFy = smem_raw + tc::HEAD;
+    unsigned char* sFx = sFy + NS * FY_PART;
+    unsigned char* sXr = sFx + NS * FX_PART;
+    const int64_t room = static_cast<int64_t>(a.smem_fwd_tc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = (warp & 3) * 32 + lane, half = warp >> 2;
+    const uint32_t mbar = tc::saddr(smem_raw);
+    float* taps = reinterpret_cast<float*>(smem_raw + 16);
+    if (warp == 0) tc::tmem_alloc(tc::saddr(smem_raw + 8), 128);
+    if (threadIdx.x == 32) tc::mbar_init(mbar);
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + 2 * FWD_TAPS) {
+        const int i = threadIdx.x - 64;
+        taps[i] = Tab<float>::fwd(i / FWD_TAPS, i % FWD_TAPS);
+    }
+    __syncthreads();
+    // Fy[y'][k] = F_by[y' - 2y], k = by n_y + y
+    for (int ci = threadIdx.x; ci < 128 * (K1 >> 3); ci += blockDim.x) {
+        const int yo = ci / (K1 >> 3), k0 = (ci - yo * (K1 >> 3)) * 8;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + e, by = k >= ny ? 1 : 0, y = k - by * ny, m = yo - 2 * y;
+            x[e] = (yo < Y && k < 2 * ny && m >= 0 && m < FWD_TAPS) ? taps[by * FWD_TAPS + m] : 0.f;
+        }
+        tc::put8<NS>(sFy, FY_PART, tc::core_off(yo, k0, K1), x, st, room - (sFy - smem_raw));
+    }
+    // Fx[x'][i] = F_bx[x' - 2q], i = bx n_x + q
+    for (int ci = threadIdx.x; ci < N2 * (K2 >> 3); ci += blockDim.x) {
+        const int xo = ci / (K2 >> 3), i0 = (ci - xo * (K2 >> 3)) * 8;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = i0 + e, bx = i >= nx ? 1 : 0, q = i - bx * nx, m = xo - 2 * q;
+            x[e] = (xo < X && i < 2 * nx && m >= 0 && m < FWD_TAPS) ? taps[bx * FWD_TAPS + m] : 0.f;
+        }
+        tc::put8<NS>(sFx, FX_PART, tc::core_off(xo, i0, K2), x, st, room - (sFx - smem_raw));
+    }
+    // Din[k][i] as the N1 x K1 operand (row i, column k); consecutive threads take
+    // consecutive q (contiguous in D)
+    const float* D = static_cast<const float*>(a.ws) + r.ws_D;
+    const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
+    for (int ci = threadIdx.x; ci < N1 * (K1 >> 3); ci += blockDim.x) {
+        const int c = ci / N1, i = ci - c * N1, k0 = c * 8;
+        const int bx = i >= nx ? 1 : 0, q = i - bx * nx;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + e, by = k >= ny ? 1 : 0, y = k - by * ny;
+            x[e] = (i < 2 * nx && k < 2 * ny)
+                       ? LD(D, (bx + 2 * by + 4 * bz) * plane + (static_cast<int64_t>(z) * ny + y) * nx + q, 8 * plane)
+                       : 0.f;
+        }
+        tc::put8<NS>(sXr, P_PART, tc::core_off(i, k0, K1), x, st, room - (sXr - smem_raw));
+    }
+    tc::fence_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + 8);
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    if (threadIdx.x == 0) {
+        const uint32_t id = tc::idesc(128, N1);
+        for (int k = 0; k < (K1 >> 4); ++k)
+#pragma unroll
+            for (int t = 0; t < tc::Terms<NS>::n; ++t)
+                tc::mma(tmem, tc::sdesc(tc::saddr(sFy + tc::Terms<NS>::a(t) * FY_PART + k * 256), K1),
+                        tc::sdesc(tc::saddr(sXr + tc::Terms<NS>::b(t) * P_PART + k * 256), K1), id, k > 0 || t > 0);
+        tc::commit(mbar);
+    }
+    bool ok = tc::mbar_wait(mbar, 0);
+    if (__syncthreads_and(ok)) {
+        tc::fence_after();
+        for (int c = half; c < (N1 >> 3); c += 2) {
+            float u[8];
+            tc::tmem_ld8(tlane + c * 8, u);
+            tc::put8<NS>(sXr, M_PART, tc::core_off(row, c * 8, K2), u, st, room - (sXr - smem_raw));
+        }
+        tc::fence_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t id = tc::idesc(128, N2);
+            for (int k = 0; k < (K2 >> 4); ++k)
+#pragma unroll
+                for (int t = 0; t < tc::Terms<NS>::n; ++t)
+                    tc::mma(tmem, tc::sdesc(tc::saddr(sXr + tc::Terms<NS>::a(t) * M_PART + k * 256), K2),
+                            tc::sdesc(tc::saddr(sFx + tc::Terms<NS>::b(t) * FX_PART + k * 256), K2), id,
+                            k > 0 || t > 0);
+            tc::commit(mbar);
+        }
+        ok = tc::mbar_wait(mbar, 1);
+        if (__syncthreads_and(ok)) {
+            tc::fence_after();
+            float* Bf = static_cast<float*>(a.ws) + r.ws_Bf + (static_cast<int64_t>(bz) * nz + z) * Y * X;
+            [[maybe_unused]] const int64_t bf_room = 2LL * nz * Y * X - (static_cast<int64_t>(bz) * nz + z) * Y * X;
+            for (int c = half; c < (N2 >> 3); c += 2) {
+                float u[8];
+                tc::tmem_ld8(tlane + c * 8, u);
+                if (row < Y) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if (c * 8 + e < X) ST(Bf, static_cast<int64_t>(row) * X + c * 8 + e, bf_room, u[e]);
+                }
+            }
+        } else if (threadIdx.x == 0) {
+            atomicOr(st, ST_WAIT_TIMEOUT);
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(st, ST_WAIT_TIMEOUT);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_free(tmem, 128);
+}
+
 // ---------------------------------------------------------------- kinetic z arm
 
 // Per (x, y) column of the L box and type pair (t, t + 4): the kinetic arm along z,
 // written to G on the L' box column (G holds only this arm; the backward plane kernel
-// adds the rest).  Runs before the backward plane kernel.
+// adds the rest).  Runs before the backward plane kernel.  The column pair is staged in
+// shared memory; a column pair that is zero (outside the L sphere, or wavelet types off
+// the fine region) only clears its flag, and the plane kernel then skips its G.
 template <class T>
 __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 5;
     int* st = a.status;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const FnRec r = a.fn[blockIdx.y];
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int nxp = r.np[0], nyp = r.np[1], nzp = r.np[2];
     const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;   // column (x, y) of the L box
+    const int pn = nx * ny;
+    if (static_cast<int>(blockIdx.x) * 128 >= pn) return;
+    const int t = threadIdx.x;
+    const int c = blockIdx.x * 128 + t;                    // column (x, y) of the L box
     const int tb = blockIdx.z;                             // type pair (tb, tb + 4)
+    T* col = reinterpret_cast<T*>(smem_raw);               // [2][nz][128]: this thread's column pair
+    [[maybe_unused]] const int64_t col_n = static_cast<int64_t>(a.smem_kin / sizeof(T));
+    unsigned char* flag = reinterpret_cast<unsigned char*>(static_cast<T*>(a.ws) + r.ws_Gf) + tb * pn;
     T ekin_t = 0;
-    if (c < nx * ny) {
+    if (c < pn) {
+        const T* D = static_cast<const T*>(a.ws) + r.ws_D;
+        const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
+        for (int q = 0; q < nz; ++q) {
+            CPA(col, q * 128 + t, col_n, D, tb * plane + static_cast<int64_t>(q) * pn + c, 8 * plane);
+            CPA(col, (nz + q) * 128 + t, col_n, D, (tb + 4) * plane + static_cast<int64_t>(q) * pn + c, 8 * plane);
+        }
+        cp_wait();
+        bool nonzero = false;
+        for (int q = 0; q < 2 * nz; ++q) nonzero |= LD(col, q * 128 + t, col_n) != T(0);
+        ST(flag, c, 4LL * pn, nonzero ? 1 : 0);
         const int y = c / nx, x = c - y * nx;
         const int xb = x - dx, yb = y - dy;             // the same column in the L' box
-        if (xb >= 0 && xb < nxp && yb >= 0 && yb < nyp) {
-            const T* D = static_cast<const T*>(a.ws) + r.ws_D;
+        if (nonzero && xb >= 0 && xb < nxp && yb >= 0 && yb < nyp) {
             T* G = static_cast<T*>(a.ws) + r.ws_G;
-            const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
-            const int pn = nx * ny;
             const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
             const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
             const int64_t gcol = static_cast<int64_t>(yb) * nxp + xb;
             const T ks = static_cast<T>(a.kin_scale);
             for (int b0 = 0; b0 < nzp; b0 += BB) {
                 T k0[KW], k1[KW], o0[BB], o1[BB];
-                win(k0, D, tb * plane + c, pn, b0 + dz - KIN_HALF, nz, 8 * plane, st);
-                win(k1, D, (tb + 4) * plane + c, pn, b0 + dz - KIN_HALF, nz, 8 * plane, st);
+                swin(k0, col, t, 128, b0 + dz - KIN_HALF, nz, col_n, st);
+                swin(k1, col, nz * 128 + t, 128, b0 + dz - KIN_HALF, nz, col_n, st);
                 kin_block(k0, k1, o0, o1);
 #pragma unroll
                 for (int j = 0; j < BB; ++j) {
@@ -893,8 +1048,133 @@ constexpr int BWD_MAX_TASKS = 2048;
 #define LSW_BWD_MIN_BLOCKS 2      // resident blocks per SM the FP32 version is compiled for
 #endif
 
-template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) k_bwd_xy(HphiLaunch a) {
+// Potential part of the backward plane kernel on the tensor cores (the two products
+// described at k_bwd_xy): builds the filter operands Fy (128 x K1) and Fx (N2 x K2) and
+// the plane operand P (N1 x K1: row x', column y') from Bb, runs both products and writes
+// Gs[bx + 2 by][b][b2] for every b < n_y', b2 < n_x'.  512 threads.  Returns false (for
+// every thread) if a completion wait ran out.
+template <int NS>
+__device__ bool bwd_tc_potential(const float* Bb, [[maybe_unused]] int64_t bb_room, int X, int Y, int nyp, int nxp,
+                                 int dx, int dy, int K1, int N1, int K2, int N2, int FY_PART, int FX_PART,
+                                 [[maybe_unused]] int XR, unsigned char* sFy, unsigned char* sFx, unsigned char* sXr,
+                                 float* Gs, unsigned char* smem_raw, int64_t room, int* st) {
+    [[maybe_unused]] int* ST_ = st;
+    [[maybe_unused]] constexpr int KID = 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = (warp & 3) * 32 + lane, part = warp >> 2;
+    const int P_PART = N1 * K1 * 2, M_PART = 128 * K2 * 2;
+    const float* taps = reinterpret_cast<const float*>(smem_raw + 16);
+    const uint32_t mbar = tc::saddr(smem_raw);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + 8);
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    // Fy[j][y'] = F_by[y' - 2 (b + dy)], j = by n_y' + b
+    for (int ci = threadIdx.x; ci < 128 * (K1 >> 3); ci += blockDim.x) {
+        const int j = ci / (K1 >> 3), y0 = (ci - j * (K1 >> 3)) * 8;
+        const int by = j >= nyp ? 1 : 0, b = j - by * nyp;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int m = y0 + e - 2 * (b + dy);
+            x[e] = (j < 2 * nyp && y0 + e < Y && m >= 0 && m < FWD_TAPS) ? taps[by * FWD_TAPS + m] : 0.f;
+        }
+        tc::put8<NS>(sFy, FY_PART, tc::core_off(j, y0, K1), x, st, room - (sFy - smem_raw));
+    }
+    // Fx[i][x'] = F_bx[x' - 2 (b2 + dx)], i = bx n_x' + b2
+    for (int ci = threadIdx.x; ci < N2 * (K2 >> 3); ci += blockDim.x) {
+        const int i = ci / (K2 >> 3), x0 = (ci - i * (K2 >> 3)) * 8;
+        const int bx = i >= nxp ? 1 : 0, b2 = i - bx * nxp;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int m = x0 + e - 2 * (b2 + dx);
+            x[e] = (i < 2 * nxp && x0 + e < X && m >= 0 && m < FWD_TAPS) ? taps[bx * FWD_TAPS + m] : 0.f;
+        }
+        tc::put8<NS>(sFx, FX_PART, tc::core_off(i, x0, K2), x, st, room - (sFx - smem_raw));
+    }
+    // P[x'][y'] = Bb plane (y', x'); consecutive threads take consecutive x' (coalesced)
+    for (int ci = threadIdx.x; ci < N1 * (K1 >> 3); ci += blockDim.x) {
+        const int c = ci / N1, xo = ci - c * N1, y0 = c * 8;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            x[e] = (xo < X && y0 + e < Y) ? LD(Bb, static_cast<int64_t>(y0 + e) * X + xo, bb_room) : 0.f;
+        tc::put8<NS>(sXr, P_PART, tc::core_off(xo, y0, K1), x, st, room - (sXr - smem_raw));
+    }
+    tc::fence_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x == 0) {
+        const uint32_t id = tc::idesc(128, N1);
+        for (int k = 0; k < (K1 >> 4); ++k)
+#pragma unroll
+            for (int t = 0; t < tc::Terms<NS>::n; ++t)
+                tc::mma(tmem, tc::sdesc(tc::saddr(sFy + tc::Terms<NS>::a(t) * FY_PART + k * 256), K1),
+                        tc::sdesc(tc::saddr(sXr + tc::Terms<NS>::b(t) * P_PART + k * 256), K1), id, k > 0 || t > 0);
+        tc::commit(mbar);
+    }
+    bool ok = tc::mbar_wait(mbar, 0);
+    if (!__syncthreads_and(ok)) return false;
+    tc::fence_after();
+    // M1 row `row` -> operand of the second product (the P operand is dead)
+    for (int c = part; c < (N1 >> 3); c += 4) {
+        float u[8];
+        tc::tmem_ld8(tlane + c * 8, u);
+        tc::put8<NS>(sXr, M_PART, tc::core_off(row, c * 8, K2), u, st, room - (sXr - smem_raw));
+    }
+    tc::fence_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x == 0) {
+        const uint32_t id = tc::idesc(128, N2);
+        for (int k = 0; k < (K2 >> 4); ++k)
+#pragma unroll
+            for (int t = 0; t < tc::Terms<NS>::n; ++t)
+                tc::mma(tmem, tc::sdesc(tc::saddr(sXr + tc::Terms<NS>::a(t) * M_PART + k * 256), K2),
+                        tc::sdesc(tc::saddr(sFx + tc::Terms<NS>::b(t) * FX_PART + k * 256), K2), id, k > 0 || t > 0);
+        tc::commit(mbar);
+    }
+    ok = tc::mbar_wait(mbar, 1);
+    if (!__syncthreads_and(ok)) return false;
+    tc::fence_after();
+    // Q row `row` -> Gs (the M1 operand is dead)
+    const int by = row >= nyp ? 1 : 0, b = row - by * nyp;
+    [[maybe_unused]] const int64_t gs_n = 4LL * nyp * nxp;
+    for (int c = part; c < (N2 >> 3); c += 4) {
+        float q[8];
+        tc::tmem_ld8(tlane + c * 8, q);
+        if (row < 2 * nyp) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = c * 8 + e;
+                if (i < 2 * nxp) {
+                    const int bx = i >= nxp ? 1 : 0, b2 = i - bx * nxp;
+                    ST(Gs, ((bx + 2 * by) * nyp + b) * nxp + b2, gs_n, q[e]);
+                }
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return true;
+}
+
+// NS = 0: the transposed y and x filters run on the FMA units (256 threads, several
+// blocks per SM).  NS = 2, 3 (FP32 only): they run as two band-Toeplitz tensor-core
+// products per plane with split-bfloat16 operands (NS parts) and FP32 accumulation in
+// tensor memory, as in k_z_tc (512 threads, one block per SM):
+//   M1[j][x'] = sum_y' Fy[j][y'] P[y'][x'],   j = by n_y' + b,  Fy[j][y'] = F_by[y' - 2(b + dy)]
+//   Q[j][i]   = sum_x' M1[j][x'] Fx[i][x'],   i = bx n_x' + b2, Fx[i][x'] = F_bx[x' - 2(b2 + dx)]
+// with P the plane of Bb; thread (warp w, lane l) owns row j = 32 (w mod 4) + l of both
+// products and quarter w / 4 of each K or N range.
+template <class T, int NS>
+__global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1))
+    k_bwd_xy(HphiLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 4;
     int* st = a.status;
@@ -916,11 +1196,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
     const int dx = r.lop[0] - r.lo[0], dy = r.lop[1] - r.lo[1], dz = r.lop[2] - r.lo[2];
     const int RS = nx | 1;
     const int plA = max(Y * X, 4 * nyp * nxp);
-    T* pl = sm;                         // [Y][X], later Gs [4][nyp][nxp]
-    T* Gs = sm;
-    T* mid = sm + plA;                  // [2][nyp][X]
-    T* Dp = mid + 2 * nyp * X;          // [4][ny][RS] D plane at zL = zb + dz
-    const int64_t smem_n = static_cast<int64_t>(a.smem_bwd / sizeof(T));
+    // FMA layout: pl [Y][X] (later Gs [4][nyp][nxp]), mid [2][nyp][X], Dp [4][ny][RS]
+    // tensor-core layout: header, Fy parts, Fx parts, a region holding the P operand, then
+    // the M1 operand, then Gs; Dp
+    const int K1 = (Y + 15) & ~15, N1 = (X + 15) & ~15, K2 = N1, N2 = (2 * nxp + 15) & ~15;
+    const int FY_PART = 128 * K1 * 2, FX_PART = N2 * K2 * 2, P_PART = N1 * K1 * 2, M_PART = 128 * K2 * 2;
+    const int XR = (max(max(NS * P_PART, NS * M_PART), 16 * nyp * nxp) + 15) & ~15;
+    unsigned char* sFy = smem_raw + tc::HEAD;
+    unsigned char* sFx = sFy + NS * FY_PART;
+    unsigned char* sXr = sFx + NS * FX_PART;
+    T* pl = sm;
+    T* Gs = NS ? reinterpret_cast<T*>(sXr) : sm;
+    T* mid = sm + plA;
+    T* Dp = NS ? reinterpret_cast<T*>(sXr + XR) : mid + 2 * nyp * X;
+    const int64_t smem_n = static_cast<int64_t>((NS ? a.smem_bwd_tc : a.smem_bwd) / sizeof(T));
+    if constexpr (NS > 0) {
+        if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(tc::saddr(smem_raw + 8), 128);
+        if (threadIdx.x == 32) tc::mbar_init(tc::saddr(smem_raw));
+        float* taps = reinterpret_cast<float*>(smem_raw + 16);
+        if (threadIdx.x >= 64 && threadIdx.x < 64 + 2 * FWD_TAPS) {
+            const int i = threadIdx.x - 64;
+            taps[i] = Tab<float>::fwd(i / FWD_TAPS, i % FWD_TAPS);
+        }
+    }
     const int zL = zb + dz;
     const bool dplane = zL >= 0 && zL < nz;
     if (threadIdx.x == 0) {
@@ -955,11 +1253,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
     }
     const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
     const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
-    for (int i = threadIdx.x; i < Y * X; i += blockDim.x) CPA(pl, i, smem_n, Bb, i, bb_room);
+    if constexpr (NS == 0)
+        for (int i = threadIdx.x; i < Y * X; i += blockDim.x) CPA(pl, i, smem_n, Bb, i, bb_room);
     const T* D = static_cast<const T*>(a.ws) + r.ws_D;
     const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
     const int pn = nx * ny;
-    const int64_t dp_n = smem_n - plA - 2LL * nyp * X;
+    const int64_t dp_n = smem_n - (reinterpret_cast<unsigned char*>(Dp) - smem_raw) / static_cast<int64_t>(sizeof(T));
     if (dplane) {
         const FastDiv fd_pn(pn), fd_nx(nx);
         for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
@@ -968,6 +1267,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
             CPA(Dp, (tb * ny + y) * RS + x, dp_n, D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem,
                 8 * plane);
         }
+    }
+    // z-arm column flags of the L box (written by k_kin_z), 4 bytes per copy
+    uint32_t* gfl = reinterpret_cast<uint32_t*>(Dp + 4 * ny * RS);
+    [[maybe_unused]] const int64_t gfl_n = (smem_n * static_cast<int64_t>(sizeof(T)) -
+                                            (reinterpret_cast<unsigned char*>(gfl) - smem_raw)) / 4;
+    {
+        const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(static_cast<const T*>(a.ws) + r.ws_Gf);
+        for (int i = threadIdx.x; i < pn; i += blockDim.x) CPA(gfl, i, gfl_n, gsrc, i, pn);
     }
     cp_wait();
     __syncthreads();
@@ -989,7 +1296,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
     const T ks = static_cast<T>(a.kin_scale);
     T ekin_t = 0;
     const int ylo_ = ylo, yhi_ = yhi;
+    if constexpr (NS > 0) {
+        // ---- potential part on the tensor cores -> Gs (every row and column of the plane)
+        if (yhi_ >= 0 && !bwd_tc_potential<NS>(reinterpret_cast<const float*>(Bb), bb_room, X, Y, nyp, nxp, dx, dy,
+                                                K1, N1, K2, N2, FY_PART, FX_PART, XR, sFy, sFx, sXr,
+                                                reinterpret_cast<float*>(Gs), smem_raw, smem_n * 4, st)) {
+            if (threadIdx.x == 0) atomicOr(st, ST_WAIT_TIMEOUT);
+        }
+    }
     if (yhi_ >= 0) {
+      if constexpr (NS == 0) {
         // ---- y pass: columns x', blocks of NB rows b within [ylo, yhi]
         const int nbb = (yhi_ - ylo_ + NB) / NB;
         {
@@ -1040,7 +1356,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
                 }
             }
         }
+      }
         if (dplane) {
+            int nt;
             __syncthreads();
             if (threadIdx.x == 0) ntask = 0;
             __syncthreads();
@@ -1130,6 +1448,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
     // ---- compress: members of this plane -> H phi (plus the z arm left in G by k_kin_z)
     if (yhi_ >= 0) {
         const T* G = static_cast<const T*>(a.ws) + r.ws_G;
+        const unsigned char* gflag = reinterpret_cast<const unsigned char*>(gfl);   // staged above
         const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
         T* out = static_cast<T*>(a.hphi) + r.off_hphi;
         const int64_t out_room = a.hphi_n - r.off_hphi;
@@ -1143,7 +1462,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
                 for (int xb = rx0[b] + lane; xb <= rx1[b]; xb += 32) {
                     const int x = xb + dx;
                     T v = LD(Gs, static_cast<int64_t>(b) * nxp + xb, gs_n);
-                    if (yin && x >= 0 && x < nx) v += LD(G, grow + xb, 8 * gplane);
+                    if (yin && x >= 0 && x < nx && LD(gflag, y * nx + x, 4LL * pn)) v += LD(G, grow + xb, 8 * gplane);
                     ST(out, roff[b] + (xb - rx0[b]), out_room, v);
                 }
             }
@@ -1160,7 +1479,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
                         const int t = tb + 4 * bz;
                         if (t == 0) continue;
                         T v = LD(Gs, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, gs_n);
-                        if (zin) v += LD(G, t * gplane + grow + xb, 8 * gplane);
+                        if (zin && LD(gflag, (t & 3) * pn + y * nx + x, 4LL * pn)) v += LD(G, t * gplane + grow + xb, 8 * gplane);
                         ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + fs.off + (xb - fs.x0), out_room, v);
                     }
                 }
@@ -1169,6 +1488,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1) 
     }
     const double ekin = warp_sum(static_cast<double>(ekin_t));
     if ((threadIdx.x & 31) == 0 && ekin != 0.0) atomicAdd(a.e_kin + r.f, ekin);
+    if constexpr (NS > 0) {
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if ((threadIdx.x >> 5) == 0) tc::tmem_free(*reinterpret_cast<volatile uint32_t*>(smem_raw + 8), 128);
+    }
 }
 
 // ---------------------------------------------------------------- sparse H / S
@@ -1489,8 +1814,11 @@ cudaError_t configure_kernels(size_t max_smem) {
     }
     SETMAX(k_fwd_xy<double>) SETMAX(k_fwd_xy<float>)
     SETMAX(k_z<double>) SETMAX(k_z<float>)
+    SETMAX(k_kin_z<double>) SETMAX(k_kin_z<float>)
     SETMAX(k_z_tc<2>) SETMAX(k_z_tc<3>)
-    SETMAX(k_bwd_xy<double>) SETMAX(k_bwd_xy<float>)
+    SETMAX(k_fwd_xy_tc<2>) SETMAX(k_fwd_xy_tc<3>)
+    SETMAX((k_bwd_xy<double, 0>)) SETMAX((k_bwd_xy<float, 0>))
+    SETMAX((k_bwd_xy<float, 2>)) SETMAX((k_bwd_xy<float, 3>))
     SETMAX(k_hs<double>) SETMAX(k_hs<float>)
 #undef SETMAX
     return cudaSuccess;
@@ -1510,7 +1838,16 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int nf = a.nfn;
     TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_segL + 7) / 8, nf), 256, 0, s>>>(a)));
-    TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
+    if constexpr (sizeof(T) == 4) {
+        if (a.xy_tc && a.zsplit == 3)
+            TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy_tc<3><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd_tc, s>>>(a)));
+        else if (a.xy_tc && a.zsplit == 2)
+            TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy_tc<2><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd_tc, s>>>(a)));
+        else
+            TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
+    } else {
+        TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
+    }
     if constexpr (sizeof(T) == 4) {
         if (a.zsplit) {
             // several tiles per CTA: the filter operands are built once per CTA
@@ -1526,8 +1863,17 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
         TRACED(a.tr, TK_Z, s, (k_z<T><<<dim3((a.max_cols + a.zcols - 1) / a.zcols, nf), a.zcols, a.smem_z, s>>>(a)));
     }
     TRACED(a.tr, TK_KINETIC, s,
-           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf, 4), 128, 0, s>>>(a)));
-    TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
+           (k_kin_z<T><<<dim3(static_cast<unsigned>((a.max_colsL + 127) / 128), nf, 4), 128, a.smem_kin, s>>>(a)));
+    if constexpr (sizeof(T) == 4) {
+        if (a.xy_tc && a.zsplit == 3)
+            TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<float, 3><<<dim3(2 * a.max_nzp, nf), 512, a.smem_bwd_tc, s>>>(a)));
+        else if (a.xy_tc && a.zsplit == 2)
+            TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<float, 2><<<dim3(2 * a.max_nzp, nf), 512, a.smem_bwd_tc, s>>>(a)));
+        else
+            TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<float, 0><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
+    } else {
+        TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T, 0><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
+    }
     return cudaGetLastError();
 }
 

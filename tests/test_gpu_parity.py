@@ -238,3 +238,18 @@ def test_split_bf16_option_errors():
         lsw.lsw_set_option(S.sys, "zsplit", 2)
     finally:
         S.close()
+
+
+@pytest.mark.parametrize("parts", [2, 3])
+def test_tensor_core_plane_kernels_option(parts):
+    # option "xy_tc": the x and y passes of the plane kernels on the tensor cores too
+    wl = I.scaled("atoms64", 6, seed=13)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    n = len(geo.sf_atom)
+    ref = oracle_hphi(wl, geo, range(n), V)
+    g = gpu_run(wl, phi_fn(wl), lsw.LSW_FP32_BF16X, options={"zsplit": parts, "xy_tc": 1})
+    err = check_functions(wl, geo, g, ref, 1e-5)
+    check_rows(wl, geo, g, ref, range(n), 1e-5)
+    if parts == 3:
+        assert err <= 1e-6
