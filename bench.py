@@ -41,9 +41,8 @@ from paper_1401_7441_gb300 import inputs as I  # noqa: E402
 
 METRIC = "H-phi support functions/s incl. sparse H,S build"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# CUDA-core peaks derived from the SM count and the maximum SM clock (no measured
-# figure exists for them): FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 is the
-# nominal GB300 figure.
+# Nominal CUDA-core peaks (context beside the measured ones): FP32 152 SMs x 128 lanes x
+# 2 flop x 2.07 GHz; FP64 the nominal GB300 figure.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 
@@ -406,6 +405,8 @@ def gpu_main(args):
         lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
         lsw.lsw_build_matrices(S.sys, phi, hphi, Hm, Sm)
 
+    # roofline denominators measured on this GPU (FMA loops, streaming copy)
+    peaks = dict(zip(("fp32_fma_tflops", "fp64_fma_tflops", "copy_gbs"), lsw.lsw_measure_peaks(S.ctx)))
     tune = None
     if not args.no_autotune and not args.batch and not args.tile:
         from paper_1401_7441_gb300 import autotune
@@ -478,13 +479,14 @@ def gpu_main(args):
         if dom in flops:
             launches_per_step = n_launch / args.steps
             work_per_launch = flops[dom] / launches_per_step
-            peak = (FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS)
+            peak = peaks["fp64_fma_tflops"] if prec == "fp64" else peaks["fp32_fma_tflops"]
             ach = work_per_launch / (per_launch_ms / 1000.0) / 1e12
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak,
                     "traffic": stored_traffic(dom, wl.name, prec, (tune or {}).get("chosen", {}).get("batch")),
-                    "peak_source": ("nominal GB300 FP64 rate (1.25 TFLOP/s)" if prec == "fp64"
-                                    else "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")}
+                    "peak_source": "measured on this GPU: %s FMA loop over every SM (lsw_measure_peaks); "
+                                   "nominal %.1f TFLOP/s" % ("FP64" if prec == "fp64" else "FP32",
+                                                            FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS)}
         else:
             roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
                     "frac": None, "traffic": None}
@@ -512,7 +514,7 @@ def gpu_main(args):
                            "parallelism": "replicas" if world > 1 else "single",
                            "options": (tune or {}).get("chosen", {"batch": args.batch or None, "tile": args.tile or None}),
                            "autotune_ms": {k: v for k, v in (tune or {}).items() if k != "chosen"}},
-                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "error_vs_oracle": err, "clocks": clocks,
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "error_vs_oracle": err, "peaks_measured": peaks, "clocks": clocks,
                 "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
                 "kernel_share": kshare,
                 "algorithmic_tflop_per_step": {k: v / 1e12 for k, v in flops.items()},
@@ -527,7 +529,8 @@ def gpu_main(args):
 
 
 def serving_main(args):
-    """p50/p99 latency and support functions/s of the served (FP32, batched, streams)
+    """p50/p99 latency and support functions/s of the served (split-bfloat16 z stage, FP32
+    elsewhere, batched, streams)
     form on a Poisson stream (20 req/s, 50-5,000 atoms, 30 % reuse), against each
     request run alone on the plain form (FP64, one function per batch, no graphs)."""
     import torch
@@ -557,7 +560,7 @@ def serving_main(args):
     line = {"metric": METRIC + " (serving)", "value": served["support_functions_per_s"],
             "unit": "support_functions/s", "n_gpus": 1, "steps": len(res), "warmup": 0,
             "ms_per_step": 1000.0 * served["span_s"] / max(1, len(res)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
             "config": {"workload": "serving: Poisson 20 req/s, 50-5,000 atoms log-uniform, 30% reuse",
                        "requests": len(res), "budget_gb": 150},
             "serving": served, "wall_s": wall,

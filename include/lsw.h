@@ -217,6 +217,14 @@ lsw_status lsw_build_matrices(lsw_system sys, const void* phi_dev, const void* h
 lsw_status lsw_reformat(lsw_system dst, lsw_system src, const int32_t* shift, const void* phi_src_dev,
                         void* phi_dst_dev);
 
+/* Roofline denominators measured on the context's GPU (no counterpart in the paper):
+ * FP32 and FP64 FMA rates of a dependent-chain FMA loop over every SM, TFLOP/s, and the
+ * rate of a 16-byte streaming copy between two 1 GiB device buffers, GB/s (bytes read +
+ * written).  Best of 5 timed repetitions each.  Synchronous: waits for the whole device,
+ * allocates and frees 2 GiB.  Errors: LSW_ERR_ARG, LSW_ERR_STATE (host-only context),
+ * LSW_ERR_CUDA. */
+lsw_status lsw_measure_peaks(lsw_ctx ctx, double* fp32_tflops, double* fp64_tflops, double* copy_gbs);
+
 /* Device workspace held by the system, bytes. */
 lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes);
 

@@ -1297,6 +1297,16 @@ lsw_status lsw_reformat(lsw_system dst, lsw_system src, const int32_t* shift, co
     return LSW_OK;
 }
 
+lsw_status lsw_measure_peaks(lsw_ctx ctx, double* fp32_tflops, double* fp64_tflops, double* copy_gbs) {
+    g_err.clear();
+    if (!ctx || !fp32_tflops || !fp64_tflops || !copy_gbs) return fail(LSW_ERR_ARG, "lsw_measure_peaks: NULL argument");
+    if (ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(measure_peaks(ctx->n_sm, fp32_tflops, fp64_tflops, copy_gbs));
+    return LSW_OK;
+}
+
 lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
     g_err.clear();
     if (!sys || !bytes) return fail(LSW_ERR_ARG, "lsw_workspace_bytes: NULL argument");

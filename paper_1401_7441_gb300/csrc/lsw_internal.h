@@ -171,6 +171,7 @@ cudaError_t enqueue_reformat(const ReformatLaunch& a, cudaStream_t s);
 
 // Device entry points (lsw_kernels.cu).
 cudaError_t upload_filters(const FilterSet& fs, int device);
+cudaError_t measure_peaks(int n_sm, double* fp32_tflops, double* fp64_tflops, double* copy_gbs);
 cudaError_t configure_kernels(size_t max_smem);
 cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s);
 cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s);

@@ -22,6 +22,7 @@
 // (never trap).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -1694,6 +1695,90 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) 
             if (sacc[u][v] != T(0)) atomicAdd(a.S + pos, static_cast<double>(sacc[u][v]));
         }
     }
+}
+
+// ---------------------------------------------------------------- peak probes
+//
+// Denominators of the rooflines, measured on the running GPU: a dependent-chain FMA
+// loop (8 independent chains per thread, operands from memory so nothing folds) and a
+// 16-byte streaming copy.
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_peak(const T* in, T* out, int iters) {
+    T x = in[0], y = in[1];
+    T acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = in[2 + i] + static_cast<T>(threadIdx.x);
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = acc[i] * x + y;
+    T sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sum += acc[i];
+    if (sum == static_cast<T>(-1.2345)) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;   // keeps the loop live
+}
+
+__global__ void __launch_bounds__(256) k_copy_peak(const float4* __restrict__ src, float4* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[i] = src[i];
+}
+
+cudaError_t measure_peaks(int n_sm, double* fp32_tflops, double* fp64_tflops, double* copy_gbs) {
+    cudaError_t e;
+    const int64_t n4 = (1LL << 30) / 16;       // 1 GiB per buffer
+    float4 *a = nullptr, *b = nullptr;
+    double* io = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto done = [&](cudaError_t r) {
+        if (a) cudaFree(a);
+        if (b) cudaFree(b);
+        if (io) cudaFree(io);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return r;
+    };
+    if ((e = cudaMalloc(&a, n4 * 16)) != cudaSuccess) return done(e);
+    if ((e = cudaMalloc(&b, n4 * 16)) != cudaSuccess) return done(e);
+    if ((e = cudaMalloc(&io, 4096)) != cudaSuccess) return done(e);
+    if ((e = cudaMemset(a, 0, n4 * 16)) != cudaSuccess) return done(e);
+    {
+        const double hv[10] = {0.999999, 1e-7, 1, 2, 3, 4, 5, 6, 7, 8};
+        const float hf[10] = {0.999999f, 1e-7f, 1, 2, 3, 4, 5, 6, 7, 8};
+        if ((e = cudaMemcpy(io, hv, sizeof(hv), cudaMemcpyHostToDevice)) != cudaSuccess) return done(e);
+        if ((e = cudaMemcpy(reinterpret_cast<char*>(io) + 128, hf, sizeof(hf), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return done(e);
+    }
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) return done(e);
+    const int blocks = n_sm * 8;
+    auto best_ms = [&](auto launch, float* out_ms) -> cudaError_t {
+        float best = 1e30f;
+        for (int r = 0; r < 6; ++r) {
+            cudaEventRecord(e0);
+            launch();
+            cudaEventRecord(e1);
+            cudaError_t le = cudaEventSynchronize(e1);
+            if (le != cudaSuccess) return le;
+            if ((le = cudaGetLastError()) != cudaSuccess) return le;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) best = std::min(best, ms);
+        }
+        *out_ms = best;
+        return cudaSuccess;
+    };
+    float ms;
+    const int it32 = 1 << 16, it64 = 1 << 12;
+    float* io32 = reinterpret_cast<float*>(reinterpret_cast<char*>(io) + 128);
+    if ((e = best_ms([&] { k_fma_peak<float><<<blocks, 256>>>(io32, io32 + 64, it32); }, &ms)) != cudaSuccess)
+        return done(e);
+    *fp32_tflops = 2.0 * 8.0 * it32 * blocks * 256.0 / (ms * 1e-3) / 1e12;
+    if ((e = best_ms([&] { k_fma_peak<double><<<blocks, 256>>>(io, io + 128, it64); }, &ms)) != cudaSuccess)
+        return done(e);
+    *fp64_tflops = 2.0 * 8.0 * it64 * blocks * 256.0 / (ms * 1e-3) / 1e12;
+    if ((e = best_ms([&] { k_copy_peak<<<n_sm * 16, 256>>>(a, b, n4); }, &ms)) != cudaSuccess) return done(e);
+    *copy_gbs = 2.0 * n4 * 16.0 / (ms * 1e-3) / 1e9;
+    return done(cudaSuccess);
 }
 
 // ---------------------------------------------------------------- reformat

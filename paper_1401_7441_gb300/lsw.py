@@ -75,6 +75,7 @@ _SIGS = {
     "lsw_system_set_stream": (C.c_int, [_P, _P]),
     "lsw_profile_read": (C.c_int, [_P, C.c_int32, _I32P, _DP, _I64P]),
     "lsw_save": (C.c_int, [_P, _P, C.c_char_p]),
+    "lsw_measure_peaks": (C.c_int, [_P, _DP, _DP, _DP]),
     "lsw_load": (C.c_int, [_P, C.c_char_p, C.POINTER(_P), _P]),
     "lsw_load_phi": (C.c_int, [_P, C.c_char_p, _P]),
 }
@@ -311,3 +312,10 @@ def lsw_load(ctx, path, phi=None):
 
 def lsw_load_phi(sys, path, phi):
     check(lib().lsw_load_phi(sys, os.fsencode(path), _ptr(phi)))
+
+
+def lsw_measure_peaks(ctx):
+    """(fp32 TFLOP/s, fp64 TFLOP/s, copy GB/s) measured on the context's GPU."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    check(lib().lsw_measure_peaks(ctx, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value

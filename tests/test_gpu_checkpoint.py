@@ -77,3 +77,17 @@ def test_save_load_same_results(prec, tmp_path):
     finally:
         A.close()
         lsw.lsw_ctx_destroy(ctx2)
+
+
+def test_measured_peaks_are_plausible():
+    # roofline denominators from the library's own FMA loops and streaming copy
+    ensure_built()
+    import torch
+    ctx = lsw.lsw_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        f32, f64, copy = lsw.lsw_measure_peaks(ctx)
+    finally:
+        lsw.lsw_ctx_destroy(ctx)
+    assert 10.0 < f32 < 200.0          # TFLOP/s
+    assert 0.05 < f64 < 20.0
+    assert 500.0 < copy < 20000.0      # GB/s
