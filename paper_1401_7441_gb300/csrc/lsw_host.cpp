@@ -393,7 +393,8 @@ void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, siz
     *fwd = es * static_cast<size_t>(4 * r.n[1] * RS + 2 * r.n[1] * X);
     *z = es * static_cast<size_t>((2 * r.n[2] + Z) * zcols);
     const int64_t plA = std::max<int64_t>(Y * X, 4LL * r.np[1] * r.np[0]);
-    *bwd = es * static_cast<size_t>(plA + 2 * r.np[1] * X + 4 * r.n[1] * RS) +
+    const int64_t midA = std::max<int64_t>(2LL * r.np[1] * X, 4LL * r.np[1] * r.np[0]);
+    *bwd = es * static_cast<size_t>(plA + midA + 4 * r.n[1] * RS) +
            static_cast<size_t>((4 * r.n[0] * r.n[1] + 15) / 16 * 16);   // + z-arm column flags
 }
 

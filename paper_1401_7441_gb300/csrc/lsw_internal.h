@@ -20,7 +20,7 @@ constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [
 constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
 constexpr int ZCOLS_F64 = 64;    // real-space columns per block of the z stage (FP64)
 constexpr int ZCOLS_F32 = 128;   // (FP32)
-constexpr size_t BWD_STATIC_SMEM = 12 * 1024;   // upper bound of k_bwd_xy's static shared memory
+constexpr size_t BWD_STATIC_SMEM = 14 * 1024;   // upper bound of k_bwd_xy's static shared memory
 
 // Filter tables, FP64 (rounded once from double-double).
 struct FilterSet {

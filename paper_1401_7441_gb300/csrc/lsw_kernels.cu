@@ -1183,6 +1183,7 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int16_t rx0[256], rx1[256];         // member x range per row (L' plane), -1: none
     __shared__ int roff[256];                      // coefficient offset of the row's coarse segment
+    __shared__ int fr0[256], fr1[256];             // fine segment range of the row (L' keys)
     __shared__ int task[BWD_MAX_TASKS];
     __shared__ int ntask, ylo, yhi, xlo, xhi;
     __shared__ unsigned char rowf[4][128], colf[4][128];   // D plane: nonzero per (type, row / column)
@@ -1208,8 +1209,9 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     unsigned char* sXr = sFx + NS * FX_PART;
     T* pl = sm;
     T* Gs = NS ? reinterpret_cast<T*>(sXr) : sm;
+    const int midA = max(2 * nyp * X, 4 * nyp * nxp);   // mid [2][nyp][X], later the z-arm plane
     T* mid = sm + plA;
-    T* Dp = NS ? reinterpret_cast<T*>(sXr + XR) : mid + 2 * nyp * X;
+    T* Dp = NS ? reinterpret_cast<T*>(sXr + XR) : mid + midA;
     const int64_t smem_n = static_cast<int64_t>((NS ? a.smem_bwd_tc : a.smem_bwd) / sizeof(T));
     if constexpr (NS > 0) {
         if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(tc::saddr(smem_raw + 8), 128);
@@ -1251,6 +1253,9 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
         rx0[y] = static_cast<int16_t>(lo);
         rx1[y] = static_cast<int16_t>(hi);
         roff[y] = off;
+        const int64_t frow = at.rowPf + y + static_cast<int64_t>(nyp) * zb;
+        fr0[y] = LD(a.rowptr, frow, a.rowptr_n);
+        fr1[y] = LD(a.rowptr, frow + 1, a.rowptr_n);
     }
     const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
     const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
@@ -1357,6 +1362,18 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                 }
             }
         }
+        // mid is dead: stage the z-arm plane G (types tb + 4 bz) for the compressed write,
+        // in flight during the kinetic phases
+        __syncthreads();
+        {
+            const T* G = static_cast<const T*>(a.ws) + r.ws_G;
+            const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
+            const int pnp = nyp * nxp;
+            for (int tb = 0; tb < 4; ++tb)
+                for (int i = threadIdx.x; i < pnp; i += blockDim.x)
+                    CPA(mid, tb * pnp + i, midA, G, (tb + 4 * bz) * gplane + static_cast<int64_t>(zb) * pnp + i,
+                        8 * gplane);
+        }
       }
         if (dplane) {
             int nt;
@@ -1445,8 +1462,10 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             }
         }
     }
+    cp_wait();
     __syncthreads();
-    // ---- compress: members of this plane -> H phi (plus the z arm left in G by k_kin_z)
+    // ---- compress: members of this plane -> H phi (plus the z arm left in G by k_kin_z;
+    //      the FMA path reads it from the plane staged in mid)
     if (yhi_ >= 0) {
         const T* G = static_cast<const T*>(a.ws) + r.ws_G;
         const unsigned char* gflag = reinterpret_cast<const unsigned char*>(gfl);   // staged above
@@ -1463,13 +1482,13 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                 for (int xb = rx0[b] + lane; xb <= rx1[b]; xb += 32) {
                     const int x = xb + dx;
                     T v = LD(Gs, static_cast<int64_t>(b) * nxp + xb, gs_n);
-                    if (yin && x >= 0 && x < nx && LD(gflag, y * nx + x, 4LL * pn)) v += LD(G, grow + xb, 8 * gplane);
+                    if (yin && x >= 0 && x < nx && LD(gflag, y * nx + x, 4LL * pn))
+                        v += NS ? LD(G, grow + xb, 8 * gplane) : LD(mid, static_cast<int64_t>(b) * nxp + xb, midA);
                     ST(out, roff[b] + (xb - rx0[b]), out_room, v);
                 }
             }
             // wavelet parts on the fine members of this row
-            const int64_t frow = at.rowPf + b + static_cast<int64_t>(nyp) * zb;
-            const int f0 = LD(a.rowptr, frow, a.rowptr_n), f1 = LD(a.rowptr, frow + 1, a.rowptr_n);
+            const int f0 = fr0[b], f1 = fr1[b];
             for (int q = f0; q < f1; ++q) {
                 const Seg fs = LD(a.seg, at.segPf + q, a.seg_n);
                 for (int xb = fs.x0 + lane; xb <= fs.x1; xb += 32) {
@@ -1480,7 +1499,9 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                         const int t = tb + 4 * bz;
                         if (t == 0) continue;
                         T v = LD(Gs, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, gs_n);
-                        if (zin && LD(gflag, (t & 3) * pn + y * nx + x, 4LL * pn)) v += LD(G, t * gplane + grow + xb, 8 * gplane);
+                        if (zin && LD(gflag, (t & 3) * pn + y * nx + x, 4LL * pn))
+                            v += NS ? LD(G, t * gplane + grow + xb, 8 * gplane)
+                                    : LD(mid, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, midA);
                         ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + fs.off + (xb - fs.x0), out_room, v);
                     }
                 }
