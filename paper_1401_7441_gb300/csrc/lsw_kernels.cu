@@ -114,6 +114,10 @@ __device__ __forceinline__ void cp_async(T* dst, const T* src) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N committed groups of this thread's copies are still in flight
+template <int N>
+__device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------- uncompress / compress
 
@@ -1235,6 +1239,35 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
         colf[i >> 7][i & 127] = 0;
     }
     __syncthreads();
+    // staging copies first (they fly while the row records below are read): group 1 the
+    // Bb plane, group 2 the D plane and the z-arm column flags
+    const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
+    const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
+    if constexpr (NS == 0)
+        for (int i = threadIdx.x; i < Y * X; i += blockDim.x) CPA(pl, i, smem_n, Bb, i, bb_room);
+    cp_commit();
+    const T* D = static_cast<const T*>(a.ws) + r.ws_D;
+    const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
+    const int pn = nx * ny;
+    const int64_t dp_n = smem_n - (reinterpret_cast<unsigned char*>(Dp) - smem_raw) / static_cast<int64_t>(sizeof(T));
+    if (dplane) {
+        const FastDiv fd_pn(pn), fd_nx(nx);
+        for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
+            const int tb = fd_pn.div(i), rem = i - tb * pn;
+            const int y = fd_nx.div(rem), x = rem - y * nx;
+            CPA(Dp, (tb * ny + y) * RS + x, dp_n, D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem,
+                8 * plane);
+        }
+    }
+    // z-arm column flags of the L box (written by k_kin_z), 4 bytes per copy
+    uint32_t* gfl = reinterpret_cast<uint32_t*>(Dp + 4 * ny * RS);
+    [[maybe_unused]] const int64_t gfl_n = (smem_n * static_cast<int64_t>(sizeof(T)) -
+                                            (reinterpret_cast<unsigned char*>(gfl) - smem_raw)) / 4;
+    {
+        const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(static_cast<const T*>(a.ws) + r.ws_Gf);
+        for (int i = threadIdx.x; i < pn; i += blockDim.x) CPA(gfl, i, gfl_n, gsrc, i, pn);
+    }
+    cp_commit();
     // member x range of each row of this plane (coarse part of L')
     for (int y = threadIdx.x; y < nyp; y += blockDim.x) {
         const int64_t row = at.rowPc + y + static_cast<int64_t>(nyp) * zb;
@@ -1257,44 +1290,7 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
         fr0[y] = LD(a.rowptr, frow, a.rowptr_n);
         fr1[y] = LD(a.rowptr, frow + 1, a.rowptr_n);
     }
-    const T* Bb = static_cast<const T*>(a.ws) + r.ws_Bb + (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
-    const int64_t bb_room = 2LL * nzp * Y * X - (static_cast<int64_t>(bz) * nzp + zb) * Y * X;
-    if constexpr (NS == 0)
-        for (int i = threadIdx.x; i < Y * X; i += blockDim.x) CPA(pl, i, smem_n, Bb, i, bb_room);
-    const T* D = static_cast<const T*>(a.ws) + r.ws_D;
-    const int64_t plane = static_cast<int64_t>(nx) * ny * nz;
-    const int pn = nx * ny;
-    const int64_t dp_n = smem_n - (reinterpret_cast<unsigned char*>(Dp) - smem_raw) / static_cast<int64_t>(sizeof(T));
-    if (dplane) {
-        const FastDiv fd_pn(pn), fd_nx(nx);
-        for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
-            const int tb = fd_pn.div(i), rem = i - tb * pn;
-            const int y = fd_nx.div(rem), x = rem - y * nx;
-            CPA(Dp, (tb * ny + y) * RS + x, dp_n, D, (tb + 4 * bz) * plane + static_cast<int64_t>(zL) * pn + rem,
-                8 * plane);
-        }
-    }
-    // z-arm column flags of the L box (written by k_kin_z), 4 bytes per copy
-    uint32_t* gfl = reinterpret_cast<uint32_t*>(Dp + 4 * ny * RS);
-    [[maybe_unused]] const int64_t gfl_n = (smem_n * static_cast<int64_t>(sizeof(T)) -
-                                            (reinterpret_cast<unsigned char*>(gfl) - smem_raw)) / 4;
-    {
-        const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(static_cast<const T*>(a.ws) + r.ws_Gf);
-        for (int i = threadIdx.x; i < pn; i += blockDim.x) CPA(gfl, i, gfl_n, gsrc, i, pn);
-    }
-    cp_wait();
-    __syncthreads();
-    if (dplane) {   // zero flags of the staged D plane
-        const FastDiv fd_pn(pn), fd_nx(nx);
-        for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
-            const int tb = fd_pn.div(i), rem = i - tb * pn;
-            const int y = fd_nx.div(rem), x = rem - y * nx;
-            if (LD(Dp, (tb * ny + y) * RS + x, dp_n) != T(0)) {
-                rowf[tb][y & 127] = 1;
-                colf[tb][x & 127] = 1;
-            }
-        }
-    }
+    cp_wait_group<1>();   // the Bb plane (group 2 may still be in flight)
     if (threadIdx.x == 0) ntask = 0;
     __syncthreads();
     const int64_t mid_n = 2LL * nyp * X;
@@ -1362,10 +1358,24 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                 }
             }
         }
-        // mid is dead: stage the z-arm plane G (types tb + 4 bz) for the compressed write,
-        // in flight during the kinetic phases
+      }
+        // the D plane and the flags have landed (their copies flew during the passes above)
+        cp_wait();
         __syncthreads();
-        {
+        if (dplane) {   // zero flags of the staged D plane
+            const FastDiv fd_pn(pn), fd_nx(nx);
+            for (int i = threadIdx.x; i < 4 * pn; i += blockDim.x) {
+                const int tb = fd_pn.div(i), rem = i - tb * pn;
+                const int y = fd_nx.div(rem), x = rem - y * nx;
+                if (LD(Dp, (tb * ny + y) * RS + x, dp_n) != T(0)) {
+                    rowf[tb][y & 127] = 1;
+                    colf[tb][x & 127] = 1;
+                }
+            }
+        }
+        if constexpr (NS == 0) {
+            // mid is dead: stage the z-arm plane G (types tb + 4 bz) for the compressed
+            // write, in flight during the kinetic phases
             const T* G = static_cast<const T*>(a.ws) + r.ws_G;
             const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
             const int pnp = nyp * nxp;
@@ -1374,7 +1384,6 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                     CPA(mid, tb * pnp + i, midA, G, (tb + 4 * bz) * gplane + static_cast<int64_t>(zb) * pnp + i,
                         8 * gplane);
         }
-      }
         if (dplane) {
             int nt;
             __syncthreads();

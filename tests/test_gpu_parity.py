@@ -253,3 +253,80 @@ def test_tensor_core_plane_kernels_option(parts):
     check_rows(wl, geo, g, ref, range(n), 1e-5)
     if parts == 3:
         assert err <= 1e-6
+
+
+def _full_size_sampled(wl, prec, options, fs, rows, tol):
+    # the bench's launch configuration on the full workload; sampled functions and rows
+    # against the oracle (each function's H phi from its own locreg, V from the same
+    # sum of wells)
+    import torch
+    from tests.lib_support import ensure_built, keys_to_g
+    ensure_built()
+    geo = G.build(desc_of(wl), atoms=sorted(set(int(a) for a in np.repeat(np.arange(len(wl.nsf)), wl.nsf)[fs])),
+                  pattern=False)
+    dt = torch.float64 if prec == lsw.LSW_FP64 else torch.float32
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                       wl.lprime_margin, 0, prec, device=0, stream=st.cuda_stream)
+        try:
+            for k, v in options.items():
+                lsw.lsw_set_option(S.sys, k, v)
+            phi = torch.zeros(S.total_L, dtype=dt, device="cuda")
+            atoms = sorted(set(int(a) for a in S.sf_atom))
+            I.fill_phi(wl, phi, S.off_L, S.sf_atom, {a: keys_to_g(S.keys(a, 0, 0)) for a in atoms},
+                       {a: keys_to_g(S.keys(a, 0, 1)) for a in atoms})
+            V = I.potential_fast(wl, "cuda").to(dt)
+            lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
+            hphi = torch.zeros(S.total_Lp, dtype=dt, device="cuda")
+            ek = torch.zeros(S.n_sf, dtype=torch.float64, device="cuda")
+            ep = torch.zeros_like(ek)
+            H = torch.zeros(len(S.col), dtype=torch.float64, device="cuda")
+            Sm = torch.zeros_like(H)
+            lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
+            lsw.lsw_build_matrices(S.sys, phi, hphi, H, Sm)
+            lsw.lsw_sync(S.sys, 600.0)
+            torch.cuda.synchronize()
+            hp, phd = hphi.double().cpu().numpy(), phi.double().cpu().numpy()
+            Hh, Sh, ekh, eph = H.cpu().numpy(), Sm.cpu().numpy(), ek.cpu().numpy(), ep.cpu().numpy()
+            off_L, off_Lp, rp, col = S.off_L, S.off_Lp, S.row_ptr, S.col
+        finally:
+            S.close()
+    ref = {}
+    for f in fs:
+        a = geo.sf_atom[f]
+        L = geo.L[a]
+        phi_f = I.phi_values(wl, f, a, L.coarse.g, L.fine.g)
+        assert np.allclose(phd[off_L[f]:off_L[f] + len(phi_f)], phi_f, rtol=1e-6, atol=1e-7)
+        lo = [2 * int(L.lo[d]) - 14 for d in range(3)]
+        shape = [2 * int(L.hi[d] - L.lo[d] + 1) + 29 for d in range(3)]
+        h, e_k, e_p = Hm.apply_hamiltonian(geo, f, phi_f, I.potential_block(wl, lo, shape), lo)
+        ref[f] = (phi_f, h)
+        g = hp[off_Lp[f]:off_Lp[f] + len(h)]
+        assert np.linalg.norm(g - h) / np.linalg.norm(h) <= tol, f
+        scale = np.linalg.norm(phi_f) * np.linalg.norm(h)
+        assert abs(ekh[f] - e_k) <= tol * scale and abs(eph[f] - e_p) <= tol * scale, f
+    for a in rows:
+        for k in range(rp[a], rp[a + 1]):
+            b = int(col[k])
+            if b not in ref:
+                continue
+            pa, pb, hb = ref[a][0], ref[b][0], ref[b][1]
+            s_ref = Mx.overlap_entry(geo, a, b, pa, pb)
+            h_ref = Mx.hamiltonian_entry(geo, a, b, pa, hb)
+            assert abs(Sh[k] - s_ref) <= tol * np.linalg.norm(pa) * np.linalg.norm(pb), (a, b)
+            assert abs(Hh[k] - h_ref) <= tol * np.linalg.norm(pa) * np.linalg.norm(hb), (a, b)
+
+
+def test_atoms10k_full_size_sampled_split_bf16():
+    # 28,000 functions, batch 256 and tile edge 4 (the bench's autotuned launch shape)
+    wl = I.atoms10k()
+    fs = [0, 1, 2, 3, 4, 5, 6, 7, 13999, 27999]
+    _full_size_sampled(wl, lsw.LSW_FP32_BF16X, {"batch": 256, "tile": 4}, fs, [0, 1, 2], 1e-5)
+
+
+def test_atoms1200_full_size_sampled_fp32():
+    # 4,096 functions on radii 5-8 bohr (uneven locregs in one batch)
+    wl = I.atoms1200()
+    fs = list(range(12)) + [2047, 4095]
+    _full_size_sampled(wl, lsw.LSW_FP32, {"batch": 128}, fs, [0, 1, 4], 1e-5)
