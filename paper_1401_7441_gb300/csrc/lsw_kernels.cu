@@ -1696,23 +1696,54 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) 
         }
         __syncthreads();
     }
+    // Pattern positions: the CSR rows of this item's a-functions are copied into the (now
+    // free) panel memory, so each pair's binary search runs in shared memory; rows that do
+    // not fit search global memory.
+    __shared__ int rofs[HS_BLK + 1];
+    __shared__ int rlen[HS_BLK];
+    __shared__ long long rbase[HS_BLK];
+    int* rcols = reinterpret_cast<int*>(smem_raw);
+    const int rcap = static_cast<int>(PN * sizeof(T) / sizeof(int));
+    if (tid < w.na) {
+        const int fa = LD(a.listA, w.a0 + tid, a.listA_n);
+        const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
+        rbase[tid] = r0;
+        rlen[tid] = static_cast<int>(r1 - r0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int o = 0;
+        for (int i = 0; i < w.na; ++i) {
+            rofs[i] = o;
+            if (o + rlen[i] <= rcap) o += rlen[i];
+            else rofs[i] = -1;                                   // searched in global memory
+        }
+    }
+    __syncthreads();
+    for (int i = tid >> 5; i < w.na; i += blockDim.x >> 5) {
+        if (rofs[i] < 0) continue;
+        for (int k = tid & 31; k < rlen[i]; k += 32)
+            ST(rcols, rofs[i] + k, rcap, LD(a.col, rbase[i] + k, a.nnz));
+    }
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int i = ti + 16 * u;
         if (i >= w.na) continue;
-        const int fa = LD(a.listA, w.a0 + i, a.listA_n);
-        const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
+        const int64_t r0 = rbase[i];
+        const int ro = rofs[i], rl = rlen[i];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int j = tj + 16 * v;
             if (j >= w.nb) continue;
             const int fb = LD(a.listB, w.b0 + j, a.listB_n);
-            int64_t lo = r0, hi = r1 - 1, pos = -1;
+            int lo = 0, hi = rl - 1;
+            int64_t pos = -1;
             while (lo <= hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                const int cm = LD(a.col, mid, a.nnz);
+                const int mid = (lo + hi) >> 1;
+                const int cm = ro >= 0 ? LD(rcols, ro + mid, rcap) : LD(a.col, r0 + mid, a.nnz);
                 if (cm == fb) {
-                    pos = mid;
+                    pos = r0 + mid;
                     break;
                 }
                 if (cm < fb)
