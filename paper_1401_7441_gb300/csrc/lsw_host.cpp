@@ -496,6 +496,7 @@ lsw_status build_plans(lsw_system_s* s) {
             p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
             p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
             p.max_colsL = std::max(p.max_colsL, r.n[0] * r.n[1]);
+            p.max_rowsL = std::max(p.max_rowsL, r.n[1] * r.n[2]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
             size_t a1, a2, a3;
@@ -1180,6 +1181,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
             p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
             p.max_colsL = std::max(p.max_colsL, r.n[0] * r.n[1]);
+            p.max_rowsL = std::max(p.max_rowsL, r.n[1] * r.n[2]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
             size_t a1, a2, a3;

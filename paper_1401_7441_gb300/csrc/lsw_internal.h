@@ -85,6 +85,7 @@ struct HphiLaunch {
     int64_t max_ptsP;            // largest nx'*ny'*nz' of L'
     int max_colsP;               // largest nx'*ny' of L'
     int max_colsL;               // largest nx*ny of L
+    int max_rowsL;               // largest ny*nz of L
     int max_segL;                // largest coarse+fine segment count of L
     int max_segP;
     size_t smem_fwd, smem_z, smem_bwd;

@@ -122,36 +122,47 @@ __device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_gr
 // ---------------------------------------------------------------- uncompress / compress
 
 template <class T>
-__global__ void k_uncompress(HphiLaunch a) {
+__global__ void __launch_bounds__(256) k_uncompress(HphiLaunch a) {
+    // Warp per (y, z) row of the L box: writes all 8 types of the row, the members' values
+    // from the compressed phi (one coarse segment per row of the sphere, a few fine
+    // segments) and zero elsewhere, so the box needs no separate clearing.
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 1;
     const FnRec r = a.fn[blockIdx.y];
     const AtomRec& at = a.atoms[r.atom];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sidx = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int nseg = at.nsegLc + at.nsegLf;
-    if (sidx >= nseg) return;
-    const bool fine = sidx >= at.nsegLc;
-    const Seg sg = LD(a.seg, fine ? at.segLf + (sidx - at.nsegLc) : at.segLc + sidx, a.seg_n);
-    const int64_t plane = static_cast<int64_t>(r.n[0]) * r.n[1] * r.n[2];
-    T* D = static_cast<T*>(a.ws) + r.ws_D;
+    const int nx = r.n[0], nrows = r.n[1] * r.n[2];
+    const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (row >= nrows) return;
+    const int64_t plane = static_cast<int64_t>(nx) * nrows;
+    T* D = static_cast<T*>(a.ws) + r.ws_D + static_cast<int64_t>(row) * nx;
     const T* phi = static_cast<const T*>(a.phi) + r.off_phi;
     const int64_t phi_room = a.phi_n - r.off_phi;
-    const int len = sg.x1 - sg.x0 + 1;
-    if (sg.x0 < 0 || sg.x1 >= r.n[0] || sg.row < 0 || sg.row >= r.n[1] * r.n[2]) {
-        if (lane == 0) atomicOr(a.status, ST_BAD_SEG);
-        return;
-    }
-    const int64_t base = static_cast<int64_t>(sg.row) * r.n[0] + sg.x0;
-    for (int k = lane; k < len; k += 32) {
-        if (!fine) {
-            ST(D, base + k, 8 * plane, LD(phi, sg.off + k, phi_room));
-        } else {
-#pragma unroll
-            for (int t = 1; t < 8; ++t)
-                ST(D, t * plane + base + k, 8 * plane,
-                   LD(phi, at.ncL + static_cast<int64_t>(t - 1) * at.nfL + sg.off + k, phi_room));
+    const int c0 = LD(a.rowptr, at.rowLc + row, a.rowptr_n), c1 = LD(a.rowptr, at.rowLc + row + 1, a.rowptr_n);
+    const int f0 = LD(a.rowptr, at.rowLf + row, a.rowptr_n), f1 = LD(a.rowptr, at.rowLf + row + 1, a.rowptr_n);
+    Seg cs{};
+    cs.x0 = 1;
+    cs.x1 = 0;                                         // empty unless the row has members
+    if (c1 > c0) {
+        cs = LD(a.seg, at.segLc + c0, a.seg_n);
+        if (c1 - c0 > 1 || cs.x0 < 0 || cs.x1 >= nx || cs.row != row) {
+            if (lane == 0) atomicOr(a.status, ST_BAD_SEG);
+            return;
         }
+    }
+    for (int x = lane; x < nx; x += 32) {
+        ST(D, x, 8 * plane - static_cast<int64_t>(row) * nx,
+           (x >= cs.x0 && x <= cs.x1) ? LD(phi, cs.off + (x - cs.x0), phi_room) : T(0));
+        // wavelet types: the fine segment of this row holding x, if any
+        int64_t fo = -1;
+        for (int q = f0; q < f1; ++q) {
+            const Seg fs = LD(a.seg, at.segLf + q, a.seg_n);
+            if (x >= fs.x0 && x <= fs.x1) fo = fs.off + (x - fs.x0);
+        }
+#pragma unroll
+        for (int t = 1; t < 8; ++t)
+            ST(D, t * plane + x, 8 * plane - static_cast<int64_t>(row) * nx,
+               fo >= 0 ? LD(phi, at.ncL + static_cast<int64_t>(t - 1) * at.nfL + fo, phi_room) : T(0));
     }
 }
 
@@ -489,7 +500,7 @@ namespace tc {
 
 constexpr int TILE = 128;       // real-space columns per tile (MMA M)
 constexpr int HEAD = 512;       // shared header: mbarrier, tensor-memory address, taps
-constexpr int TILES_PER_CTA = 8;
+constexpr int TILES_PER_CTA = 16;
 constexpr int MAX_KH = 64;      // largest half of K1 = 2 nz rounded up to 16 (nz <= 64)
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -1379,8 +1390,9 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             const T* G = static_cast<const T*>(a.ws) + r.ws_G;
             const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
             const int pnp = nyp * nxp;
+            const int r0 = ylo_ * nxp, r1 = (yhi_ + 1) * nxp;        // member rows only
             for (int tb = 0; tb < 4; ++tb)
-                for (int i = threadIdx.x; i < pnp; i += blockDim.x)
+                for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
                     CPA(mid, tb * pnp + i, midA, G, (tb + 4 * bz) * gplane + static_cast<int64_t>(zb) * pnp + i,
                         8 * gplane);
         }
@@ -1979,11 +1991,8 @@ cudaError_t configure_kernels(size_t max_smem) {
 
 template <class T>
 static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
-    cudaError_t e = cudaSuccess;
-    TRACED(a.tr, TK_MEMSET, s, e = cudaMemsetAsync(a.ws, 0, static_cast<size_t>(a.ws_D_elems) * sizeof(T), s));
-    if (e != cudaSuccess) return e;
     const int nf = a.nfn;
-    TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_segL + 7) / 8, nf), 256, 0, s>>>(a)));
+    TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_rowsL + 7) / 8, nf), 256, 0, s>>>(a)));
     if constexpr (sizeof(T) == 4) {
         if (a.xy_tc && a.zsplit == 3)
             TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy_tc<3><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd_tc, s>>>(a)));
