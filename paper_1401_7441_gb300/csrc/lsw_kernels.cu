@@ -34,6 +34,11 @@ __constant__ double c_fwd_d[2][FWD_TAPS];
 __constant__ float c_fwd_f[2][FWD_TAPS];
 __constant__ double c_kin_d[4][KIN_TAPS];
 __constant__ float c_kin_f[4][KIN_TAPS];
+// Tap pairs for the packed (two-lane) FP32 FMA of the blocks below: the two outputs of a
+// block that read the same input element, side by side.
+__constant__ float2 c_fwd2_bwd[FWD_TAPS];          // (F_0[m], F_1[m])
+__constant__ float2 c_fwd2_up[2][16];              // (F_b[2k], F_b[2k+1]), F_b[31] = 0
+__constant__ float2 c_kin2[2][KIN_TAPS];           // (K_0(l), K_2(l)), (K_1(l), K_3(l))
 
 template <class T>
 struct Tab;
@@ -298,6 +303,69 @@ __device__ __forceinline__ void kin_block(const T (&k0)[KW], const T (&k1)[KW], 
         o1[j] = a1;
     }
 }
+
+// FP32 versions on the packed two-lane FMA (__ffma2_rn: each lane one FMA rounded to
+// nearest, so every accumulator sees the same operations in the same order as above and
+// the results are the same bits).  The two lanes are the two outputs of a block that read
+// the same input element.
+#ifndef LSW_FFMA2
+#define LSW_FFMA2 1
+#endif
+#if LSW_FFMA2
+template <>
+__device__ __forceinline__ void fwd_block<float>(const float (&w0)[FW], const float (&w1)[FW], float (&u)[2 * FB]) {
+#pragma unroll
+    for (int j = 0; j < FB; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float a = w0[j + 15 - k], b = w1[j + 15 - k];
+            acc = __ffma2_rn(c_fwd2_up[0][k], make_float2(a, a), acc);
+            acc = __ffma2_rn(c_fwd2_up[1][k], make_float2(b, b), acc);
+        }
+        u[2 * j] = acc.x;
+        u[2 * j + 1] = acc.y;
+    }
+}
+template <int NB>
+__device__ __forceinline__ void bwd_block_f2(const float (&w)[2 * NB + 29], float (&s)[NB], float (&d)[NB]) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < FWD_TAPS; ++m) {
+            const float a = w[2 * j + m];
+            acc = __ffma2_rn(c_fwd2_bwd[m], make_float2(a, a), acc);
+        }
+        s[j] = acc.x;
+        d[j] = acc.y;
+    }
+}
+template <>
+__device__ __forceinline__ void bwd_block<float, 4>(const float (&w)[37], float (&s)[4], float (&d)[4]) {
+    bwd_block_f2<4>(w, s, d);
+}
+template <>
+__device__ __forceinline__ void bwd_block<float, 8>(const float (&w)[45], float (&s)[8], float (&d)[8]) {
+    bwd_block_f2<8>(w, s, d);
+}
+template <>
+__device__ __forceinline__ void kin_block<float>(const float (&k0)[KW], const float (&k1)[KW], float (&o0)[BB],
+                                                 float (&o1)[BB]) {
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < KIN_TAPS; ++l) {
+            const float a = k0[j + l], b = k1[j + l];
+            acc = __ffma2_rn(c_kin2[0][l], make_float2(a, a), acc);
+            acc = __ffma2_rn(c_kin2[1][l], make_float2(b, b), acc);
+        }
+        o0[j] = acc.x;
+        o1[j] = acc.y;
+    }
+}
+#endif
 
 // ---------------------------------------------------------------- forward x, y
 
@@ -1956,7 +2024,18 @@ cudaError_t upload_filters(const FilterSet& fs, int device) {
     if ((e = cudaMemcpyToSymbol(c_fwd_d, fs.fwd, sizeof(fs.fwd))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_kin_d, fs.kin, sizeof(fs.kin))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_fwd_f, f32, sizeof(f32))) != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(c_kin_f, k32, sizeof(k32));
+    if ((e = cudaMemcpyToSymbol(c_kin_f, k32, sizeof(k32))) != cudaSuccess) return e;
+    float2 bwd2[FWD_TAPS], up2[2][16], kin2[2][KIN_TAPS];
+    for (int m = 0; m < FWD_TAPS; ++m) bwd2[m] = make_float2(f32[0][m], f32[1][m]);
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 16; ++k) up2[b][k] = make_float2(f32[b][2 * k], 2 * k + 1 < FWD_TAPS ? f32[b][2 * k + 1] : 0.f);
+    for (int l = 0; l < KIN_TAPS; ++l) {
+        kin2[0][l] = make_float2(k32[0][l], k32[2][l]);
+        kin2[1][l] = make_float2(k32[1][l], k32[3][l]);
+    }
+    if ((e = cudaMemcpyToSymbol(c_fwd2_bwd, bwd2, sizeof(bwd2))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_fwd2_up, up2, sizeof(up2))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_kin2, kin2, sizeof(kin2));
 }
 
 cudaError_t configure_kernels(size_t max_smem) {
