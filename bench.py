@@ -407,6 +407,12 @@ def gpu_main(args):
 
     # roofline denominators measured on this GPU (FMA loops, streaming copy)
     peaks = dict(zip(("fp32_fma_tflops", "fp64_fma_tflops", "copy_gbs"), lsw.lsw_measure_peaks(S.ctx)))
+    try:   # the pool's own copy / bf16 GEMM measurements, as context beside these
+        pool = json.load(open(PEAKS_PATH))
+        peaks["pool_hbm_gbs"] = pool.get("hbm_gbs")
+        peaks["pool_bf16_tflops"] = pool.get("bf16_tflops")
+    except Exception:
+        pass
     tune = None
     if not args.no_autotune and not args.batch and not args.tile:
         from paper_1401_7441_gb300 import autotune

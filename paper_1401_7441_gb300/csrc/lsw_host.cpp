@@ -386,8 +386,9 @@ lsw_status build_pattern(lsw_system_s* s) {
 
 int64_t align64(int64_t x) { return (x + ALIGN_ELEMS - 1) / ALIGN_ELEMS * ALIGN_ELEMS; }
 
-// smem bytes of the three pass kernels for a function record
-void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, size_t* bwd) {
+// smem bytes of the three pass kernels for a function record (bwd: with the z-arm plane
+// and flag staging; bwd_plain: without)
+void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, size_t* bwd, size_t* bwd_plain) {
     const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29, Z = 2 * r.n[2] + 29;
     const int64_t RS = r.n[0] | 1;
     *fwd = es * static_cast<size_t>(4 * r.n[1] * RS + 2 * r.n[1] * X);
@@ -396,6 +397,7 @@ void pass_smem(const FnRec& r, size_t es, int zcols, size_t* fwd, size_t* z, siz
     const int64_t midA = std::max<int64_t>(2LL * r.np[1] * X, 4LL * r.np[1] * r.np[0]);
     *bwd = es * static_cast<size_t>(plA + midA + 4 * r.n[1] * RS) +
            static_cast<size_t>((4 * r.n[0] * r.n[1] + 15) / 16 * 16);   // + z-arm column flags
+    *bwd_plain = es * static_cast<size_t>(plA + 2 * r.np[1] * X + 4 * r.n[1] * RS);
 }
 
 // Dynamic shared memory of the tensor-core z stage for a function record and `parts`
@@ -466,6 +468,7 @@ lsw_status build_plans(lsw_system_s* s) {
         p.prec = s->prec;
         p.nfn = static_cast<int>(b.nfn);
         p.zcols = zcols;
+        size_t smem_bwd_plain = 0;
         int64_t o = 0;
         for (int64_t f = f0; f < f0 + b.nfn; ++f) {
             recs[f].ws_D = o;
@@ -499,12 +502,13 @@ lsw_status build_plans(lsw_system_s* s) {
             p.max_rowsL = std::max(p.max_rowsL, r.n[1] * r.n[2]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
-            size_t a1, a2, a3;
-            pass_smem(r, s->esize, zcols, &a1, &a2, &a3);
+            size_t a1, a2, a3, a4;
+            pass_smem(r, s->esize, zcols, &a1, &a2, &a3, &a4);
             p.smem_fwd = std::max(p.smem_fwd, a1);
             p.smem_z = std::max(p.smem_z, a2);
             p.smem_kin = std::max(p.smem_kin, static_cast<size_t>(2 * r.n[2] * 128) * (p.prec == 0 ? 8 : 4));
             p.smem_bwd = std::max(p.smem_bwd, a3);
+            smem_bwd_plain = std::max(smem_bwd_plain, a4);
             if (s->zsplit) {
                 if (!ztc_fits(r))
                     return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core kernels");
@@ -517,6 +521,9 @@ lsw_status build_plans(lsw_system_s* s) {
                 }
             }
         }
+        // stage the z-arm plane and flags when they fit beside the plane kernel's tiles
+        p.gstage = p.smem_bwd + BWD_STATIC_SMEM <= s->ctx->max_smem ? 1 : 0;
+        if (!p.gstage) p.smem_bwd = smem_bwd_plain;
         p.zsplit = s->zsplit;
         p.xy_tc = s->zsplit ? s->xy_tc : 0;
         if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem ||
@@ -1155,6 +1162,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
         p.prec = sys->prec;
         p.nfn = nb;
         p.zcols = zcols;
+        size_t smem_bwd_plain = 0;
         int64_t o = 0;
         for (int k = 0; k < nb; ++k) {
             recs[k].ws_D = o;
@@ -1184,12 +1192,13 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             p.max_rowsL = std::max(p.max_rowsL, r.n[1] * r.n[2]);
             p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
             p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
-            size_t a1, a2, a3;
-            pass_smem(r, sys->esize, zcols, &a1, &a2, &a3);
+            size_t a1, a2, a3, a4;
+            pass_smem(r, sys->esize, zcols, &a1, &a2, &a3, &a4);
             p.smem_fwd = std::max(p.smem_fwd, a1);
             p.smem_z = std::max(p.smem_z, a2);
             p.smem_kin = std::max(p.smem_kin, static_cast<size_t>(2 * r.n[2] * 128) * (p.prec == 0 ? 8 : 4));
             p.smem_bwd = std::max(p.smem_bwd, a3);
+            smem_bwd_plain = std::max(smem_bwd_plain, a4);
             if (sys->zsplit) {
                 if (!ztc_fits(r))
                     return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core kernels");
@@ -1202,6 +1211,9 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
                 }
             }
         }
+        // stage the z-arm plane and flags when they fit beside the plane kernel's tiles
+        p.gstage = p.smem_bwd + BWD_STATIC_SMEM <= sys->ctx->max_smem ? 1 : 0;
+        if (!p.gstage) p.smem_bwd = smem_bwd_plain;
         p.zsplit = sys->zsplit;
         p.xy_tc = sys->zsplit ? sys->xy_tc : 0;
         if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > sys->ctx->max_smem ||

@@ -20,7 +20,7 @@ constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [
 constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
 constexpr int ZCOLS_F64 = 64;    // real-space columns per block of the z stage (FP64)
 constexpr int ZCOLS_F32 = 128;   // (FP32)
-constexpr size_t BWD_STATIC_SMEM = 14 * 1024;   // upper bound of k_bwd_xy's static shared memory
+constexpr size_t BWD_STATIC_SMEM = 13 * 1024 + 512;   // upper bound of k_bwd_xy's static shared memory
 
 // Filter tables, FP64 (rounded once from double-double).
 struct FilterSet {
@@ -89,6 +89,9 @@ struct HphiLaunch {
     int max_segL;                // largest coarse+fine segment count of L
     int max_segP;
     size_t smem_fwd, smem_z, smem_bwd;
+    int gstage;                  // 1: the plane kernel stages the z-arm plane and column flags
+                                 // in shared memory (smem_bwd includes them); 0: reads them
+                                 // from global memory (the boxes leave no room)
     int zcols;                   // columns per CTA of the z stage
     int zsplit;                  // 0: z stage on FMA units; 2 or 3: bfloat16 parts per
                                  // FP32 operand of the tensor-core z stage

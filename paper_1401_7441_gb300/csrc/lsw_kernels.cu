@@ -1292,7 +1292,8 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     unsigned char* sXr = sFx + NS * FX_PART;
     T* pl = sm;
     T* Gs = NS ? reinterpret_cast<T*>(sXr) : sm;
-    const int midA = max(2 * nyp * X, 4 * nyp * nxp);   // mid [2][nyp][X], later the z-arm plane
+    // mid [2][nyp][X], later (when the host found room: a.gstage) the z-arm plane
+    const int midA = (NS == 0 && a.gstage) ? max(2 * nyp * X, 4 * nyp * nxp) : 2 * nyp * X;
     T* mid = sm + plA;
     T* Dp = NS ? reinterpret_cast<T*>(sXr + XR) : mid + midA;
     const int64_t smem_n = static_cast<int64_t>((NS ? a.smem_bwd_tc : a.smem_bwd) / sizeof(T));
@@ -1338,14 +1339,14 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                 8 * plane);
         }
     }
-    // z-arm column flags of the L box (written by k_kin_z), 4 bytes per copy
+    // z-arm column flags of the L box (written by k_kin_z): staged, 4 bytes per copy, when
+    // the host found room (a.gstage), else read from global memory
+    const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(static_cast<const T*>(a.ws) + r.ws_Gf);
     uint32_t* gfl = reinterpret_cast<uint32_t*>(Dp + 4 * ny * RS);
     [[maybe_unused]] const int64_t gfl_n = (smem_n * static_cast<int64_t>(sizeof(T)) -
                                             (reinterpret_cast<unsigned char*>(gfl) - smem_raw)) / 4;
-    {
-        const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(static_cast<const T*>(a.ws) + r.ws_Gf);
+    if (a.gstage)
         for (int i = threadIdx.x; i < pn; i += blockDim.x) CPA(gfl, i, gfl_n, gsrc, i, pn);
-    }
     cp_commit();
     // member x range of each row of this plane (coarse part of L')
     for (int y = threadIdx.x; y < nyp; y += blockDim.x) {
@@ -1452,7 +1453,7 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                 }
             }
         }
-        if constexpr (NS == 0) {
+        if (NS == 0 && a.gstage) {
             // mid is dead: stage the z-arm plane G (types tb + 4 bz) for the compressed
             // write, in flight during the kinetic phases
             const T* G = static_cast<const T*>(a.ws) + r.ws_G;
@@ -1557,7 +1558,8 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     //      the FMA path reads it from the plane staged in mid)
     if (yhi_ >= 0) {
         const T* G = static_cast<const T*>(a.ws) + r.ws_G;
-        const unsigned char* gflag = reinterpret_cast<const unsigned char*>(gfl);   // staged above
+        const unsigned char* gflag = reinterpret_cast<const unsigned char*>(a.gstage ? gfl : gsrc);
+        const bool gsm = NS == 0 && a.gstage;               // the z-arm plane is in mid
         const int64_t gplane = static_cast<int64_t>(nxp) * nyp * nzp;
         T* out = static_cast<T*>(a.hphi) + r.off_hphi;
         const int64_t out_room = a.hphi_n - r.off_hphi;
@@ -1572,7 +1574,7 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                     const int x = xb + dx;
                     T v = LD(Gs, static_cast<int64_t>(b) * nxp + xb, gs_n);
                     if (yin && x >= 0 && x < nx && LD(gflag, y * nx + x, 4LL * pn))
-                        v += NS ? LD(G, grow + xb, 8 * gplane) : LD(mid, static_cast<int64_t>(b) * nxp + xb, midA);
+                        v += gsm ? LD(mid, static_cast<int64_t>(b) * nxp + xb, midA) : LD(G, grow + xb, 8 * gplane);
                     ST(out, roff[b] + (xb - rx0[b]), out_room, v);
                 }
             }
@@ -1589,8 +1591,8 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                         if (t == 0) continue;
                         T v = LD(Gs, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, gs_n);
                         if (zin && LD(gflag, (t & 3) * pn + y * nx + x, 4LL * pn))
-                            v += NS ? LD(G, t * gplane + grow + xb, 8 * gplane)
-                                    : LD(mid, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, midA);
+                            v += gsm ? LD(mid, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, midA)
+                                     : LD(G, t * gplane + grow + xb, 8 * gplane);
                         ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + fs.off + (xb - fs.x0), out_room, v);
                     }
                 }
@@ -1684,10 +1686,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) 
     // per-work-item sums in the panel precision (<= T^3 + 7 * fine points terms);
     // the sums over tiles are FP64 (the atomic adds into the CSR values)
     T sacc[4][4], hacc[4][4];
+    [[maybe_unused]] float2 sh2[4][4];     // FP32: (S, H) sums of pair (u, v), packed
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) sacc[u][v] = T(0), hacc[u][v] = T(0);
+        for (int v = 0; v < 4; ++v) sacc[u][v] = T(0), hacc[u][v] = T(0), sh2[u][v] = make_float2(0.f, 0.f);
     const T* phi = static_cast<const T*>(a.phi);
     const T* hphi = static_cast<const T*>(a.hphi);
     const int nslot = w.na + w.nb;
@@ -1765,16 +1768,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) 
                     vq[u] = LD(PQ, (tj + 16 * u) * HS_LD + k, PN - 2 * HS_BLK * HS_LD);
                 }
             }
+            if constexpr (sizeof(T) == 4) {
+                // (S, H) of a pair as the two lanes of one packed FMA (same bits as below)
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (u < UA && v < UB) {
-                        sacc[u][v] += va[u] * vb[v];
-                        hacc[u][v] += va[u] * vq[v];
-                    }
+                    for (int v = 0; v < 4; ++v)
+                        if (u < UA && v < UB)
+                            sh2[u][v] = __ffma2_rn(make_float2(va[u], va[u]), make_float2(vb[v], vq[v]), sh2[u][v]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (u < UA && v < UB) {
+                            sacc[u][v] += va[u] * vb[v];
+                            hacc[u][v] += va[u] * vq[v];
+                        }
+            }
         }
         __syncthreads();
+    }
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sacc[u][v] = sh2[u][v].x, hacc[u][v] = sh2[u][v].y;
     }
     // Pattern positions: the CSR rows of this item's a-functions are copied into the (now
     // free) panel memory, so each pair's binary search runs in shared memory; rows that do

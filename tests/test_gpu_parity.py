@@ -330,3 +330,14 @@ def test_atoms1200_full_size_sampled_fp32():
     wl = I.atoms1200()
     fs = list(range(12)) + [2047, 4095]
     _full_size_sampled(wl, lsw.LSW_FP32, {"batch": 128}, fs, [0, 1, 4], 1e-5)
+
+
+def test_fp64_largest_locregs_plane_kernel_without_staging():
+    # FP64 locregs of 8 bohr leave no shared-memory room for staging the z-arm plane in
+    # the backward plane kernel; the host then has it read from global memory
+    wl = I.scaled("atoms1200", 40, seed=31)
+    big = [i for i in range(len(wl.r_loc)) if wl.r_loc[i] >= 8.0 and wl.nsf[i] > 0]
+    assert big, "the scaled workload has an 8-bohr locreg"
+    first = np.concatenate([[0], np.cumsum(wl.nsf)])
+    fs = sorted({int(first[big[0]]), int(first[big[-1]]), 0})
+    _full_size_sampled(wl, lsw.LSW_FP64, {"batch": 8}, fs, fs[:1], 1e-12)
