@@ -87,19 +87,25 @@ def kernels_source_hash():
 
 
 def stored_traffic(kernel, workload, prec, batch):
-    """DRAM bytes per launch of ``kernel`` from profiles/roofline_traffic.json, if that
-    file was written from an ncu capture of the current kernel source (else None)."""
+    """(DRAM bytes per launch of ``kernel``, note) from profiles/roofline_traffic.json, if
+    that file was written from an ncu capture of the current kernel source (else (None,
+    reason)).  The plane and z-stage kernels move bytes in proportion to the functions of
+    a launch, so a capture at another batch size is scaled by the batch ratio."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
-        return None
+        return None, "no stored capture"
     if rec.get("kernels_sha256") != kernels_source_hash():
-        return None
+        return None, "stored capture is of another kernel source"
     ent = rec.get("kernels", {}).get(kernel)
-    if not ent or ent.get("precision") != prec or ent.get("batch") != batch:
-        return None
-    return ent.get("dram_bytes_per_launch")
+    if not ent or ent.get("precision") != prec or not batch:
+        return None, "no stored capture for this kernel and precision"
+    per = ent.get("dram_bytes_per_launch")
+    if ent.get("batch") == batch:
+        return per, "ncu capture, %s" % rec.get("note", "")
+    return per * batch / ent["batch"], ("ncu capture at batch %d scaled to batch %d by the functions per launch; %s"
+                                        % (ent["batch"], batch, rec.get("note", "")))
 
 
 def keys_to_g(keys):
@@ -487,9 +493,11 @@ def gpu_main(args):
             work_per_launch = flops[dom] / launches_per_step
             peak = peaks["fp64_fma_tflops"] if prec == "fp64" else peaks["fp32_fma_tflops"]
             ach = work_per_launch / (per_launch_ms / 1000.0) / 1e12
+            traffic, traffic_note = stored_traffic(dom, wl.name, prec,
+                                                   args.batch or (tune or {}).get("chosen", {}).get("batch"))
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak,
-                    "traffic": stored_traffic(dom, wl.name, prec, (tune or {}).get("chosen", {}).get("batch")),
+                    "traffic": traffic, "traffic_note": traffic_note,
                     "peak_source": "measured on this GPU: %s FMA loop over every SM (lsw_measure_peaks); "
                                    "nominal %.1f TFLOP/s" % ("FP64" if prec == "fp64" else "FP32",
                                                             FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS)}

@@ -10,8 +10,8 @@ from __future__ import annotations
 
 from . import lsw
 
-BATCH_CANDIDATES = (16, 32, 64, 128, 256)
-TILE_CANDIDATES = (4, 5, 6, 8)
+BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512)
+TILE_CANDIDATES = (3, 4, 5, 6, 8)
 
 
 def _time(fn, stream, reps):

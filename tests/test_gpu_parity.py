@@ -128,7 +128,8 @@ def test_options_do_not_change_results():
     base = gpu_run(wl, phi_fn(wl), lsw.LSW_FP64)
     # the alignment gaps between functions are never written (NaN from the fill)
     gap = np.isnan(base["hphi"])
-    for opts in ({"batch": 1}, {"batch": 7, "graph": 0}, {"tile": 4}, {"tile": 5, "batch": 64}):
+    for opts in ({"batch": 1}, {"batch": 7, "graph": 0}, {"tile": 3}, {"tile": 4}, {"tile": 5, "batch": 64},
+                 {"tile": 8, "batch": 512}):
         o = gpu_run(wl, phi_fn(wl), lsw.LSW_FP64, options=opts, repeat=2)
         assert np.array_equal(np.isnan(o["hphi"]), gap), opts
         d = np.abs(o["hphi"][~gap] - base["hphi"][~gap])
