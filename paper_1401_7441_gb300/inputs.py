@@ -403,3 +403,27 @@ def fill_phi(wl: Workload, phi, off_L, sf_atom, coarse_g, fine_g, chunk_coefs=1 
         dest = torch.as_tensor(np.asarray(off_L)[fs], device=dev)
         phi[torch.repeat_interleave(dest, cnt) + k] = v.to(phi.dtype)
         f = f1
+
+
+# ----------------------------------------------------------------- density kernel
+
+def density_kernel(wl: Workload, sf_atom, row_ptr, col, scale: float = 3.0):
+    """Seeded symmetric density kernel K on a CSR pattern (values in pattern order).
+
+    K_ab = (0.5 + xi) exp(-|R_A - R_B|^2 / (2 scale^2)), A, B the atoms of a and b, with
+    xi ~ U[0, 1) drawn once per unordered pair {a, b}: K_ab = K_ba whenever both entries
+    are stored.  A stand-in for a converged kernel: positive, decaying with distance."""
+    sf_atom = np.asarray(sf_atom, np.int64)
+    row_ptr = np.asarray(row_ptr, np.int64)
+    col = np.asarray(col, np.int64)
+    n = len(row_ptr) - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_ptr))
+    lo = np.minimum(rows, col)
+    hi = np.maximum(rows, col)
+    key = lo * n + hi
+    k = mix32(mix32((key & _M32) ^ (0x5BD1E995 & _M32)) ^ ((key >> 32) & _M32) ^ (wl.seed & _M32))
+    xi = (k.astype(np.float64) + 0.5) / 4294967296.0
+    pos = np.asarray(wl.pos, np.float64)
+    d = pos[sf_atom[rows]] - pos[sf_atom[col]]
+    d2 = np.sum(d * d, axis=1)
+    return (0.5 + xi) * np.exp(-d2 / (2.0 * scale * scale))

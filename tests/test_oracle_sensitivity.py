@@ -69,3 +69,54 @@ def test_high_pass_sign_in_synthesis_only(monkeypatch):
 
     monkeypatch.setattr(Hm, "synthesis3d", wrong)
     _fails(TO.test_analysis_inverts_synthesis_and_keeps_norm)
+
+
+# ------------------------------------------------------------------ density (Eq. density)
+
+from oracle import density as Dn
+from tests import test_oracle_density as TD
+
+
+def test_density_block_of_one_function_shifted(monkeypatch):
+    # the real-space block of function 1 placed one fine point off along x
+    real = Dn.realspace
+
+    def shifted(geo, f, phi_f, F):
+        u, st = real(geo, f, phi_f, F)
+        return u, [st[0] + 1, st[1], st[2]] if f == 1 else st
+
+    monkeypatch.setattr(Dn, "realspace", shifted)
+    _fails(TD.test_density_equals_dense_matrices, 5, 6, 1.2, 0.6)
+
+
+def test_density_lower_triangle_dropped(monkeypatch):
+    # only the entries a <= b of the kernel summed (a symmetry folded without the factor 2)
+    real = Dn.pattern_entries
+
+    def upper(row_ptr, col, K):
+        return [(a, b, k) for a, b, k in real(row_ptr, col, K) if a <= b]
+
+    monkeypatch.setattr(Dn, "pattern_entries", upper)
+    _fails(TD.test_density_trace_identity_with_potential_matrix)
+
+
+def test_density_square_instead_of_pair_product(monkeypatch):
+    # u_a^2 in place of u_a u_b
+    real = Dn.accumulate
+
+    def squares(fields, entries, lo, dims):
+        return real(fields, [(a, a, k) for a, b, k in entries], lo, dims)
+
+    monkeypatch.setattr(Dn, "accumulate", squares)
+    _fails(TD.test_density_of_two_gaussians_closed_form)
+
+
+def test_density_magic_filter_reversed(monkeypatch):
+    # the magic filter applied as a correlation (taps reversed) in the real-space values
+    real = Dn.realspace_block
+
+    def reversed_w(c, lo, F):
+        return real(c, lo, dataclasses.replace(F, magic=F.magic[::-1].copy()))
+
+    monkeypatch.setattr(Dn, "realspace_block", reversed_w)
+    _fails(TD.test_density_of_two_gaussians_closed_form)
