@@ -103,3 +103,44 @@ def density(geo, phi, K, grid_lo, grid_dims, F=None, absolute=False):
         v = np.asarray(phi[f], np.float64)
         fields[f] = realspace(geo, f, np.abs(v) if absolute else v, F)
     return accumulate(fields, entries, grid_lo, grid_dims)
+
+
+def density_points(geo, phi, K, points, F=None, absolute=False):
+    """rho_j at the listed fine points only: at each point, the sum over the pattern
+    entries (a, b) of K_ab u_a(j) u_b(j) for the functions a, b whose blocks contain it
+    (taken row by row of the pattern; same steps as ``density`` otherwise).
+
+    ``points``: (n, 3) global fine indices (x, y, z).  ``phi`` maps function -> vector
+    for at least the functions whose blocks contain a point.  Returns (n,) values."""
+    F = F or _filters.load()
+    Kv = np.asarray(K, np.float64)
+    if absolute:
+        F = abs_filters(F)
+        Kv = np.abs(Kv)
+    pts = np.asarray(points, np.int64).reshape(-1, 3)
+    rp, col = geo.row_ptr, geo.col
+    # real-space block of every function: fine points [2 lo - 14, 2 hi + 16]
+    blo = np.array([2 * np.asarray(geo.L[a].lo) - 14 for a in geo.sf_atom], np.int64).reshape(-1, 3)
+    bhi = np.array([2 * np.asarray(geo.L[a].hi) + 16 for a in geo.sf_atom], np.int64).reshape(-1, 3)
+    covers = [np.nonzero(np.all((blo <= p) & (p <= bhi), axis=1))[0] for p in pts]
+    fields = {}
+    for f in sorted(set(int(f) for c in covers for f in c)):
+        v = np.asarray(phi[f], np.float64)
+        fields[f] = realspace(geo, f, np.abs(v) if absolute else v, F)
+    out = np.zeros(len(pts))
+    for i, p in enumerate(pts):
+        C = covers[i]
+        if len(C) == 0:
+            continue
+        uval = np.empty(len(C))
+        for j, f in enumerate(C):
+            u, st = fields[int(f)]
+            uval[j] = u[p[0] - st[0], p[1] - st[1], p[2] - st[2]]
+        acc = 0.0
+        for ia, a in enumerate(C):
+            cols = col[rp[a]:rp[a + 1]]
+            sel = np.isin(cols, C)
+            ub = uval[np.searchsorted(C, cols[sel])]
+            acc += uval[ia] * float(np.dot(Kv[rp[a]:rp[a + 1]][sel], ub))
+        out[i] = acc
+    return out

@@ -118,3 +118,19 @@ def test_density_positive_kernel_gives_nonnegative_density():
     assert rho.min() >= -1e-15 * rho_abs.max()
     assert np.all(np.abs(rho) <= rho_abs * (1 + 1e-14) + 1e-300)
     assert rho.max() > 1e-6 * rho_abs.max()
+
+
+def test_density_points_equal_the_grid_values():
+    # the point-sampled form used at sizes where the whole grid is out of reach
+    wl = tiny_workload(n=7, seed=21, n_atoms=3, r_loc=1.3, r_fine=0.7)
+    geo = G.build(desc_of(wl))
+    phi = phi_all(wl, geo)
+    K = I.density_kernel(wl, geo.sf_atom, geo.row_ptr, geo.col)
+    rho = Dn.density(geo, phi, K, wl.V_lo, wl.V_shape)
+    rng = np.random.default_rng(2)
+    pts = np.stack([rng.integers(wl.V_lo[d], wl.V_lo[d] + wl.V_shape[d], 40) for d in range(3)], axis=1)
+    pts[0] = np.unravel_index(np.argmax(rho), rho.shape)[::-1] + np.asarray(wl.V_lo)
+    got = Dn.density_points(geo, phi, K, pts)
+    ref = rho[pts[:, 2] - wl.V_lo[2], pts[:, 1] - wl.V_lo[1], pts[:, 0] - wl.V_lo[0]]
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(rho))
+    assert got[0] == pytest.approx(rho.max(), rel=1e-13)
