@@ -52,11 +52,12 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="atoms10k")
+    p.add_argument("--workload", default=None, help="default atoms10k (atoms1200 for --mode density)")
     p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64", "bf16x"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="step", choices=["step", "serving"],
-                   help="serving: Poisson request stream through the continuous-batching server")
+    p.add_argument("--mode", default="step", choices=["step", "serving", "density"],
+                   help="serving: Poisson request stream through the continuous-batching server; "
+                        "density: rho = sum_ab K_ab phi_a phi_b on the fine grid (default workload atoms1200)")
     p.add_argument("--requests", type=int, default=60)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -204,7 +205,7 @@ def reference_main(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    wl = workload(args.workload)
+    wl = workload(args.workload or "atoms10k")
     prec = args.precision or wl.precision
     # the whole --steps/--warmup run must end within a few minutes: bound each step
     per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
@@ -376,7 +377,7 @@ def gpu_main(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     B.build()
-    wl = workload(args.workload)
+    wl = workload(args.workload or "atoms10k")
     prec = args.precision or wl.precision
     P = {"fp64": lsw.LSW_FP64, "fp32": lsw.LSW_FP32, "bf16x": lsw.LSW_FP32_BF16X}[prec]
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -586,12 +587,156 @@ def serving_main(args):
     return 0
 
 
+def density_work(wl, geo_boxes, row_ptr, col):
+    """Algorithmic work of one density build.  The quadratic form at a point needs, with
+    K's symmetry, one multiply-add per unordered pattern pair (a <= b) whose real-space
+    blocks both contain the point, and one per function there (the outer product):
+    FMAs = sum over pattern pairs a <= b of |B_a n B_b| + sum_a |B_a|."""
+    lo, hi = geo_boxes                     # (n_sf, 3) inclusive fine-index blocks
+    n = len(row_ptr) - 1
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    cols = np.asarray(col, np.int64)
+    keep = rows <= cols
+    a, b = rows[keep], cols[keep]
+    ext = np.clip(np.minimum(hi[a], hi[b]) - np.maximum(lo[a], lo[b]) + 1, 0, None)
+    pair_pts = float(np.sum(np.prod(ext.astype(np.float64), axis=1)))
+    own = float(np.sum(np.prod((hi - lo + 1).astype(np.float64), axis=1)))
+    return pair_pts + own
+
+
+def density_main(args):
+    """Throughput of lsw_build_density (Eq. density) on a locreg workload: support
+    functions per second for the real-space values of every function plus the density
+    on the whole fine grid, inputs resident in HBM, L2 flushed before every step."""
+    import torch
+    from paper_1401_7441_gb300 import build as B
+    from paper_1401_7441_gb300 import lsw
+    torch.cuda.set_device(0)
+    B.build()
+    wl = workload(args.workload or "atoms1200")
+    prec = args.precision or ("fp64" if wl.precision == "fp64" else "fp32")
+    P = {"fp64": lsw.LSW_FP64, "fp32": lsw.LSW_FP32, "bf16x": lsw.LSW_FP32_BF16X}[prec]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t_setup = time.perf_counter()
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   wl.lprime_margin, 0, P, device=0, stream=stream.cuda_stream)
+    phi = torch.zeros(S.total_L, dtype=dt, device="cuda")
+    atoms = sorted(set(int(a) for a in S.sf_atom))
+    cg = {a: keys_to_g(S.keys(a, 0, 0)) for a in atoms}
+    fg = {a: keys_to_g(S.keys(a, 0, 1)) for a in atoms}
+    I.fill_phi(wl, phi, S.off_L, S.sf_atom, cg, fg)
+    Kh = I.density_kernel(wl, S.sf_atom, S.row_ptr, S.col)
+    K = torch.tensor(Kh, dtype=torch.float64, device="cuda")
+    dims = wl.V_shape
+    rho = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def box(k):
+        g0, g1 = k[:, 0], k[:, 1]
+        return (np.array([(g0 % wl.N[0]).min(), ((g0 // wl.N[0]) % wl.N[1]).min(), (g0 // (wl.N[0] * wl.N[1])).min()]),
+                np.array([(g1 % wl.N[0]).max(), ((g1 // wl.N[0]) % wl.N[1]).max(), (g1 // (wl.N[0] * wl.N[1])).max()]))
+    bx = {a: box(S.keys(a, 0, 0)) for a in atoms}
+    blo = np.array([2 * bx[int(a)][0] - 14 for a in S.sf_atom])
+    bhi = np.array([2 * bx[int(a)][1] + 16 for a in S.sf_atom])
+    fma = density_work(wl, (blo, bhi), S.row_ptr, S.col)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
+    def step():
+        lsw.lsw_build_density(S.sys, phi, K, rho, wl.V_lo, dims)
+
+    peaks = dict(zip(("fp32_fma_tflops", "fp64_fma_tflops", "copy_gbs"), lsw.lsw_measure_peaks(S.ctx)))
+    for _ in range(max(1, args.warmup)):
+        step()
+    lsw.lsw_sync(S.sys, 600.0)
+    lsw.lsw_profile(S.sys, 1)
+    step()
+    lsw.lsw_profile_read(S.sys)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    prof = {}
+    with ClockSampler(os.path.join(tempfile.gettempdir(), "lsw_clk_dens_%d.csv" % os.getpid())) as clk:
+        time.sleep(0.3)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+            torch.cuda.synchronize()
+            for k, (ms, n) in lsw.lsw_profile_read(S.sys).items():
+                a, b = prof.get(k, (0.0, 0))
+                prof[k] = (a + ms, b + n)
+    lsw.lsw_profile(S.sys, 0)
+    lsw.lsw_sync(S.sys, 60.0)
+    step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    roof = None
+    if "dens_products" in kinds:
+        ms_tot, n_launch = kinds["dens_products"]
+        ach = 2.0 * fma / (ms_tot / n_launch / 1000.0) / 1e12
+        peak = peaks["fp64_fma_tflops"] if prec == "fp64" else peaks["fp32_fma_tflops"]
+        roof = {"kernel": "dens_products", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "work": "2 x (sum over pattern pairs a <= b of the points both real-space blocks contain "
+                        "+ sum of block sizes) = %.3e flop per launch" % (2.0 * fma),
+                "peak_source": "measured on this GPU: %s FMA loop over every SM (lsw_measure_peaks)"
+                               % ("FP64" if prec == "fp64" else "FP32")}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import density as Dn
+        from oracle import filters as OF
+        from oracle import geometry as G
+        c = np.asarray(wl.pos).mean(axis=0)
+        near = set(np.nonzero(np.sum((np.asarray(wl.pos) - c) ** 2, axis=1) <= 8.0 ** 2)[0].tolist())
+        sel = [f for f in range(S.n_sf) if int(S.sf_atom[f]) in near]
+        t0 = time.perf_counter()
+        desc = G.SystemDesc(tuple(wl.N), wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff,
+                            wl.pair_mode, wl.lprime_margin, wl.fine_mode)
+        geo = G.build(desc, atoms=sorted(near), pattern=False)
+        FO = OF.load()
+        fields = {}
+        for f in sel:
+            L = geo.L[int(S.sf_atom[f])]
+            fields[f] = Dn.realspace(geo, f, I.phi_values(wl, f, int(S.sf_atom[f]), L.coarse.g, L.fine.g), FO)
+        ents = [(a, int(S.col[k]), float(Kh[k])) for a in sel for k in range(S.row_ptr[a], S.row_ptr[a + 1])
+                if int(S.col[k]) in fields]
+        Dn.accumulate(fields, ents, wl.V_lo, dims)
+        el = time.perf_counter() - t0
+        cpu = {"value": len(sel) / el, "unit": "support_functions/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle (numpy FP64, 1 thread of %d host cores): real-space values of the %d functions "
+                         "on the atoms within 8 bohr of the centre and the density of the %d pattern entries "
+                         "among them on the whole grid; %.1f s" % (os.cpu_count() or 1, len(sel), len(ents), el)}
+    line = {"metric": "density build: support functions/s (real-space values + rho on the fine grid)",
+            "value": S.n_sf * args.steps / (total_ms / 1000.0), "unit": "support_functions/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16x": "f32"}[prec] + " (FP64 sums per point)",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "atoms": len(wl.pos), "support_functions": S.n_sf,
+                       "pattern_nnz": len(S.col), "grid_points": int(np.prod(dims)), "precision": prec,
+                       "l2": "flushed (512 MB write) before every timed step"},
+            "roofline": roof, "cpu_baseline": cpu, "peaks_measured": peaks, "clocks": clk.summary(0),
+            "gpu_launches": int(sum(v[1] for v in kinds.values())) if kinds else None,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+            "algorithmic_gflop_per_step": 2.0 * fma / 1e9,
+            "workspace_gb": lsw.lsw_workspace_bytes(S.sys) / 1e9, "setup_s": t_setup, "step_ms": step_ms}
+    print(json.dumps(line))
+    S.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
     if args.mode == "serving":
         return serving_main(args)
+    if args.mode == "density":
+        return density_main(args)
     return gpu_main(args)
 
 

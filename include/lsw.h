@@ -202,6 +202,33 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi_dev, vo
 lsw_status lsw_build_matrices(lsw_system sys, const void* phi_dev, const void* hphi_dev,
                               double* H_dev, double* S_dev);
 
+/* Electronic density (Sec. II.A, Eq. density; App. D forms it like the scalar
+ * products): rho_j = sum_ab K_ab u_a(j) u_b(j) at every fine point x_j = j h/2 of the
+ * grid block [fine_lo, fine_lo + fine_dims), where u_a = M W L phi_a are the real-space
+ * values of support function a (uncompress, one-level synthesis, magic filter: the
+ * values the potential step of lsw_apply_hamiltonian multiplies), defined on the fine
+ * points [2 lo - 14, 2 hi + 16] of its locreg's coarse bounding box [lo, hi], 0 outside.
+ * rho_j is the electron count carried by point j; the density there is rho_j / (h/2)^3.
+ * - phi_dev: compressed support functions (layout of lsw_system_layout), FP64 for an
+ *   FP64 system, FP32 otherwise.
+ * - K_dev: FP64 values of the density kernel on the pattern (lsw_pattern): K_dev[k]
+ *   belongs to the k-th entry (a, b); entries outside the pattern count as 0.  K need
+ *   not be symmetric (the result depends only on its symmetric part).
+ * - rho_dev: FP64 output, fine_dims[2] x fine_dims[1] x fine_dims[0] values stored
+ *   [z][y][x] (x fastest), every point written.
+ * - The grid must cover fine indices [-14, 2 N_d + 14] in every dimension (the points
+ *   any block reaches), like the potential.
+ * The real-space values are computed in the system's precision (FP64, or FP32 with FMA
+ * arithmetic for LSW_FP32 and LSW_FP32_BF16X); the pair products of a point run in that
+ * precision per group of 32 x 32 functions, the sum over groups in FP64.  The first
+ * call for a grid builds per-tile function lists on the host and allocates a device
+ * store of every function's real-space block (counted by lsw_workspace_bytes); later
+ * calls on the same grid reuse them.  Asynchronous.
+ * Errors: LSW_ERR_ARG (NULL, grid not covering), LSW_ERR_STATE (host-only context),
+ * LSW_ERR_UNSUPPORTED (grid too large), LSW_ERR_OOM / LSW_ERR_CUDA. */
+lsw_status lsw_build_density(lsw_system sys, const void* phi_dev, const double* K_dev, double* rho_dev,
+                             const int64_t fine_lo[3], const int64_t fine_dims[3]);
+
 /* Reuse support functions on a changed geometry (the paper moves them with the atoms
  * between geometry steps, section "Flexibility of the minimal basis formalism",
  * subsection "Geometry optimization", with an interpolation scheme it does not
@@ -253,7 +280,8 @@ lsw_status lsw_profile(lsw_system sys, int32_t enable);
 
 /* Summed device milliseconds and launch counts per kernel kind since the last read,
  * kinds in this order: 0 memset, 1 uncompress, 2 forward xy, 3 z stage with V,
- * 4 backward xy (with the compressed write), 5 kinetic z arm, 6 (unused), 7 H/S tiles.  Waits for the stream.  Writes
+ * 4 backward xy (with the compressed write), 5 kinetic z arm, 6 (unused), 7 H/S tiles,
+ * 8 density real-space values, 9 density pair products.  Waits for the stream.  Writes
  * min(max_kinds, *n_kinds) entries of ms[] and launches[]; resets the totals. */
 lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds, double* ms,
                             int64_t* launches);

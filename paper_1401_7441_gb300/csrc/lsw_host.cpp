@@ -187,6 +187,12 @@ struct lsw_system_s {
     DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
     DeviceBuf d_tile_org, d_tile_fine, d_listA, d_listB, d_work, d_ws, d_status, d_escratch;
     DeviceBuf d_shift, d_fn_all;   // reformat: per-atom shifts, records of every function
+    // density: real-space store, block records, tile lists (built for one grid)
+    DeviceBuf d_U, d_dfn, d_tptr, d_tfn;
+    bool dens_ready = false;
+    int64_t dens_lo[3] = {0, 0, 0}, dens_n[3] = {0, 0, 0};
+    int32_t dens_ntile[3] = {0, 0, 0};
+    int64_t U_elems = 0;
     std::vector<Batch> batches;
     int64_t ws_elems = 0;
     int batch_size = 0;
@@ -201,7 +207,7 @@ struct lsw_system_s {
         cudaGraphExec_t exec = nullptr;
         std::unique_ptr<Tracer> tr;
     };
-    std::map<GraphKey, GraphEntry> graphs_h, graphs_m;
+    std::map<GraphKey, GraphEntry> graphs_h, graphs_m, graphs_d;
     int profiling = 0;
     std::unique_ptr<Tracer> direct_tr;   // tracer of work enqueued without a graph
     double prof_ms[TK_COUNT] = {0};
@@ -670,8 +676,10 @@ lsw_status upload_geometry(lsw_system_s* s) {
 void drop_graphs(lsw_system_s* s) {
     for (auto& kv : s->graphs_h) cudaGraphExecDestroy(kv.second.exec);
     for (auto& kv : s->graphs_m) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& kv : s->graphs_d) cudaGraphExecDestroy(kv.second.exec);
     s->graphs_h.clear();
     s->graphs_m.clear();
+    s->graphs_d.clear();
 }
 
 // fold the elapsed times of a tracer's recorded pairs into the system's totals
@@ -764,6 +772,114 @@ lsw_status enqueue_matrices(lsw_system_s* s, Tracer* tr, const void* phi, const 
     p.n_atoms = s->n_atoms;
     p.n_sf = static_cast<int>(s->sf_atom.size());
     CUDA_TRY(enqueue_hs(p, st));
+    return LSW_OK;
+}
+
+// Density plan for the grid [lo, lo + dims): each function's real-space block (origin on
+// the grid, extents, offset in the store) and, per tile of the grid, the functions whose
+// blocks meet it (ascending).  Allocates the store.
+lsw_status build_density_plan(lsw_system_s* s, const int64_t* lo, const int64_t* dims) {
+    const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+    std::vector<DensFn> dfn(nf);
+    int64_t off = 0;
+    for (int64_t f = 0; f < nf; ++f) {
+        const LocregHost& L = s->L[s->sf_atom[f]];
+        DensFn& r = dfn[f];
+        r.off = off;
+        int64_t vol = 1;
+        for (int d = 0; d < 3; ++d) {
+            r.o[d] = static_cast<int32_t>(2LL * L.lo[d] - V_REACH - lo[d]);
+            r.d[d] = 2 * L.n[d] + 29;
+            vol *= r.d[d];
+        }
+        off += align64(vol);
+    }
+    const int tdim[3] = {DT_X, DT_Y, DT_Z};
+    int32_t nt[3];
+    for (int d = 0; d < 3; ++d) nt[d] = static_cast<int32_t>((dims[d] + tdim[d] - 1) / tdim[d]);
+    const int64_t ntiles = static_cast<int64_t>(nt[0]) * nt[1] * nt[2];
+    if (ntiles > (1LL << 31) - 1) return fail(LSW_ERR_UNSUPPORTED, "lsw_build_density: grid has too many tiles");
+    std::vector<int64_t> tptr(ntiles + 1, 0);
+    auto each_tile = [&](const DensFn& r, auto fn) {
+        int32_t t0[3], t1[3];
+        for (int d = 0; d < 3; ++d) {
+            t0[d] = r.o[d] / tdim[d];
+            t1[d] = (r.o[d] + r.d[d] - 1) / tdim[d];
+        }
+        for (int32_t z = t0[2]; z <= t1[2]; ++z)
+            for (int32_t y = t0[1]; y <= t1[1]; ++y)
+                for (int32_t x = t0[0]; x <= t1[0]; ++x) fn((static_cast<int64_t>(z) * nt[1] + y) * nt[0] + x);
+    };
+    for (int64_t f = 0; f < nf; ++f) each_tile(dfn[f], [&](int64_t t) { tptr[t + 1]++; });
+    for (int64_t t = 0; t < ntiles; ++t) tptr[t + 1] += tptr[t];
+    std::vector<int32_t> tfn(static_cast<size_t>(tptr[ntiles]));
+    {
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int64_t f = 0; f < nf; ++f)
+            each_tile(dfn[f], [&](int64_t t) { tfn[fill[t]++] = static_cast<int32_t>(f); });
+    }
+    s->dens_ready = false;
+    cudaStream_t st = s->stream;
+    CUDA_TRY(s->d_dfn.upload(dfn, st));
+    CUDA_TRY(s->d_tptr.upload(tptr, st));
+    CUDA_TRY(s->d_tfn.upload(tfn, st));
+    CUDA_TRY(s->d_U.alloc(static_cast<size_t>(off) * s->esize));
+    s->U_elems = off;
+    for (int d = 0; d < 3; ++d) {
+        s->dens_lo[d] = lo[d];
+        s->dens_n[d] = dims[d];
+        s->dens_ntile[d] = nt[d];
+    }
+    s->dens_ready = true;
+    return LSW_OK;
+}
+
+lsw_status enqueue_density_all(lsw_system_s* s, Tracer* tr, const void* phi, const double* K, double* rho) {
+    cudaStream_t st = s->stream;
+    for (const Batch& b : s->batches) {
+        HphiLaunch p = b.proto;
+        p.tr = tr;
+        p.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
+        p.seg = static_cast<const Seg*>(s->d_seg.p);
+        p.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
+        p.phi = phi;
+        p.ws = s->d_ws.p;
+        p.status = static_cast<int*>(s->d_status.p);
+        p.phi_n = s->off_L.back();
+        p.ws_n = s->ws_elems;
+        p.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
+        p.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
+        p.n_atoms = s->n_atoms;
+        p.U = s->d_U.p;
+        p.dfn = static_cast<const DensFn*>(s->d_dfn.p);
+        p.U_n = s->U_elems;
+        CUDA_TRY(enqueue_dens_batch(p, st));
+    }
+    DensLaunch d;
+    std::memset(&d, 0, sizeof(d));
+    d.tr = tr;
+    d.prec = s->prec;
+    d.fn = static_cast<const DensFn*>(s->d_dfn.p);
+    d.U = s->d_U.p;
+    d.tptr = static_cast<const int64_t*>(s->d_tptr.p);
+    d.tfn = static_cast<const int32_t*>(s->d_tfn.p);
+    d.row_ptr = static_cast<const int64_t*>(s->d_rowp.p);
+    d.col = static_cast<const int32_t*>(s->d_col.p);
+    d.K = K;
+    d.rho = rho;
+    for (int k = 0; k < 3; ++k) {
+        d.gn[k] = s->dens_n[k];
+        d.ntile[k] = s->dens_ntile[k];
+    }
+    d.status = static_cast<int*>(s->d_status.p);
+    d.U_n = s->U_elems;
+    d.tfn_n = static_cast<int64_t>(s->d_tfn.bytes / sizeof(int32_t));
+    d.nnz = static_cast<int64_t>(s->col.size());
+    d.rho_n = s->dens_n[0] * s->dens_n[1] * s->dens_n[2];
+    d.fn_n = static_cast<int64_t>(s->sf_atom.size());
+    d.tptr_n = static_cast<int64_t>(s->d_tptr.bytes / sizeof(int64_t));
+    d.rowp_n = static_cast<int64_t>(s->row_ptr.size());
+    CUDA_TRY(enqueue_density(d, st));
     return LSW_OK;
 }
 
@@ -1096,6 +1212,32 @@ lsw_status lsw_build_matrices(lsw_system sys, const void* phi, const void* hphi,
     return run_maybe_graph(sys, &sys->graphs_m, key, [&](Tracer* tr) { return enqueue_matrices(sys, tr, phi, hphi, H, S); });
 }
 
+lsw_status lsw_build_density(lsw_system sys, const void* phi, const double* K, double* rho, const int64_t fine_lo[3],
+                             const int64_t fine_dims[3]) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !phi || !K || !rho || !fine_lo || !fine_dims) return fail(LSW_ERR_ARG, "lsw_build_density: NULL argument");
+    for (int d = 0; d < 3; ++d) {
+        const int64_t need_lo = -V_REACH, need_hi = 2LL * sys->N[d] + V_REACH;
+        if (fine_dims[d] < 1 || fine_lo[d] > need_lo || fine_lo[d] + fine_dims[d] - 1 < need_hi)
+            return fail(LSW_ERR_ARG, "lsw_build_density: dimension %d covers [%lld, %lld], needs [%lld, %lld]", d,
+                        static_cast<long long>(fine_lo[d]), static_cast<long long>(fine_lo[d] + fine_dims[d] - 1),
+                        static_cast<long long>(need_lo), static_cast<long long>(need_hi));
+        if (fine_dims[d] > (1LL << 30)) return fail(LSW_ERR_ARG, "lsw_build_density: dimension %d too large", d);
+    }
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    bool same = sys->dens_ready;
+    for (int d = 0; d < 3; ++d) same = same && sys->dens_lo[d] == fine_lo[d] && sys->dens_n[d] == fine_dims[d];
+    if (!same) {
+        for (auto& kv : sys->graphs_d) cudaGraphExecDestroy(kv.second.exec);
+        sys->graphs_d.clear();
+        lsw_status rs = build_density_plan(sys, fine_lo, fine_dims);
+        if (rs != LSW_OK) return rs;
+    }
+    GraphKey key{phi, K, rho, nullptr};
+    return run_maybe_graph(sys, &sys->graphs_d, key, [&](Tracer* tr) { return enqueue_density_all(sys, tr, phi, K, rho); });
+}
+
 // Allocation-free variant of lsw_apply_hamiltonian.  Works like it, batch by batch, but
 // every batch's workspace and its function records live in the library's fixed device
 // array (noalloc_scratch); the batches are planned here on the stack, the records are
@@ -1329,7 +1471,8 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
                                &sys->d_sfatom, &sys->d_rowp, &sys->d_col, &sys->d_tile_org, &sys->d_tile_fine,
                                &sys->d_listA, &sys->d_listB, &sys->d_work, &sys->d_ws, &sys->d_status,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
-                               &sys->d_ep, &sys->d_shift, &sys->d_fn_all};
+                               &sys->d_ep, &sys->d_shift, &sys->d_fn_all, &sys->d_U, &sys->d_dfn,
+                               &sys->d_tptr, &sys->d_tfn};
     int64_t b = 0;
     for (auto* p : bufs) b += static_cast<int64_t>(p->bytes);
     *bytes = b;

@@ -49,6 +49,21 @@ struct AtomRec {
     int64_t rowLc, rowLf, rowPc, rowPf;  // first index of the per-row CSR (n_rows + 1)
 };
 
+// One support function's real-space block in the density store (Eq. density): the
+// values u = M W L phi on the fine points [2 lo - 14, 2 hi + 16] of its L box, stored
+// [Z][Y][X] (x fastest) from element `off`.
+struct DensFn {
+    int64_t off;
+    int32_t o[3];                // block origin, as a fine index local to the density grid
+    int32_t d[3];                // X, Y, Z = 2 n + 29
+};
+
+// Density tiles: DT_X x DT_Y x DT_Z fine points (x fastest), one CTA each.
+constexpr int DT_X = 32, DT_Y = 4, DT_Z = 4;
+constexpr int DT_THREADS = 256;
+constexpr int DT_PP = DT_X * DT_Y * DT_Z / DT_THREADS;   // points per thread
+constexpr int DT_MC = 32;                                 // functions per chunk
+
 // One support function inside an H phi batch.
 struct FnRec {
     int32_t f, atom;
@@ -66,7 +81,8 @@ struct HSWork {
 
 // Kernel kinds of the per-launch device trace (lsw_profile / lsw_profile_read).
 enum TraceKind : int {
-    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_RESERVED, TK_HS, TK_COUNT
+    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_RESERVED, TK_HS,
+    TK_DENS_U, TK_DENSITY, TK_COUNT
 };
 
 // Host-side recorder of CUDA event pairs around launches; NULL = no tracing.
@@ -117,6 +133,29 @@ struct HphiLaunch {
     // extents used by the self-checking build (-DLSW_CHECKED)
     int64_t phi_n, hphi_n, v_n, ws_n, seg_n, rowptr_n;
     int n_atoms;
+    // density: real-space store written by the density z stage (NULL otherwise)
+    void* U;
+    const DensFn* dfn;           // per function (indexed by FnRec::f)
+    int64_t U_n;
+};
+
+// The density products rho_j = sum_ab K_ab u_a(j) u_b(j) over the tiles of the grid.
+struct DensLaunch {
+    Tracer* tr;
+    int prec;
+    const DensFn* fn;            // per function
+    const void* U;               // real-space store
+    const int64_t* tptr;         // [ntiles + 1]: functions of tile t are tfn[tptr[t] .. tptr[t+1])
+    const int32_t* tfn;          // ascending within a tile
+    const int64_t* row_ptr;      // pattern CSR
+    const int32_t* col;
+    const double* K;             // density kernel on the pattern
+    double* rho;                 // [gz][gy][gx]
+    int64_t gn[3];               // grid extents
+    int32_t ntile[3];
+    int* status;
+    // extents used by the self-checking build (-DLSW_CHECKED)
+    int64_t U_n, tfn_n, nnz, rho_n, fn_n, tptr_n, rowp_n;
 };
 
 struct HSLaunch {
@@ -179,6 +218,8 @@ cudaError_t measure_peaks(int n_sm, double* fp32_tflops, double* fp64_tflops, do
 cudaError_t configure_kernels(size_t max_smem);
 cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s);
 cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s);
+cudaError_t enqueue_dens_batch(const HphiLaunch& a, cudaStream_t s);   // real-space values
+cudaError_t enqueue_density(const DensLaunch& a, cudaStream_t s);      // pair products
 
 // Status word bits set by device-side checks.
 enum : int {

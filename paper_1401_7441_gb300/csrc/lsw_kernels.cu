@@ -543,6 +543,52 @@ __global__ void __launch_bounds__(ZCols<T>::C) k_z(HphiLaunch a) {
     if ((threadIdx.x & 31) == 0 && epot != 0.0) atomicAdd(a.e_pot + r.f, epot);
 }
 
+// ---------------------------------------------------------------- density: real-space values
+
+// The forward half of k_z for the density (Eq. density): per (x', y') column, synthesis +
+// magic filter along z, and the real-space values u written to the function's block of
+// the density store (no potential, no backward pass).
+template <class T>
+__global__ void __launch_bounds__(ZCols<T>::C) k_z_dens(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 12;
+    constexpr int C = ZCols<T>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* cin = reinterpret_cast<T*>(smem_raw);   // [2][nz][C] (each thread owns its column)
+    const FnRec r = a.fn[blockIdx.y];
+    const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
+    const int X = 2 * nx + 29, Y = 2 * ny + 29, Z = 2 * nz + 29;
+    const int cols = X * Y;
+    const int c = blockIdx.x * C + threadIdx.x;
+    if (c >= cols) return;   // no barrier below: threads leave independently
+    const int t = threadIdx.x;
+    [[maybe_unused]] const int64_t smem_n = static_cast<int64_t>(a.smem_z / sizeof(T));
+    const T* Bf = static_cast<const T*>(a.ws) + r.ws_Bf;
+    const DensFn df = a.dfn[r.f];
+    T* U = static_cast<T*>(a.U) + df.off;
+    [[maybe_unused]] const int64_t room = a.U_n - df.off;
+    for (int q = 0; q < 2 * nz; ++q)
+        CPA(cin, q * C + t, smem_n, Bf, static_cast<int64_t>(q) * cols + c, 2LL * nz * cols);
+    cp_wait();
+    for (int p0 = 0; 2 * p0 < Z; p0 += FB) {
+        T w0[FW], w1[FW], u[2 * FB];
+        const int q0 = p0 - 15;
+#pragma unroll
+        for (int i = 0; i < FW; ++i) {
+            const int q = q0 + i;
+            const bool ok = q >= 0 && q < nz;
+            w0[i] = ok ? LD(cin, q * C + t, smem_n) : T(0);
+            w1[i] = ok ? LD(cin, (nz + q) * C + t, smem_n) : T(0);
+        }
+        fwd_block(w0, w1, u);
+#pragma unroll
+        for (int k = 0; k < 2 * FB; ++k) {
+            const int zo = 2 * p0 + k;
+            if (zo < Z) ST(U, static_cast<int64_t>(zo) * cols + c, room, u[k]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- z stage on tensor cores
 //
 // The z stage of k_z cast as two band-Toeplitz products per tile of 128 real-space
@@ -1857,6 +1903,142 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) 
     }
 }
 
+// ---------------------------------------------------------------- density: pair products
+//
+// rho_j = sum_ab K_ab u_a(j) u_b(j) (Eq. density) per tile of DT_X x DT_Y x DT_Z grid
+// points, over the functions whose real-space blocks meet the tile (App. D: the density
+// is formed like the scalar products, from the functions present at each point).  The
+// quadratic form depends only on the symmetric part of K, so the functions of a tile are
+// taken in chunks of DT_MC and every pair of chunks A <= B once: the coefficient block is
+// K_ab for A = B and K_ab + K_ba for A < B.  Each thread owns DT_PP points and keeps the
+// B chunk's values there in registers; the coefficient block sits in shared memory and is
+// read as a broadcast.  Products and the chunk-pair partial sums run in T, the total per
+// point in FP64; every point of the grid is written (0 where no block reaches).
+
+// K_ab from the pattern CSR (binary search of b in row a), 0 outside the pattern.
+__device__ __forceinline__ double dens_k(const DensLaunch& a, int fa, int fb) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 13;
+    int64_t lo = LD(a.row_ptr, fa, a.rowp_n), hi = LD(a.row_ptr, fa + 1, a.rowp_n);
+    const int64_t end = hi;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (LD(a.col, mid, a.nnz) < fb)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < end && LD(a.col, lo, a.nnz) == fb) ? LD(a.K, lo, a.nnz) : 0.0;
+}
+
+// u_f at grid point (x, y, z); 0 outside f's block.
+template <class T>
+__device__ __forceinline__ T dens_u(const DensLaunch& a, const DensFn& df, int x, int y, int z) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 13;
+    const int lx = x - df.o[0], ly = y - df.o[1], lz = z - df.o[2];
+    if (static_cast<unsigned>(lx) >= static_cast<unsigned>(df.d[0]) ||
+        static_cast<unsigned>(ly) >= static_cast<unsigned>(df.d[1]) ||
+        static_cast<unsigned>(lz) >= static_cast<unsigned>(df.d[2]))
+        return T(0);
+    const T* U = static_cast<const T*>(a.U);
+    return LD(U, df.off + (static_cast<int64_t>(lz) * df.d[1] + ly) * df.d[0] + lx, a.U_n);
+}
+
+__device__ __forceinline__ void lds16(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void lds16(const double* p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x, v[1] = t.y;
+}
+
+template <class T>
+__global__ void __launch_bounds__(DT_THREADS) k_density(DensLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 13;
+    constexpr int VW = 16 / sizeof(T);
+    __shared__ __align__(16) T kb[DT_MC * DT_MC];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.ntile[0];
+    const int ty = (tile / a.ntile[0]) % a.ntile[1];
+    const int tz = tile / (a.ntile[0] * a.ntile[1]);
+    const int64_t t0 = LD(a.tptr, tile, a.tptr_n);
+    const int m = static_cast<int>(LD(a.tptr, tile + 1, a.tptr_n) - t0);
+    int px[DT_PP], py[DT_PP], pz[DT_PP];
+    double acc[DT_PP];
+#pragma unroll
+    for (int i = 0; i < DT_PP; ++i) {
+        const int p = threadIdx.x + i * DT_THREADS;
+        px[i] = tx * DT_X + p % DT_X;
+        py[i] = ty * DT_Y + (p / DT_X) % DT_Y;
+        pz[i] = tz * DT_Z + p / (DT_X * DT_Y);
+        acc[i] = 0.0;
+    }
+    for (int cb = 0; cb < m; cb += DT_MC) {
+        const int nb = min(DT_MC, m - cb);
+        T ub[DT_MC][DT_PP];
+#pragma unroll
+        for (int j = 0; j < DT_MC; ++j) {
+            if (j < nb) {
+                const DensFn df = LD(a.fn, LD(a.tfn, t0 + cb + j, a.tfn_n), a.fn_n);
+#pragma unroll
+                for (int i = 0; i < DT_PP; ++i) ub[j][i] = dens_u<T>(a, df, px[i], py[i], pz[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < DT_PP; ++i) ub[j][i] = T(0);
+            }
+        }
+        for (int ca = 0; ca <= cb; ca += DT_MC) {
+            const int na = min(DT_MC, m - ca);
+            __syncthreads();   // the previous block's readers are done
+            for (int e = threadIdx.x; e < DT_MC * DT_MC; e += DT_THREADS) {
+                const int ia = e / DT_MC, ib = e % DT_MC;
+                double v = 0.0;
+                if (ia < na && ib < nb) {
+                    const int fa = LD(a.tfn, t0 + ca + ia, a.tfn_n);
+                    const int fb = LD(a.tfn, t0 + cb + ib, a.tfn_n);
+                    v = dens_k(a, fa, fb);
+                    if (ca != cb) v += dens_k(a, fb, fa);
+                }
+                kb[e] = static_cast<T>(v);
+            }
+            __syncthreads();
+            T part[DT_PP];
+#pragma unroll
+            for (int i = 0; i < DT_PP; ++i) part[i] = T(0);
+            for (int ia = 0; ia < na; ++ia) {
+                const DensFn df = LD(a.fn, LD(a.tfn, t0 + ca + ia, a.tfn_n), a.fn_n);
+                T ua[DT_PP], z[DT_PP];
+#pragma unroll
+                for (int i = 0; i < DT_PP; ++i) {
+                    ua[i] = dens_u<T>(a, df, px[i], py[i], pz[i]);
+                    z[i] = T(0);
+                }
+                const T* row = kb + ia * DT_MC;
+#pragma unroll
+                for (int q = 0; q < DT_MC; q += VW) {
+                    T k[VW];
+                    lds16(row + q, k);
+#pragma unroll
+                    for (int w = 0; w < VW; ++w)
+#pragma unroll
+                        for (int i = 0; i < DT_PP; ++i) z[i] += k[w] * ub[q + w][i];
+                }
+#pragma unroll
+                for (int i = 0; i < DT_PP; ++i) part[i] += ua[i] * z[i];
+            }
+#pragma unroll
+            for (int i = 0; i < DT_PP; ++i) acc[i] += static_cast<double>(part[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < DT_PP; ++i)
+        if (px[i] < a.gn[0] && py[i] < a.gn[1] && pz[i] < a.gn[2])
+            ST(a.rho, (pz[i] * a.gn[1] + py[i]) * a.gn[0] + px[i], a.rho_n, acc[i]);
+}
+
 // ---------------------------------------------------------------- peak probes
 //
 // Denominators of the rooflines, measured on the running GPU: a dependent-chain FMA
@@ -2076,6 +2258,7 @@ cudaError_t configure_kernels(size_t max_smem) {
     SETMAX((k_bwd_xy<double, 0>)) SETMAX((k_bwd_xy<float, 0>))
     SETMAX((k_bwd_xy<float, 2>)) SETMAX((k_bwd_xy<float, 3>))
     SETMAX(k_hs<double>) SETMAX(k_hs<float>)
+    SETMAX(k_z_dens<double>) SETMAX(k_z_dens<float>)
 #undef SETMAX
     return cudaSuccess;
 }
@@ -2132,6 +2315,33 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
 
 cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     return a.prec == 0 ? hphi_batch<double>(a, s) : hphi_batch<float>(a, s);
+}
+
+// Density, per batch: uncompress, forward x, y (FMA plane kernel in every precision) and
+// the density z stage writing u into the store.
+template <class T>
+static cudaError_t dens_batch(HphiLaunch a, cudaStream_t s) {
+    const int nf = a.nfn;
+    constexpr int C = ZCols<T>::C;
+    a.smem_z = sizeof(T) * 2 * static_cast<size_t>(a.max_nz) * C;
+    TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_rowsL + 7) / 8, nf), 256, 0, s>>>(a)));
+    TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
+    TRACED(a.tr, TK_DENS_U, s, (k_z_dens<T><<<dim3((a.max_cols + C - 1) / C, nf), C, a.smem_z, s>>>(a)));
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_dens_batch(const HphiLaunch& a, cudaStream_t s) {
+    return a.prec == 0 ? dens_batch<double>(a, s) : dens_batch<float>(a, s);
+}
+
+cudaError_t enqueue_density(const DensLaunch& a, cudaStream_t s) {
+    const int64_t nt = static_cast<int64_t>(a.ntile[0]) * a.ntile[1] * a.ntile[2];
+    if (nt == 0) return cudaSuccess;
+    if (a.prec == 0)
+        TRACED(a.tr, TK_DENSITY, s, (k_density<double><<<static_cast<unsigned>(nt), DT_THREADS, 0, s>>>(a)));
+    else
+        TRACED(a.tr, TK_DENSITY, s, (k_density<float><<<static_cast<unsigned>(nt), DT_THREADS, 0, s>>>(a)));
+    return cudaGetLastError();
 }
 
 cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s) {

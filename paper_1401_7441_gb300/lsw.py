@@ -65,6 +65,7 @@ _SIGS = {
     "lsw_set_potential": (C.c_int, [_P, _P, _I64P, _I64P]),
     "lsw_apply_hamiltonian": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_build_matrices": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lsw_build_density": (C.c_int, [_P, _P, _P, _P, _I64P, _I64P]),
     "lsw_apply_hamiltonian_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_reformat": (C.c_int, [_P, _P, _I32P, _P, _P]),
     "lsw_workspace_bytes": (C.c_int, [_P, _I64P]),
@@ -80,7 +81,8 @@ _SIGS = {
     "lsw_load_phi": (C.c_int, [_P, C.c_char_p, _P]),
 }
 
-TRACE_KINDS = ["memset", "uncompress", "fwd_xy", "z_stage", "bwd_xy", "kinetic", "unused", "hs_tiles"]
+TRACE_KINDS = ["memset", "uncompress", "fwd_xy", "z_stage", "bwd_xy", "kinetic", "unused", "hs_tiles",
+               "dens_realspace", "dens_products"]
 
 
 def lib():
@@ -195,6 +197,13 @@ def lsw_apply_hamiltonian_noalloc(sys, phi, hphi, e_kin=None, e_pot=None):
 
 def lsw_build_matrices(sys, phi, hphi, H, S):
     check(lib().lsw_build_matrices(sys, _ptr(phi), _ptr(hphi), _ptr(H), _ptr(S)))
+
+
+def lsw_build_density(sys, phi, K, rho, fine_lo, fine_dims):
+    """rho_j = sum_ab K_ab u_a(j) u_b(j) on the fine grid block (FP64, [z][y][x])."""
+    lo = (C.c_int64 * 3)(*fine_lo)
+    dims = (C.c_int64 * 3)(*fine_dims)
+    check(lib().lsw_build_density(sys, _ptr(phi), _ptr(K), _ptr(rho), lo, dims))
 
 
 def lsw_reformat(dst, src, shift, phi_src, phi_dst):

@@ -98,6 +98,9 @@ def test_argument_errors(ctx):
         with pytest.raises(lsw.LswError) as e:
             lsw.lsw_apply_hamiltonian(S.sys, 16, 32)
         assert e.value.status == lsw.LSW_ERR_STATE   # host-only context: no device work
+        with pytest.raises(lsw.LswError) as e:
+            lsw.lsw_build_density(S.sys, 16, 32, 48, wl.V_lo, wl.V_shape)
+        assert e.value.status == lsw.LSW_ERR_STATE
         with pytest.raises(lsw.LswError):
             lsw.lsw_set_option(S.sys, "nonsense", 1)
     finally:
