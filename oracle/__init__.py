@@ -24,4 +24,8 @@ geometry     grid, fine region, locregs L and L' and their segment keys, compres
 hamiltonian  H phi = L' (T + W^T M^T V M W) L phi per support function (Sec. III.B).
 matrices     S_ab = <phi_a|phi_b>, H_ab = <phi_a|H phi_b> on the CSR pattern (Sec. II.A).
 brute        explicit dense matrices on tiny boxes (pin for the separable oracle).
+density      rho_j = sum_ab K_ab u_a(j) u_b(j) on the fine grid (Sec. II.A, Eq. density).
+confinement  quartic confining potential a (r - R)^4 in the two-level basis and the
+             preconditioning equation solved by conjugate gradients (Sec. "Support
+             function optimization", Eq. precond).
 """

@@ -25,6 +25,10 @@ Readings taken where the paper is silent:
 * magic filter w_l, l = -7..8: the 16-tap filter with the moments of phi,
   sum_l w_l l^p = M_p for p = 0..15; u_j = sum_k w_{j-k} c_k maps scaling
   coefficients to point values (window centred on supp phi since M_1 ~ 0.16).
+* moment overlaps F^p(l) = int x^p phi(x) phi(x - l) dx, p <= 4, |l| <= 14, from the
+  refinement equation (the multiplication operators x^p of the quartic confining
+  potential, Sec. "Support function optimization": evaluated by convolutions like the
+  kinetic energy).
 * kinetic filters: Galerkin connection coefficients r_l = int phi(x) phi''(x-l) dx,
   |l| <= 14, from r_l = 4 sum_{i,j} h_i h_j r_{2l+j-i} with sum_l l^2 r_l = 2
   (Beylkin 1992); the scale-h blocks T_XY(l) = 4 sum_{k,k'} X_k Y_k' r_{2l+k'-k},
@@ -218,6 +222,45 @@ def kinetic_blocks(h, g, r):
     return out
 
 
+def moment_overlaps(h, pmax: int = 4):
+    """F^p(l) = int x^p phi(x) phi(x - l) dx, p = 0..pmax, l = -14..14: the Galerkin
+    entries of the multiplication operators x^p between scaling functions, which the
+    quartic confining potential a (r - R)^4 of the support-function optimization needs
+    ("evaluated via convolutions in the same manner as the kinetic energy").
+
+    Refinement equation in both factors, then x = (s + a)/2:
+      F^p(l) = 2^-p sum_{a,b} h_a h_b sum_{q<=p} C(p,q) a^(p-q) F^q(2l + b - a),
+    i.e. (I - 2^-p T) F^p = 2^-p sum_{q<p} ..., with (T F)(l) = sum_n A_n F(2l + n) and
+    A_n = sum_a h_a h_{a+n}.  F^0(l) = delta_l0 (orthonormal translates); for p >= 1 the
+    matrix I - 2^-p T is regular (T has spectral radius 1)."""
+    mp = _mp()
+    L = KIN_HALF
+    n = len(h)
+    js = list(range(H_LO, H_LO + n))
+    A = {}
+    for d in range(-(n - 1), n):
+        A[d] = sum(h[i] * h[i + d] for i in range(n) if 0 <= i + d < n)
+    size = 2 * L + 1
+    F = [[mp.mpf(1) if l == 0 else mp.mpf(0) for l in range(-L, L + 1)]]
+    for p in range(1, pmax + 1):
+        M = mp.matrix(size, size)
+        b = mp.matrix([0] * size)
+        for li, l in enumerate(range(-L, L + 1)):
+            for mi, m in enumerate(range(-L, L + 1)):
+                M[li, mi] = (1 if li == mi else 0) - mp.mpf(2) ** (-p) * A.get(m - 2 * l, 0)
+            acc = mp.mpf(0)
+            for q in range(p):
+                for ja, ha in zip(js, h):
+                    for jb, hb in zip(js, h):
+                        idx = 2 * l + jb - ja
+                        if -L <= idx <= L:
+                            acc += mp.binomial(p, q) * mp.mpf(ja) ** (p - q) * ha * hb * F[q][idx + L]
+            b[li] = mp.mpf(2) ** (-p) * acc
+        x = mp.lu_solve(M, b)
+        F.append([x[k] for k in range(size)])
+    return F
+
+
 def derive(dps: int = 60):
     """Every table entry in mpmath precision: dict name -> (lo, [values])."""
     h = least_asymmetric_h(dps)
@@ -235,6 +278,8 @@ def derive(dps: int = 60):
     }
     for k, v in T.items():
         tab["kin_" + k] = (-KIN_HALF, v)
+    for p, v in enumerate(moment_overlaps(h)):
+        tab["movl_%d" % p] = (-KIN_HALF, v)
     return tab
 
 
@@ -270,6 +315,7 @@ class Filters:
     h_lo: int = H_LO
     magic_lo: int = MAGIC_LO
     kin_lo: int = -KIN_HALF
+    movl: np.ndarray = None   # [p][l + 14]: int x^p phi(x) phi(x - l) dx, p = 0..4
 
 
 def read_table(path: str = TABLE_PATH) -> dict:
@@ -295,6 +341,7 @@ def load(path: str = TABLE_PATH) -> Filters:
             h=t["h"][1], g=t["g"][1], moments=t["moments"][1], magic=t["magic"][1],
             kin_r=t["kin_r"][1],
             kin={k: t["kin_" + k][1] for k in ("hh", "hg", "gh", "gg")},
+            movl=np.array([t["movl_%d" % p][1] for p in range(5)]),
         )
     return _CACHE[path]
 

@@ -120,3 +120,62 @@ def test_density_magic_filter_reversed(monkeypatch):
 
     monkeypatch.setattr(Dn, "realspace_block", reversed_w)
     _fails(TD.test_density_of_two_gaussians_closed_form)
+
+
+# ------------------------------------------------------------------ confinement (Eq. precond)
+
+from oracle import confinement as Cf
+from tests import test_oracle_confinement as TC
+
+
+def test_confinement_moment_overlaps_index_shifted(monkeypatch):
+    # F^p(l) read one index off
+    bad = dataclasses.replace(TC.FT, movl=np.roll(TC.FT.movl, 1, axis=1))
+    monkeypatch.setattr(TC, "FT", bad)
+    Cf._BLOCKS.clear()
+    try:
+        _fails(TC.test_quartic_block_gaussian_moments_1d, 2)
+    finally:
+        Cf._BLOCKS.clear()
+
+
+def test_confinement_scaling_wavelet_coupling_dropped(monkeypatch):
+    # the 1D operator applied type by type, without the scaling <-> wavelet blocks
+    real = Cf._apply_1d
+
+    def diagonal_only(arr, axis, blocks):
+        z = {k: (v if k[0] == k[1] else np.zeros_like(v)) for k, v in blocks.items()}
+        return real(arr, axis, z)
+
+    monkeypatch.setattr(Cf, "_apply_1d", diagonal_only)
+    _fails(TC.test_confinement_assembly_against_kronecker_products)
+
+
+def test_confinement_wavelet_filter_in_place_of_scaling(monkeypatch):
+    # the wavelet-wavelet block built with h in place of g (an operand swapped in the 1D blocks)
+    real = Cf.quartic_block_1d
+
+    def swapped(m, b, bp, i_idx, j_idx, c, h, F):
+        return real(m, 0 if (b, bp) == (1, 1) else b, 0 if (b, bp) == (1, 1) else bp, i_idx, j_idx, c, h, F)
+
+    monkeypatch.setattr(Cf, "quartic_block_1d", swapped)
+    _fails(TC.test_quartic_blocks_by_cascade_quadrature)
+
+
+def test_confinement_cross_terms_dropped(monkeypatch):
+    # (r - R)^4 taken as sum_d X_d^4 only (the 2 X_d^2 X_e^2 terms lost)
+    real = Cf._blocks
+
+    def no_square(d_lo, n, c, h, F):
+        b = real(d_lo, n, c, h, F)
+        return {2: {k: np.zeros_like(v) for k, v in b[2].items()}, 4: b[4]}
+
+    monkeypatch.setattr(Cf, "_blocks", no_square)
+    _fails(TC.test_confinement_gaussian_closed_form_3d)
+
+
+def test_precond_kinetic_sign_flipped(monkeypatch):
+    # +1/2 nabla^2 in place of -1/2 nabla^2 in the preconditioning operator
+    real = Hm.kinetic3d
+    monkeypatch.setattr(Hm, "kinetic3d", lambda c, h, F: -real(c, h, F))
+    _fails(TC.test_precond_operator_against_explicit_matrices)
