@@ -28,4 +28,6 @@ density      rho_j = sum_ab K_ab u_a(j) u_b(j) on the fine grid (Sec. II.A, Eq. 
 confinement  quartic confining potential a (r - R)^4 in the two-level basis and the
              preconditioning equation solved by conjugate gradients (Sec. "Support
              function optimization", Eq. precond).
+combine      sparse combinations P_L sum_beta M_ab phi_beta and the first-order Taylor
+             Loewdin step (Sec. "Orthogonalization", Eq. gradient).
 """

@@ -179,3 +179,47 @@ def test_precond_kinetic_sign_flipped(monkeypatch):
     real = Hm.kinetic3d
     monkeypatch.setattr(Hm, "kinetic3d", lambda c, h, F: -real(c, h, F))
     _fails(TC.test_precond_operator_against_explicit_matrices)
+
+
+# ------------------------------------------------------------------ sparse combinations (Loewdin)
+
+from oracle import combine as Cb
+from tests import test_oracle_combine as TB
+
+
+def test_combine_matrix_transposed(monkeypatch):
+    # M_beta,alpha used in row alpha (the transposed operand)
+    real = Cb.combine
+
+    def transposed(geo, M, phi, rows=None):
+        rp, col = geo.row_ptr, geo.col
+        pos = {(a, int(col[k])): k for a in range(len(rp) - 1) for k in range(rp[a], rp[a + 1])}
+        Mt = np.array([M[pos[(int(col[k]), a)]] for a in range(len(rp) - 1) for k in range(rp[a], rp[a + 1])])
+        return real(geo, Mt, phi, rows)
+
+    monkeypatch.setattr(Cb, "combine", transposed)
+    _fails(TB.test_combination_is_the_adjoint_of_the_scalar_products, 5, 3, 1.3)
+
+
+def test_combine_placed_at_the_wrong_origin(monkeypatch):
+    # phi_beta placed at L(alpha)'s origin instead of its own
+    real_place = Cb._H._place
+
+    def misplaced(dst, dst_lo, src, src_lo):
+        return real_place(dst, dst_lo, src, dst_lo)
+
+    monkeypatch.setattr(Cb._H, "_place", misplaced)
+    _fails(TB.test_combination_is_the_adjoint_of_the_scalar_products, 5, 3, 1.3)
+
+
+def test_taylor_step_with_the_wrong_sign(monkeypatch):
+    # (3I + S)/2 in place of (3I - S)/2
+    real = Cb.combine
+
+    def plus(geo, M, phi, rows=None):
+        rp, col = geo.row_ptr, geo.col
+        diag = np.array([float(int(col[k]) == a) for a in range(len(rp) - 1) for k in range(rp[a], rp[a + 1])])
+        return real(geo, 3.0 * diag - M, phi, rows)       # (3I - S)/2 -> (3I + S)/2 when M = (3I - S)/2
+
+    monkeypatch.setattr(Cb, "combine", plus)
+    _fails(TB.test_taylor_loewdin_error_is_second_order)
