@@ -223,3 +223,50 @@ def test_taylor_step_with_the_wrong_sign(monkeypatch):
 
     monkeypatch.setattr(Cb, "combine", plus)
     _fails(TB.test_taylor_loewdin_error_is_second_order)
+
+
+# ------------------------------------------------------------------ Fermi operator expansion
+
+from oracle import foe as Fo
+from tests import test_oracle_foe as TF2
+
+
+def test_foe_recursion_without_the_factor_two(monkeypatch):
+    # t^{j+1} = H t^j - t^{j-1} (the Chebyshev recursion's factor 2 dropped)
+    def bad(Ht, c):
+        n = len(Ht)
+        K = np.zeros((n, n))
+        for l in range(n):
+            t_prev = np.zeros(n)
+            t_prev[l] = 1.0
+            k = 0.5 * c[0] * t_prev
+            t = Ht @ t_prev
+            k = k + c[1] * t
+            for j in range(2, len(c)):
+                t_prev, t = t, Ht @ t - t_prev
+                k = k + c[j] * t
+            K[:, l] = k
+        return K
+
+    monkeypatch.setattr(Fo, "kernel_prime", bad)
+    _fails(TF2.test_kernel_equals_exact_diagonalization)
+
+
+def test_foe_zeroth_coefficient_not_halved(monkeypatch):
+    real = Fo.chebyshev_value
+
+    monkeypatch.setattr(Fo, "chebyshev_value", lambda c, x: real(c, x) + 0.5 * c[0])
+    _fails(TF2.test_chebyshev_interpolation_and_evaluation)
+
+
+def test_foe_kernel_not_transformed_back(monkeypatch):
+    # K = K' (the S^-1/2 ... S^-1/2 back-transform forgotten)
+    real_foe = Fo.foe
+
+    def no_back(H, S, n_el, n_pl, de, **kw):
+        r = real_foe(H, S, n_el, n_pl, de, **kw)
+        r["K"] = r["Kp"]
+        return r
+
+    monkeypatch.setattr(Fo, "foe", no_back)
+    _fails(TF2.test_kernel_equals_exact_diagonalization)
