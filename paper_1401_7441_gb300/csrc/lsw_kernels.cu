@@ -17,6 +17,12 @@
 //                 H phi of the functions touching the tile; S_ab += <phi_a|phi_b>,
 //                 H_ab += <phi_a|H phi_b> over the tile; FP64 accumulation
 //
+// Density rho = sum_ab K_ab phi_a phi_b on the fine grid (Sec. II.A Eq. density):
+//   k_z_dens      the forward half of k_z: real-space values u of every function into
+//                 a store (after k_uncompress and k_fwd_xy)
+//   k_density     per tile of grid points: sum over chunk pairs of the functions whose
+//                 blocks meet the tile of K_ab u_a u_b, FP64 total per point
+//
 // All kernels are templated on the storage/compute type T (double or float); energy
 // and matrix accumulations are FP64.  Device-side checks set bits of a status word
 // (never trap).
