@@ -1,0 +1,158 @@
+"""Sharding over ranks with one halo exchange (host logic, CPU): partition balance, the
+symmetry of the halo plan, and world_size-2 gloo ranks that each apply H to their own
+functions, exchange phi and H phi of the halo, and form their own rows of H and S,
+identical to the single-process result."""
+import datetime
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1401_7441_gb300 import inputs as I
+from paper_1401_7441_gb300 import lsw
+from paper_1401_7441_gb300 import shard
+from tests.lib_support import ensure_built, host_system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_partition_balances_support_functions():
+    wl = I.atoms64()
+    for world in (2, 3, 4, 8):
+        owner = shard.partition_atoms(wl.pos, wl.nsf, world)
+        assert owner.min() >= 0 and owner.max() == world - 1
+        counts = np.bincount(owner, weights=wl.nsf, minlength=world)
+        assert counts.max() - counts.min() <= 2 * wl.nsf.max(), counts
+        # slabs: x order is rank order
+        order = np.argsort(wl.pos[:, 0], kind="stable")
+        assert np.all(np.diff(owner[order]) >= 0)
+
+
+def test_halo_plan_is_symmetric_and_complete():
+    ensure_built()
+    wl = I.atoms64()
+    ctx = lsw.lsw_ctx_create(lsw.LSW_HOST_ONLY)
+    S = host_system(wl, ctx)
+    try:
+        world = 3
+        owner = shard.partition_atoms(wl.pos, wl.nsf, world)
+        plans = [shard.halo_plan(S.row_ptr, S.col, S.sf_atom, owner, r) for r in range(world)]
+        fown = owner[S.sf_atom]
+        for q in range(world):
+            send, recv = plans[q]
+            for r in range(world):
+                assert send.get(r, []) == plans[r][1].get(q, [])     # q -> r equals r <- q
+            # every column of an owned row is owned here or received
+            have = set(np.nonzero(fown == q)[0].tolist()) | set(f for v in recv.values() for f in v)
+            for a in np.nonzero(fown == q)[0]:
+                assert set(S.col[S.row_ptr[a]:S.row_ptr[a + 1]].tolist()) <= have
+            assert all(int(fown[f]) == r for r, v in recv.items() for f in v)
+        assert any(plans[0][1])                                  # a real halo
+    finally:
+        S.close()
+        lsw.lsw_ctx_destroy(ctx)
+
+
+def _worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from oracle import geometry as G
+    from oracle import hamiltonian as Hm
+    from oracle import matrices as Mx
+    from paper_1401_7441_gb300 import inputs as I_
+    from paper_1401_7441_gb300 import lsw as L_
+    from paper_1401_7441_gb300 import shard as SH
+    from tests.lib_support import host_system as hs
+    from tests.oracle_support import desc_of
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
+    try:
+        wl = I_.scaled("atoms64", 8, seed=5)
+        ctx = L_.lsw_ctx_create(L_.LSW_HOST_ONLY)
+        S = hs(wl, ctx)
+        owner = SH.partition_atoms(wl.pos, wl.nsf, world)
+        plan = SH.halo_plan(S.row_ptr, S.col, S.sf_atom, owner, rank)
+        geo = G.build(desc_of(wl))
+        V = I_.potential(wl)
+        fown = owner[S.sf_atom]
+        phi = torch.full((S.total_L,), float("nan"), dtype=torch.float64)
+        hphi = torch.full((S.total_Lp,), float("nan"), dtype=torch.float64)
+        ref = {}
+        for f in range(S.n_sf):
+            a = geo.sf_atom[f]
+            p = I_.phi_values(wl, f, a, geo.L[a].coarse.g, geo.L[a].fine.g)
+            ref[f] = p
+            if fown[f] == rank:                                   # own functions only
+                phi[S.off_L[f]:S.off_L[f] + len(p)] = torch.from_numpy(p)
+                h = Hm.apply_hamiltonian(geo, f, p, V, wl.V_lo)[0]
+                hphi[S.off_Lp[f]:S.off_Lp[f] + len(h)] = torch.from_numpy(h)
+        SH.exchange([phi, hphi], [S.off_L, S.off_Lp], plan)
+        rows = {}
+        for a in np.nonzero(fown == rank)[0]:
+            na = len(ref[a])
+            pa = phi[S.off_L[a]:S.off_L[a] + na].numpy()
+            vals = []
+            for k in range(S.row_ptr[a], S.row_ptr[a + 1]):
+                b = int(S.col[k])
+                pb = phi[S.off_L[b]:S.off_L[b] + len(ref[b])].numpy()
+                hlen = geo.Lp[geo.sf_atom[b]].n_coef
+                hb = hphi[S.off_Lp[b]:S.off_Lp[b] + hlen].numpy()
+                assert np.all(np.isfinite(pb)) and np.all(np.isfinite(hb)), (rank, a, b)
+                vals.append((Mx.overlap_entry(geo, a, b, pa, pb), Mx.hamiltonian_entry(geo, a, b, pa, hb)))
+            rows[int(a)] = vals
+        n_halo = sum(len(v) for v in plan[1].values())
+        q.put(("ok", rank, rows, n_halo))
+        S.close()
+        L_.lsw_ctx_destroy(ctx)
+    except Exception as e:                     # report instead of leaving the parent waiting
+        q.put(("error", rank, repr(e), 0))
+        raise
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_rows_equal_single_process_gloo():
+    import torch.multiprocessing as mp
+    from oracle import geometry as G
+    from oracle import hamiltonian as Hm
+    from oracle import matrices as Mx
+    from tests.oracle_support import desc_of, phi_all
+    ensure_built()
+    ctx = mp.get_context("spawn")
+    qu = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, qu)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [qu.get(timeout=600) for _ in range(2)]
+    for p in procs:
+        p.join(120)
+    assert all(r[0] == "ok" for r in res), res
+    assert all(p.exitcode == 0 for p in procs)
+    res = [r[1:] for r in res]
+    wl = I.scaled("atoms64", 8, seed=5)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    phi = phi_all(wl, geo)
+    hphi = {f: Hm.apply_hamiltonian(geo, f, phi[f], V, wl.V_lo)[0] for f in phi}
+    H, Sm = Mx.build_matrices(geo, phi, hphi)
+    seen = set()
+    for rank, rows, n_halo in res:
+        assert n_halo > 0
+        for a, vals in rows.items():
+            assert a not in seen
+            seen.add(a)
+            for j, k in enumerate(range(geo.row_ptr[a], geo.row_ptr[a + 1])):
+                assert vals[j][0] == Sm[k] and vals[j][1] == H[k], (a, k)
+    assert seen == set(range(len(geo.sf_atom)))                   # every row owned once
