@@ -30,6 +30,7 @@ confinement  quartic confining potential a (r - R)^4 in the two-level basis and 
              function optimization", Eq. precond).
 combine      sparse combinations P_L sum_beta M_ab phi_beta and the first-order Taylor
              Loewdin step (Sec. "Orthogonalization", Eq. gradient).
+gradient     support-function gradient of the band-structure energy (Eq. gradient).
 foe          density kernel by the Fermi operator expansion (App. "Fermi operator
              expansion"): Chebyshev recursion, erf smearing, bisection on mu.
 """

@@ -270,3 +270,34 @@ def test_foe_kernel_not_transformed_back(monkeypatch):
 
     monkeypatch.setattr(Fo, "foe", no_back)
     _fails(TF2.test_kernel_equals_exact_diagonalization)
+
+
+# ------------------------------------------------------------------ gradient (Eq. gradient)
+
+from oracle import gradient as Gr
+from tests import test_oracle_gradient as TG
+
+
+def _patched_gradient(half=0.5, sym=True):
+    def energy_gradient(geo, phi, hphi, K, S, sinv="exact"):
+        n = len(geo.sf_atom)
+        Phi = np.stack([Gr.to_box(geo, geo.L[geo.sf_atom[f]], phi[f]) for f in range(n)])
+        HPhi = np.stack([Gr.to_box(geo, geo.Lp[geo.sf_atom[f]], hphi[f]) for f in range(n)])
+        D = np.tensordot(np.asarray(K), HPhi, axes=([1], [0]))
+        Chi = np.tensordot(np.asarray(S), D, axes=([1], [0]))
+        Lam = np.array([[float(np.sum(Phi[a] * Chi[b])) for b in range(n)] for a in range(n)])
+        M = half * np.linalg.inv(S) @ ((Lam + Lam.T) if sym else 2.0 * Lam)
+        G = Chi - np.tensordot(M, Phi, axes=([1], [0]))
+        return {f: Gr.from_box(geo, geo.L[geo.sf_atom[f]], G[f]) for f in range(n)}
+    return energy_gradient
+
+
+def test_gradient_without_the_half(monkeypatch):
+    monkeypatch.setattr(Gr, "energy_gradient", _patched_gradient(half=1.0))
+    _fails(TG.test_gradient_is_tangent_to_the_orthonormality_constraint)
+
+
+def test_gradient_with_unsymmetrized_multipliers(monkeypatch):
+    # 2 Lambda in place of Lambda + Lambda^T
+    monkeypatch.setattr(Gr, "energy_gradient", _patched_gradient(sym=False))
+    _fails(TG.test_gradient_is_the_derivative_along_tangent_directions, 3)
