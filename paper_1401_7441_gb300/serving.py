@@ -261,6 +261,35 @@ class Server:
             ent.phi = None
         return self.used + need <= self.budget
 
+    def _admit(self, cand, inflight, max_inflight):
+        """Admit prepared jobs (in arrival order) while a stream is free and their memory
+        fits the budget after evicting idle resident systems; returns the admitted jobs.
+
+        A job larger than the whole budget can never run: that is an error.  While work
+        is in flight a job that does not fit waits for it (first come, first served);
+        when nothing is in flight nothing would release memory for it, so later jobs
+        that fit go first."""
+        admitted = []
+        for job in cand:
+            if len(inflight) + len(admitted) >= max_inflight:
+                break
+            if job.est_bytes > self.budget:
+                raise RuntimeError("request %d needs %.3f GB, more than the whole %.3f GB budget"
+                                   % (job.req.rid, job.est_bytes / 1e9, self.budget / 1e9))
+            if not self._evict(job.est_bytes):
+                if inflight or admitted:
+                    break
+                continue
+            busy = {id(j.stream) for j in list(inflight) + admitted}
+            free = [st for st in self.streams if id(st) not in busy]
+            if not free:
+                break
+            job.stream = free[0]
+            job.t_admit = time.perf_counter()
+            self.used += job.est_bytes
+            admitted.append(job)
+        return admitted
+
     # ---------------------------------------------------------------- the loop
     def run(self, requests, realtime=True, max_inflight=None):
         """Serve ``requests`` (sorted by arrival); returns results in completion order.
@@ -338,20 +367,9 @@ class Server:
                 # admission: prepared requests whose memory fits, on a free stream
                 with lock:
                     cand = list(ready)
-                for job in cand:
-                    if len(inflight) >= max_inflight:
-                        break
-                    if not self._evict(job.est_bytes):
-                        break
-                    busy = {id(j.stream) for j in inflight}
-                    free = [st for st in self.streams if id(st) not in busy]
-                    if not free:
-                        break
+                for job in self._admit(cand, inflight, max_inflight):
                     with lock:
                         ready.remove(job)
-                    job.stream = free[0]
-                    job.t_admit = time.perf_counter()
-                    self.used += job.est_bytes
                     inflight.append(job)
                     tasks.put(("launch", job))
                 done = [j for j in inflight if j.bufs.get("launched") and j.event.query()]
