@@ -12,7 +12,6 @@ from oracle import confinement as Cf
 from oracle import filters as F
 from oracle import geometry as G
 from oracle import matrices as Mx
-from paper_1401_7441_gb300 import inputs as I
 from tests.oracle_support import desc_of, phi_all, tiny_workload
 from tests.test_oracle_filters import _cascade
 from tests.test_oracle_operator import _gauss_1d_coeffs, _gauss_3d

@@ -5,7 +5,6 @@ energy, the second-order error of the Taylor S^-1/2 and idempotency at low smear
 import math
 
 import numpy as np
-import pytest
 from scipy.linalg import eigh
 from scipy.optimize import brentq
 

@@ -8,7 +8,6 @@ import socket
 import sys
 
 import numpy as np
-import pytest
 
 from paper_1401_7441_gb300 import inputs as I
 from paper_1401_7441_gb300 import lsw
