@@ -21,8 +21,12 @@ Readings taken where the paper is silent:
 * mu and de are given in the units of the Hamiltonian; the target of Tr(K') is the
   number of occupied orbitals (occupations in [0, 1]);
 * mu is found by bisection on [e_min, e_max] until |Tr(K') - n_el| <= tol;
-* the matrices are dense here (the oracle applies no sparsity truncation); "taylor"
-  (the paper's choice) or "exact" S^-1/2 selects the transform.
+* the matrices are dense by default; "taylor" (the paper's choice) or "exact" S^-1/2
+  selects the transform;
+* sparse form (``pattern``, a boolean n x n mask of the kernel's pattern, symmetric,
+  diagonal included): H~' is kept on the mask and every Chebyshev column t_l^j is cut
+  to the mask's column l after each product, as a linear-scaling evaluation must; with
+  a complete mask the result equals the dense one.
 """
 from __future__ import annotations
 
@@ -71,25 +75,27 @@ def spectrum_bounds(H, S):
     return float(e[0]), float(e[-1])
 
 
-def kernel_prime(Ht, c):
-    """K' = c_0/2 I + sum c_i T_i(Ht), column by column with the Chebyshev recursion."""
+def kernel_prime(Ht, c, pattern=None):
+    """K' = c_0/2 I + sum c_i T_i(Ht), column by column with the Chebyshev recursion;
+    with ``pattern`` every column is cut to the mask after each product."""
     n = len(Ht)
     K = np.zeros((n, n))
     for l in range(n):
+        keep = np.ones(n) if pattern is None else pattern[:, l].astype(np.float64)
         t_prev = np.zeros(n)
         t_prev[l] = 1.0
         k = 0.5 * c[0] * t_prev
         if len(c) > 1:
-            t = Ht @ t_prev
+            t = (Ht @ t_prev) * keep
             k = k + c[1] * t
             for j in range(2, len(c)):
-                t_prev, t = t, 2.0 * (Ht @ t) - t_prev
+                t_prev, t = t, (2.0 * (Ht @ t) - t_prev) * keep
                 k = k + c[j] * t
         K[:, l] = k
     return K
 
 
-def foe(H, S, n_el, n_pl, de, sinv="taylor", bounds=None, tol=1e-10, max_bisect=200):
+def foe(H, S, n_el, n_pl, de, sinv="taylor", bounds=None, tol=1e-10, max_bisect=200, pattern=None):
     """Density kernel by FOE.  Returns dict(K, Kp, mu, sigma, tau, c, E_BS, bounds)."""
     H = np.asarray(H, np.float64)
     S = np.asarray(S, np.float64)
@@ -99,11 +105,13 @@ def foe(H, S, n_el, n_pl, de, sinv="taylor", bounds=None, tol=1e-10, max_bisect=
     Ht = sigma * (H - tau * S)
     X = s_inv_half(S, sinv)
     Htp = X @ Ht @ X
+    if pattern is not None:
+        Htp = np.where(pattern, Htp, 0.0)
     lo, hi = e_min, e_max
     for _ in range(max_bisect):
         mu = 0.5 * (lo + hi)
         c = chebyshev_coefficients(lambda x: fermi_erf(x, sigma * (mu - tau), sigma * de), n_pl)
-        Kp = kernel_prime(Htp, c)
+        Kp = kernel_prime(Htp, c, pattern)
         tr = float(np.trace(Kp))
         if abs(tr - n_el) <= tol:
             break

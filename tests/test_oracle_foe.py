@@ -87,3 +87,32 @@ def test_low_smearing_kernel_is_a_projector():
     Kp = r["Kp"]
     assert np.max(np.abs(Kp @ Kp - Kp)) <= 1e-8
     assert abs(float(np.trace(Kp)) - 6.0) <= 1e-10
+
+
+def _chain(n, t=1.0, gap=3.0):
+    """Tight-binding chain with alternating on-site energies (+-gap/2): a gapped,
+    nearsighted Hamiltonian (density matrix decays exponentially with distance)."""
+    H = np.diag(np.where(np.arange(n) % 2 == 0, gap / 2, -gap / 2)) - t * (np.eye(n, k=1) + np.eye(n, k=-1))
+    return H, np.eye(n)
+
+
+def test_complete_pattern_equals_the_dense_expansion():
+    H, S = _system(10, 0.05, 2)
+    full = np.ones((10, 10), bool)
+    a = Fo.foe(H, S, 4.0, 120, 0.3, sinv="taylor", tol=1e-12)
+    b = Fo.foe(H, S, 4.0, 120, 0.3, sinv="taylor", tol=1e-12, pattern=full)
+    assert np.array_equal(a["K"], b["K"])
+
+
+def test_truncated_kernel_error_decays_with_the_pattern_radius():
+    # nearsightedness: cutting the Chebyshev columns to |i - j| <= r loses less as r grows
+    n = 40
+    H, S = _chain(n)
+    ref = Fo.foe(H, S, n / 2, 200, 0.2, sinv="exact", tol=1e-11)["K"]
+    errs = []
+    for r in (2, 4, 6, 8, 12):
+        mask = np.abs(np.subtract.outer(np.arange(n), np.arange(n))) <= r
+        K = Fo.foe(H, S, n / 2, 200, 0.2, sinv="exact", tol=1e-11, pattern=mask)["K"]
+        errs.append(float(np.max(np.abs(K - ref))))
+    assert all(errs[k + 1] < 0.5 * errs[k] for k in range(len(errs) - 1)), errs
+    assert errs[-1] < 1e-4 * np.max(np.abs(ref))

@@ -233,7 +233,7 @@ from tests import test_oracle_foe as TF2
 
 def test_foe_recursion_without_the_factor_two(monkeypatch):
     # t^{j+1} = H t^j - t^{j-1} (the Chebyshev recursion's factor 2 dropped)
-    def bad(Ht, c):
+    def bad(Ht, c, pattern=None):
         n = len(Ht)
         K = np.zeros((n, n))
         for l in range(n):
