@@ -76,6 +76,9 @@ def workload(name):
         return I.scaled("atoms10k", int(name.split("_n")[1]))
     if name.startswith("atoms64_n"):
         return I.scaled("atoms64", int(name.split("_n")[1]))
+    if name.endswith(".json"):                      # a JSON system spec (spec.py)
+        from paper_1401_7441_gb300 import spec
+        return spec.load(name)
     raise SystemExit("unknown workload " + name)
 
 
