@@ -86,3 +86,43 @@ def exchange(buffers, offsets, plan, group=None):
         for s, e in rg:
             buf[s:e] = t[p:p + (e - s)]
             p += e - s
+
+
+def subsystem(wl, owner, rank, sf_atom, row_ptr, col):
+    """The atoms a rank hands to the library for its share of a sharded run.
+
+    Its own atoms, the atoms of the functions its rows reach (the halo), and ghost atoms
+    (no support functions) whose fine spheres can reach the L' region of an own atom, so
+    that the fine region -- the union of every atom's fine sphere -- is the same as the
+    whole system's wherever an own function lives.  The grid, the potential's wells and
+    every radius are the whole system's.  Returns (workload, global atom of each
+    sub-system atom, global function of each sub-system function)."""
+    import copy
+    pos = np.asarray(wl.pos, np.float64)
+    owner = np.asarray(owner, np.int64)
+    sf_atom = np.asarray(sf_atom, np.int64)
+    row_ptr = np.asarray(row_ptr, np.int64)
+    col = np.asarray(col, np.int64)
+    own_atoms = np.nonzero(owner == rank)[0]
+    halo_atoms = set()
+    for a in np.nonzero(owner[sf_atom] == rank)[0]:
+        halo_atoms.update(int(sf_atom[b]) for b in col[row_ptr[a]:row_ptr[a + 1]])
+    # L' radius plus the largest fine radius, with a grid diagonal of slack: an extra ghost
+    # only repeats fine points the whole system has anyway
+    reach = np.asarray(wl.r_loc)[own_atoms] + wl.lprime_margin * wl.h + np.max(wl.r_fine) + 2.0 * wl.h
+    d2 = np.sum((pos[None, :, :] - pos[own_atoms][:, None, :]) ** 2, axis=2)
+    ghosts = set(np.nonzero(np.any(d2 <= (reach[:, None]) ** 2, axis=0))[0].tolist())
+    keep = sorted(set(own_atoms.tolist()) | halo_atoms | ghosts)
+    with_fns = set(own_atoms.tolist()) | halo_atoms
+    nsf = np.asarray(wl.nsf, np.int64)
+    sub_nsf = np.array([nsf[a] if a in with_fns else 0 for a in keep], np.int64)
+    first = np.concatenate([[0], np.cumsum(nsf)])
+    fn_map = np.concatenate([np.arange(first[a], first[a] + sub_nsf[k]) for k, a in enumerate(keep)]) \
+        if keep else np.zeros(0, np.int64)
+    w = copy.copy(wl)
+    w.name = "%s_rank%d" % (wl.name, rank)
+    w.pos = pos[keep]
+    w.r_loc = np.asarray(wl.r_loc)[keep]
+    w.r_fine = np.asarray(wl.r_fine)[keep]
+    w.nsf = sub_nsf
+    return w, np.asarray(keep, np.int64), fn_map.astype(np.int64)

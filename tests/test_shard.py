@@ -8,6 +8,7 @@ import socket
 import sys
 
 import numpy as np
+import pytest
 
 from paper_1401_7441_gb300 import inputs as I
 from paper_1401_7441_gb300 import lsw
@@ -155,3 +156,47 @@ def test_sharded_rows_equal_single_process_gloo():
             for j, k in enumerate(range(geo.row_ptr[a], geo.row_ptr[a + 1])):
                 assert vals[j][0] == Sm[k] and vals[j][1] == H[k], (a, k)
     assert seen == set(range(len(geo.sf_atom)))                   # every row owned once
+
+
+@pytest.mark.parametrize("name,world", [("atoms64", 2), ("atoms64", 3), ("atoms1200_small", 2),
+                                        ("atoms64_cutoff8", 2)])
+def test_subsystem_reproduces_the_owned_functions(name, world):
+    # through the library (host-only): in each rank's sub-system every own function has
+    # the same L and L' keys and offsets as in the whole system, and its pattern row maps
+    # onto the whole system's row.  With an 8 bohr pair cutoff the halo alone misses atoms
+    # whose fine spheres reach L' (R + 8h + r_f = 11.6 bohr): the ghost atoms keep those
+    # fine points (without them 82 fine key sets of own functions differ)
+    ensure_built()
+    wl = I.scaled("atoms1200", 150, seed=4) if name == "atoms1200_small" else I.atoms64()
+    if name == "atoms64_cutoff8":
+        wl.pair_cutoff = 8.0
+    ctx = lsw.lsw_ctx_create(lsw.LSW_HOST_ONLY)
+    S = host_system(wl, ctx)
+    try:
+        owner = shard.partition_atoms(wl.pos, wl.nsf, world)
+        fown = owner[S.sf_atom]
+        covered = set()
+        for r in range(world):
+            sw, amap, fmap = shard.subsystem(wl, owner, r, S.sf_atom, S.row_ptr, S.col)
+            T = host_system(sw, ctx)
+            try:
+                assert T.n_sf == len(fmap)
+                for fs in range(T.n_sf):
+                    f = int(fmap[fs])
+                    if fown[f] != r:
+                        continue
+                    covered.add(f)
+                    a, asub = int(S.sf_atom[f]), int(T.sf_atom[fs])
+                    assert amap[asub] == a
+                    for region in (lsw.LSW_REGION_L, lsw.LSW_REGION_LP):
+                        for part in (lsw.LSW_PART_COARSE, lsw.LSW_PART_FINE):
+                            assert np.array_equal(S.keys(a, region, part), T.keys(asub, region, part)), (f, region, part)
+                    assert S.off_L[f + 1] - S.off_L[f] == T.off_L[fs + 1] - T.off_L[fs]
+                    row = fmap[T.col[T.row_ptr[fs]:T.row_ptr[fs + 1]]]
+                    assert np.array_equal(np.sort(row), S.col[S.row_ptr[f]:S.row_ptr[f + 1]])
+            finally:
+                T.close()
+        assert covered == set(range(S.n_sf))
+    finally:
+        S.close()
+        lsw.lsw_ctx_destroy(ctx)
