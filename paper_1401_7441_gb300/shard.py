@@ -126,3 +126,42 @@ def subsystem(wl, owner, rank, sf_atom, row_ptr, col):
     w.r_fine = np.asarray(wl.r_fine)[keep]
     w.nsf = sub_nsf
     return w, np.asarray(keep, np.int64), fn_map.astype(np.int64)
+
+
+def cell_weights(blocks_lo, blocks_hi, dims, symmetric=True):
+    """Per grid plane along x, the total App. D weight of its points: m(m + 1)/2 per point
+    (m^2 without symmetry), m the number of blocks [lo, hi] (inclusive, grid indices) that
+    contain the point.  Returns an array of length dims[0]."""
+    cnt = np.zeros(tuple(int(d) for d in dims[::-1]), np.int32)        # [z][y][x]
+    for lo, hi in zip(np.asarray(blocks_lo), np.asarray(blocks_hi)):
+        lo = np.maximum(lo, 0)
+        hi = np.minimum(hi, np.asarray(dims) - 1)
+        if np.any(hi < lo):
+            continue
+        cnt[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] += 1
+    m = cnt.astype(np.float64)
+    w = m * (m + 1) / 2 if symmetric else m * m
+    return w.sum(axis=(0, 1))
+
+
+def cell_partition(plane_weights, world):
+    """Cut the cell into ``world`` slabs of consecutive x planes whose weights are as even
+    as a plane-granular cut allows (App. D: the total weight divided among the tasks).
+    Returns the first plane of each slab and the end: bounds[r] .. bounds[r + 1] - 1.
+
+    Cut r is placed at the plane where the running total first reaches r / world of the
+    total, moved back by one plane when that leaves the slab closer to its share."""
+    w = np.asarray(plane_weights, np.float64)
+    n = len(w)
+    total = float(w.sum())
+    csum = np.concatenate([[0.0], np.cumsum(w)])
+    bounds = [0]
+    for r in range(1, world):
+        target = total * r / world
+        k = int(np.searchsorted(csum, target, side="left"))
+        k = min(max(k, bounds[-1] + 1), n - (world - r))
+        if k - 1 > bounds[-1] and abs(csum[k - 1] - target) < abs(csum[k] - target):
+            k -= 1
+        bounds.append(k)
+    bounds.append(n)
+    return np.asarray(bounds, np.int64)

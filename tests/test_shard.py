@@ -200,3 +200,53 @@ def test_subsystem_reproduces_the_owned_functions(name, world):
     finally:
         S.close()
         lsw.lsw_ctx_destroy(ctx)
+
+
+def test_cell_weights_count_the_blocks_touching_each_point():
+    # two blocks on a 6 x 1 x 1 line: points 0-1 in one, 2-3 in both, 4-5 in the other
+    lo = np.array([[0, 0, 0], [2, 0, 0]])
+    hi = np.array([[3, 0, 0], [5, 0, 0]])
+    assert np.array_equal(shard.cell_weights(lo, hi, [6, 1, 1]), [1, 1, 3, 3, 1, 1])       # m(m+1)/2
+    assert np.array_equal(shard.cell_weights(lo, hi, [6, 1, 1], symmetric=False), [1, 1, 4, 4, 1, 1])
+
+
+def test_cell_partition_is_as_even_as_planes_allow():
+    rng = np.random.default_rng(0)
+    for world in (2, 3, 4, 7):
+        w = rng.uniform(0, 10, 97) ** 2
+        b = shard.cell_partition(w, world)
+        assert b[0] == 0 and b[-1] == len(w) and np.all(np.diff(b) >= 1)
+        loads = np.array([w[b[r]:b[r + 1]].sum() for r in range(world)])
+        # each cut is within one plane of its ideal position
+        assert np.max(np.abs(np.cumsum(loads)[:-1] - w.sum() * np.arange(1, world) / world)) <= w.max()
+    # uniform weights split exactly
+    assert np.array_equal(shard.cell_partition(np.ones(12), 4), [0, 3, 6, 9, 12])
+
+
+def test_cell_partition_balances_the_density_work_of_a_workload():
+    # the real-space blocks of atoms64: slabs by weight carry about equal m(m+1)/2 totals,
+    # unlike equal-width slabs (the centre of the cell is denser than its edges)
+    ensure_built()
+    wl = I.atoms64()
+    ctx = lsw.lsw_ctx_create(lsw.LSW_HOST_ONLY)
+    S = host_system(wl, ctx)
+    try:
+        boxes = []
+        for f in range(S.n_sf):
+            k = S.keys(int(S.sf_atom[f]), lsw.LSW_REGION_L, lsw.LSW_PART_COARSE)
+            g0, g1 = k[:, 0], k[:, 1]
+            N = wl.N
+            lo = np.array([(g0 % N[0]).min(), ((g0 // N[0]) % N[1]).min(), (g0 // (N[0] * N[1])).min()])
+            hi = np.array([(g1 % N[0]).max(), ((g1 // N[0]) % N[1]).max(), (g1 // (N[0] * N[1])).max()])
+            boxes.append((2 * lo - 14 - np.array(wl.V_lo), 2 * hi + 16 - np.array(wl.V_lo)))
+        w = shard.cell_weights([b[0] for b in boxes], [b[1] for b in boxes], wl.V_shape)
+        world = 4
+        b = shard.cell_partition(w, world)
+        loads = np.array([w[b[r]:b[r + 1]].sum() for r in range(world)])
+        eq = np.linspace(0, len(w), world + 1).astype(int)
+        eq_loads = np.array([w[eq[r]:eq[r + 1]].sum() for r in range(world)])
+        assert loads.max() / loads.mean() < 1.02
+        assert eq_loads.max() / eq_loads.mean() > loads.max() / loads.mean()
+    finally:
+        S.close()
+        lsw.lsw_ctx_destroy(ctx)
