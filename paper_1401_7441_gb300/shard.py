@@ -153,6 +153,8 @@ def cell_partition(plane_weights, world):
     total, moved back by one plane when that leaves the slab closer to its share."""
     w = np.asarray(plane_weights, np.float64)
     n = len(w)
+    if not 1 <= world <= n:
+        raise ValueError("cell_partition: %d slabs of %d planes" % (world, n))
     total = float(w.sum())
     csum = np.concatenate([[0.0], np.cumsum(w)])
     bounds = [0]

@@ -219,8 +219,11 @@ def test_cell_partition_is_as_even_as_planes_allow():
         loads = np.array([w[b[r]:b[r + 1]].sum() for r in range(world)])
         # each cut is within one plane of its ideal position
         assert np.max(np.abs(np.cumsum(loads)[:-1] - w.sum() * np.arange(1, world) / world)) <= w.max()
-    # uniform weights split exactly
+    # uniform weights split exactly; one plane per slab at the limit; more slabs than planes
     assert np.array_equal(shard.cell_partition(np.ones(12), 4), [0, 3, 6, 9, 12])
+    assert np.array_equal(shard.cell_partition(np.array([5.0, 0.0, 0.0]), 3), [0, 1, 2, 3])
+    with pytest.raises(ValueError):
+        shard.cell_partition(np.ones(2), 3)
 
 
 def test_cell_partition_balances_the_density_work_of_a_workload():
