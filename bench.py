@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--tile", type=int, default=0)
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--oracle-functions", type=int, default=512,
+                   help="functions of the oracle sample (CPU baseline and errors)")
     p.add_argument("--sync-each", action="store_true",
                    help="warm-up only: wait for the device and check its status after every call")
     return p.parse_args()
@@ -83,18 +85,24 @@ def workload(name):
 
 
 def kernels_source_hash():
-    """SHA-256 of the kernel source: ties a stored ncu traffic figure to the kernels
-    it was measured on."""
+    """SHA-256 over the CUDA sources (every .cu file and the internal header, in name
+    order): ties a stored ncu traffic figure to the kernels it was measured on."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1401_7441_gb300", "csrc", "lsw_kernels.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+    d = os.path.join(ROOT, "paper_1401_7441_gb300", "csrc")
+    hs = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith(".cu") or name == "lsw_internal.h":
+            hs.update(name.encode())
+            hs.update(open(os.path.join(d, name), "rb").read())
+    return hs.hexdigest()
 
 
-def stored_traffic(kernel, workload, prec, batch):
+def stored_traffic(kernel, prec, fns_per_launch):
     """(DRAM bytes per launch of ``kernel``, note) from profiles/roofline_traffic.json, if
-    that file was written from an ncu capture of the current kernel source (else (None,
-    reason)).  The plane and z-stage kernels move bytes in proportion to the functions of
-    a launch, so a capture at another batch size is scaled by the batch ratio."""
+    that file was written from an ncu capture of the current kernel sources (else (None,
+    reason)).  The capture stores bytes per support function of a launch (the kernels'
+    traffic grows with the functions they process); they are scaled to this launch's
+    functions."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         rec = json.load(open(path))
@@ -103,13 +111,11 @@ def stored_traffic(kernel, workload, prec, batch):
     if rec.get("kernels_sha256") != kernels_source_hash():
         return None, "stored capture is of another kernel source"
     ent = rec.get("kernels", {}).get(kernel)
-    if not ent or ent.get("precision") != prec or not batch:
+    if not ent or ent.get("precision") != prec or not fns_per_launch:
         return None, "no stored capture for this kernel and precision"
-    per = ent.get("dram_bytes_per_launch")
-    if ent.get("batch") == batch:
-        return per, "ncu capture, %s" % rec.get("note", "")
-    return per * batch / ent["batch"], ("ncu capture at batch %d scaled to batch %d by the functions per launch; %s"
-                                        % (ent["batch"], batch, rec.get("note", "")))
+    per_fn = ent["dram_bytes_per_function"]
+    return per_fn * fns_per_launch, ("ncu capture (%s: %d functions per launch) scaled to %d functions per launch"
+                                     % (rec.get("workload", "?"), ent.get("functions_per_launch", 0), fns_per_launch))
 
 
 def keys_to_g(keys):
@@ -121,87 +127,189 @@ def keys_to_g(keys):
 
 
 # ---------------------------------------------------------------- oracle (CPU) leg
+#
+# The oracle (plain FP64 numpy, written from the paper) timed on the host cores: H phi of
+# a bounded sample of functions, spread over a pool of worker processes (spawned, so no
+# process inherits a CUDA context), then S/H entries of pattern pairs among them.
 
-def oracle_sample(wl, budget_s=20.0, max_fn=None, keep=None):
-    """Time the oracle on a bounded sample: H phi of the first functions, then the S/H
-    entries between them.  Returns (functions/s, cores, description); with ``keep`` (a
-    dict) also stores the sample's results there for the error report."""
+_ORC = {}
+
+
+def _orc_desc(wl):
     from oracle import geometry as G
-    from oracle import hamiltonian as Hm
-    from oracle import matrices as Mx
-    desc = G.SystemDesc(tuple(wl.N), wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff,
+    return G.SystemDesc(tuple(wl.N), wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff,
                         wl.pair_mode, wl.lprime_margin, wl.fine_mode)
-    nsf = int(np.sum(wl.nsf))
-    sf_atom = np.repeat(np.arange(len(wl.nsf)), wl.nsf)
-    t0 = time.perf_counter()
-    geo = G.build(desc, atoms=sorted(set(sf_atom[:min(nsf, 64)].tolist())), pattern=False)
-    V = None
-    done = []
-    tf = time.perf_counter()
-    hphi, phi = {}, {}
-    for f in range(nsf if max_fn is None else min(nsf, max_fn)):
-        a = int(sf_atom[f])
-        if geo.L[a] is None:
-            break
+
+
+def _orc_init(wl_name, atoms):
+    from oracle import geometry as G
+    wl = workload(wl_name)
+    _ORC["wl"] = wl
+    _ORC["geo"] = G.build(_orc_desc(wl), atoms=atoms, pattern=False)
+
+
+def _orc_hphi(fs):
+    """H phi, E_kin, E_pot of the functions ``fs`` by the oracle (in a worker)."""
+    from oracle import hamiltonian as Hm
+    wl, geo = _ORC["wl"], _ORC["geo"]
+    out = []
+    for f in fs:
+        a = int(geo.sf_atom[f])
         L = geo.L[a]
-        phi[f] = I.phi_values(wl, f, a, L.coarse.g, L.fine.g)
+        phi = I.phi_values(wl, f, a, L.coarse.g, L.fine.g)
         lo = [2 * int(L.lo[d]) - 14 for d in range(3)]
         shape = [2 * int(L.hi[d] - L.lo[d] + 1) + 29 for d in range(3)]
         Vb = I.potential_block(wl, lo, shape)
-        hphi[f], ek_f, ep_f = Hm.apply_hamiltonian(geo, f, phi[f], Vb, lo)
-        if keep is not None:
-            keep.setdefault("energies", {})[f] = (ek_f, ep_f)
-        done.append(f)
-        if time.perf_counter() - tf > budget_s:
-            break
-    ents = {}
-    for a in done:
-        for b in done:
-            ents[(a, b)] = (Mx.overlap_entry(geo, a, b, phi[a], phi[b]),
-                            Mx.hamiltonian_entry(geo, a, b, phi[a], hphi[b]))
-    dt = time.perf_counter() - tf
-    if keep is not None:
-        keep.update(done=done, phi=phi, hphi=hphi, entries=ents)
-    cores = 1
+        h, ek, ep = Hm.apply_hamiltonian(geo, f, phi, Vb, lo)
+        out.append((f, phi, h, ek, ep))
+    return out
+
+
+def cpu_model():
     try:
-        import threadpoolctl  # noqa: F401
+        for ln in open("/proc/cpuinfo"):
+            k = ln.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware"):
+                return ln.split(":", 1)[1].strip()
     except Exception:
         pass
-    sample = ("oracle (numpy FP64, 1 thread of %d host cores) on the first %d of %d support functions: "
-              "H phi each, then S and H entries among them; %.1f s" % (os.cpu_count() or 1, len(done), nsf, dt))
-    _ = t0
-    return len(done) / dt, cores, sample
+    import platform
+    return platform.processor() or platform.machine()
 
 
-def error_report(ref, S, hphi_dev, ek_dev, ep_dev, H_dev, S_dev, cutoff_pairs):
-    """Errors of the GPU results against the oracle sample (scaled as in the parity
-    tests: H phi normwise per function, energies and H/S entries by Cauchy-Schwarz
-    bounds)."""
-    done = ref["done"]
-    hp = hphi_dev.double().cpu().numpy()
-    ek, ep = ek_dev.cpu().numpy(), ep_dev.cpu().numpy()
-    e_h, e_en = [], []
+class OraclePool:
+    """Worker processes (spawn) holding the oracle's geometry of a sample of atoms."""
+
+    def __init__(self, wl_name, atoms, cores):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.cores = max(1, int(cores))
+        old = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in old:
+            os.environ[k] = "1"                      # one thread per worker process
+        try:
+            self.ex = cf.ProcessPoolExecutor(self.cores, mp_context=mp.get_context("spawn"),
+                                             initializer=_orc_init, initargs=(wl_name, atoms))
+            list(self.ex.map(int, range(self.cores)))   # start every worker now
+            _orc_init(wl_name, atoms)                    # this process: the entries
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def hphi(self, fs):
+        chunks = [fs[i::self.cores] for i in range(self.cores) if fs[i::self.cores]]
+        out = []
+        for part in self.ex.map(_orc_hphi, chunks):
+            out.extend(part)
+        return out
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def sample_functions(wl, n_fn):
+    """The n_fn functions whose atoms are nearest the cell's centre (so that many of their
+    pattern partners are in the sample), and their atoms."""
+    pos = np.asarray(wl.pos)
+    c = pos.mean(axis=0)
+    order = np.argsort(np.sum((pos - c) ** 2, axis=1), kind="stable")
+    first = np.concatenate([[0], np.cumsum(wl.nsf)])
+    fs, atoms = [], []
+    for a in order:
+        if len(fs) >= n_fn:
+            break
+        if wl.nsf[a] == 0:
+            continue
+        atoms.append(int(a))
+        fs.extend(range(int(first[a]), int(first[a + 1])))
+    return sorted(fs[:n_fn]), sorted(atoms)
+
+
+def oracle_entries(geo, done, row_ptr, col, max_entries, seed=3):
+    """Pattern entries (a, b) with both functions in ``done`` (seeded subsample of at most
+    max_entries): {(a, b): (S_ab, H_ab)} by the oracle, and the time it took."""
+    from oracle import matrices as Mx
+    have = set(done["phi"].keys())
+    pairs = [(a, int(col[k])) for a in sorted(have) for k in range(row_ptr[a], row_ptr[a + 1]) if int(col[k]) in have]
+    if len(pairs) > max_entries:
+        rng = np.random.default_rng(seed)
+        pairs = [pairs[i] for i in sorted(rng.choice(len(pairs), size=max_entries, replace=False))]
+    t0 = time.perf_counter()
+    ents = {(a, b): (Mx.overlap_entry(geo, a, b, done["phi"][a], done["phi"][b]),
+                     Mx.hamiltonian_entry(geo, a, b, done["phi"][a], done["hphi"][b])) for a, b in pairs}
+    return ents, time.perf_counter() - t0
+
+
+def oracle_run(wl, pool, fs, row_ptr, col, max_entries):
+    """The oracle on functions ``fs`` (pool) and the entries among them (this process,
+    whose geometry the pool set up).
+    Returns (results dict, seconds for H phi, seconds per entry)."""
+    t0 = time.perf_counter()
+    res = pool.hphi(fs)
+    t_h = time.perf_counter() - t0
+    done = {"phi": {f: p for f, p, _, _, _ in res}, "hphi": {f: h for f, _, h, _, _ in res},
+            "energies": {f: (ek, ep) for f, _, _, ek, ep in res}}
+    ents, t_e = oracle_entries(_ORC["geo"], done, row_ptr, col, max_entries)
+    done["entries"] = ents
+    return done, t_h, (t_e / len(ents) if ents else 0.0)
+
+
+def cpu_baseline_of(wl, n_fn, nnz_per_fn, t_h, t_entry, cores, n_entries):
+    """Oracle support functions/s for H phi plus the function's row of S and H: H phi
+    time per function (measured on ``cores`` processes) plus the measured time per entry
+    times the mean pattern entries per function (extrapolated)."""
+    per_fn = t_h / n_fn + t_entry * nnz_per_fn / cores
+    sample = ("oracle (numpy FP64) on %d host cores (%d in the machine, %s): H phi of the %d support functions "
+              "nearest the cell centre in %.1f s, then %d S/H entries among them at %.2f ms each (one process); "
+              "per function: H phi time + %.0f entries (the mean pattern row) at that rate / %d cores, extrapolated"
+              % (cores, os.cpu_count() or 1, cpu_model(), n_fn, t_h, n_entries, 1e3 * t_entry, nnz_per_fn, cores))
+    return {"value": 1.0 / per_fn, "unit": "support_functions/s", "cores": cores, "kind": "oracle",
+            "sample": sample}
+
+
+def error_report(ref, S, hphi_dev, ek_dev, ep_dev, H_dev, S_dev, tag="FP64 CPU oracle"):
+    """Errors of the GPU results against a reference sample: H phi normwise per function
+    and element by element (each element against tau-free scale |H phi|_max of its
+    function), energies and H/S entries by Cauchy-Schwarz bounds."""
+    done = sorted(ref["hphi"].keys())
+    hp = hphi_dev.double().cpu().numpy() if hasattr(hphi_dev, "cpu") else hphi_dev
+    ek = ek_dev.cpu().numpy() if hasattr(ek_dev, "cpu") else ek_dev
+    ep = ep_dev.cpu().numpy() if hasattr(ep_dev, "cpu") else ep_dev
+    e_h, e_el, e_en = [], [], []
     for f in done:
         h = ref["hphi"][f]
         o = int(S.off_Lp[f])
         g = hp[o:o + len(h)]
         e_h.append(float(np.linalg.norm(g - h) / np.linalg.norm(h)))
+        e_el.append(float(np.max(np.abs(g - h)) / np.max(np.abs(h))))
         scale = np.linalg.norm(ref["phi"][f]) * np.linalg.norm(h)
         rk, rp_ = ref["energies"][f]
         e_en.append(float(max(abs(ek[f] - rk), abs(ep[f] - rp_)) / scale))
-    Hh, Sh = H_dev.cpu().numpy(), S_dev.cpu().numpy()
+    Hh = H_dev.cpu().numpy() if hasattr(H_dev, "cpu") else H_dev
+    Sh = S_dev.cpu().numpy() if hasattr(S_dev, "cpu") else S_dev
     e_s, e_hh = [], []
-    for (a, b), (sv, hv) in ref["entries"].items():
+    for (a, b), (sv, hv) in ref.get("entries", {}).items():
         row = S.col[S.row_ptr[a]:S.row_ptr[a + 1]]
         k = np.searchsorted(row, b)
         if k < len(row) and row[k] == b:
             kk = int(S.row_ptr[a] + k)
             e_s.append(abs(Sh[kk] - sv) / (np.linalg.norm(ref["phi"][a]) * np.linalg.norm(ref["phi"][b])))
             e_hh.append(abs(Hh[kk] - hv) / (np.linalg.norm(ref["phi"][a]) * np.linalg.norm(ref["hphi"][b])))
-    return {"against": "FP64 CPU oracle", "functions": len(done), "entries": len(e_s),
+    return {"against": tag, "functions": len(done), "entries": len(e_s),
             "hphi_rel_max": max(e_h), "hphi_rel_mean": float(np.mean(e_h)),
+            "hphi_elem_rel_max": max(e_el),
             "energy_scaled_max": max(e_en),
             "S_scaled_max": float(max(e_s)) if e_s else None, "H_scaled_max": float(max(e_hh)) if e_hh else None}
+
+
+def canonical_config(wl, prec, n_sf):
+    """The workload's identity, the same in both arms of the benchmark."""
+    return {"workload": wl.name, "atoms": int(len(wl.pos)), "support_functions": int(n_sf),
+            "grid": [int(x) for x in wl.N], "h_bohr": wl.h, "precision": prec,
+            "l2": "flushed (512 MB write) before every timed step"}
 
 
 def reference_main(args):
@@ -210,20 +318,33 @@ def reference_main(args):
         return 0
     wl = workload(args.workload or "atoms10k")
     prec = args.precision or wl.precision
-    # the whole --steps/--warmup run must end within a few minutes: bound each step
-    per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, cores, sample = oracle_sample(wl, budget_s=per_step)
-        if i >= args.warmup:
-            vals.append(v)
+    cores = os.cpu_count() or 1
+    from oracle import geometry as G
+    row_ptr, col = G.pair_pattern(_orc_desc(wl), np.repeat(np.arange(len(wl.nsf)), wl.nsf))
+    nnz_per_fn = len(col) / max(1, wl.n_sf)
+    # one step = H phi of 2 functions per core + their row entries (extrapolated), so the
+    # whole --steps/--warmup run ends within a few minutes
+    n_step = 2 * cores
+    fs_all, atoms = sample_functions(wl, n_step * (args.steps + args.warmup))
+    pool = OraclePool(args.workload or "atoms10k", atoms, cores)
+    vals, samples = [], []
+    try:
+        for i in range(args.warmup + args.steps):
+            fs = fs_all[i * n_step:(i + 1) * n_step] or fs_all[:n_step]
+            done, t_h, t_e = oracle_run(wl, pool, fs, row_ptr, col, max_entries=64)
+            cb = cpu_baseline_of(wl, len(fs), nnz_per_fn, t_h, t_e, cores, len(done["entries"]))
+            if i >= args.warmup:
+                vals.append(cb["value"])
+                samples.append(cb["sample"])
+    finally:
+        pool.close()
     val = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "support_functions/s",
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / val,
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * n_step / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "precision_of_ours": prec},
+            "data": "synthetic", "config": canonical_config(wl, prec, wl.n_sf),
             "cpu_baseline": {"value": val, "unit": "support_functions/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": "per step: " + samples[-1]},
             "e2e": {"value": val, "unit": "support_functions/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -464,81 +585,124 @@ def gpu_main(args):
     clocks = clk.summary(local)
     value = job_value(S.n_sf, args.steps, world, total_ms)
 
-    # end to end through host buffers (pinned)
-    e2e = None
+    # end to end through the host API (pinned host buffers): phi host -> device, the
+    # step, H and S device -> host; and the same with H phi copied back too
+    e2e = e2e_h = None
     if not args.no_e2e:
         phi_h = phi.cpu().pin_memory()
         hphi_h = torch.empty(S.total_Lp, dtype=dt).pin_memory()
         H_h = torch.empty(max(1, nnz), dtype=torch.float64).pin_memory()
         S_h = torch.empty(max(1, nnz), dtype=torch.float64).pin_memory()
-        lsw.lsw_step_host(S.sys, phi_h, None, H_h, S_h)
         k2 = max(1, min(args.steps, 3))
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(k2):
-            lsw.lsw_step_host(S.sys, phi_h, None, H_h, S_h)
-        el = aggregate(time.perf_counter() - t0, world, device="cuda")
-        e2e = {"value": job_value(S.n_sf, k2, world, 1000.0 * el), "unit": "support_functions/s",
-               "h2d_bytes_per_step": int(phi_h.numel() * phi_h.element_size()),
-               "d2h_bytes_per_step": int(2 * nnz * 8)}
-        _ = hphi_h
+        for with_h in (False, True):
+            lsw.lsw_step_host(S.sys, phi_h, hphi_h if with_h else None, H_h, S_h)
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(k2):
+                lsw.lsw_step_host(S.sys, phi_h, hphi_h if with_h else None, H_h, S_h)
+            el = aggregate(time.perf_counter() - t0, world, device="cuda")
+            rec = {"value": job_value(S.n_sf, k2, world, 1000.0 * el), "unit": "support_functions/s",
+                   "h2d_bytes_per_step": int(phi_h.numel() * phi_h.element_size()),
+                   "d2h_bytes_per_step": int(2 * nnz * 8 + (hphi_h.numel() * hphi_h.element_size() if with_h else 0)),
+                   "steps": k2}
+            if with_h:
+                e2e_h = rec
+            else:
+                e2e = rec
 
-    # roofline of the dominant kernel
-    flops, comp_bytes = kernel_work(S, wl, prec)
+    # roofline: the method's own work per kernel (workcount) over the kernels' device time
+    from paper_1401_7441_gb300 import workcount as WC
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as wpool:
+        flops, wnote = WC.hphi_work(S, wl.N, pool=wpool)
+    hs_mac, hs_se = WC.hs_work(S)
+    flops["hs_tiles"] = 2.0 * hs_mac
+    wnote["hs_rel_se"] = hs_se
+    dense, comp_bytes = kernel_work(S, wl, prec)
+    peak_alu = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+    peak_meas = peaks["fp64_fma_tflops"] if prec == "fp64" else peaks["fp32_fma_tflops"]
+    hbm_peak = None
+    try:
+        hbm_peak = json.load(open(PEAKS_PATH)).get("hbm_gbs")
+    except Exception:
+        pass
+    hbm_peak = hbm_peak or 6800.0
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    batch_now = args.batch or (tune or {}).get("chosen", {}).get("batch") or None
+    per_kernel = {}
+    for k, (ms_tot, n_l) in kinds.items():
+        ms_step, l_step = ms_tot / args.steps, n_l / args.steps
+        ent = {"ms_per_step": ms_step, "launches_per_step": l_step}
+        if k in flops:
+            ent["method_tflop_per_step"] = flops[k] / 1e12
+            ent["method_tflops"] = flops[k] / (ms_step / 1e3) / 1e12
+            ent["alu_frac"] = ent["method_tflops"] / peak_alu
+        if k in dense:
+            ent["dense_box_tflops"] = dense[k] / (ms_step / 1e3) / 1e12
+        fpl = S.n_sf / l_step if l_step else None
+        tr, _ = stored_traffic(k, prec, fpl)
+        if tr is not None:
+            ent["dram_gb_per_launch"] = tr / 1e9
+            ent["dram_gbs"] = tr / (ms_tot / n_l / 1e3) / 1e9
+            ent["hbm_frac"] = ent["dram_gbs"] / hbm_peak
+        per_kernel[k] = ent
     dom = max(kinds, key=lambda k: kinds[k][0]) if kinds else None
     roof = None
     if dom is not None:
         ms_tot, n_launch = kinds[dom]
         per_launch_ms = ms_tot / n_launch
+        fpl = S.n_sf / (n_launch / args.steps)
+        traffic, traffic_note = stored_traffic(dom, prec, fpl)
         if dom in flops:
-            launches_per_step = n_launch / args.steps
-            work_per_launch = flops[dom] / launches_per_step
-            peak = peaks["fp64_fma_tflops"] if prec == "fp64" else peaks["fp32_fma_tflops"]
+            work_per_launch = flops[dom] / (n_launch / args.steps)
             ach = work_per_launch / (per_launch_ms / 1000.0) / 1e12
-            traffic, traffic_note = stored_traffic(dom, wl.name, prec,
-                                                   args.batch or (tune or {}).get("chosen", {}).get("batch"))
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak,
-                    "traffic": traffic, "traffic_note": traffic_note,
-                    "peak_source": "measured on this GPU: %s FMA loop over every SM (lsw_measure_peaks); "
-                                   "nominal %.1f TFLOP/s" % ("FP64" if prec == "fp64" else "FP32",
-                                                            FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS)}
-        else:
-            roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
-                    "frac": None, "traffic": None}
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
+                    "frac": ach / peak_alu, "traffic": traffic, "traffic_note": traffic_note,
+                    "work": "method flop per launch %.4g (workcount: in-range taps over the nonzero support of each "
+                            "pass, %s)" % (work_per_launch, "exact" if wnote.get("exact") else
+                                           "exact on %d sampled atoms" % wnote.get("atoms_counted", 0)),
+                    "peak_source": "%s: 152 SMs x %s x 2 flop x 2.07 GHz (recipe unit counts and clock); the FMA "
+                                   "loop of lsw_measure_peaks reaches %.1f on this GPU"
+                                   % ("FP64 nominal" if prec == "fp64" else "FP32 nominal",
+                                      "FP64 units" if prec == "fp64" else "128 lanes", peak_meas)}
     kshare = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()} if kinds else {}
     launches_per_step = int(sum(v[1] for v in kinds.values()) / args.steps) if kinds else None
 
-    cpu = None
-    err = None
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        ref = {}
-        v, cores, sample = oracle_sample(wl, budget_s=20.0, keep=ref)
-        cpu = {"value": v, "unit": "support_functions/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cores = os.cpu_count() or 1
+        n_fn = min(S.n_sf, args.oracle_functions)
+        fs, atoms = sample_functions(wl, n_fn)
+        pool = OraclePool(args.workload or "atoms10k", atoms, cores)
+        try:
+            ref, t_h, t_e = oracle_run(wl, pool, fs, S.row_ptr, S.col, max_entries=400)
+        finally:
+            pool.close()
+        cpu = cpu_baseline_of(wl, len(fs), nnz / S.n_sf, t_h, t_e, cores, len(ref["entries"]))
         step()
         torch.cuda.synchronize()
-        err = error_report(ref, S, hphi, ek, ep, Hm, Sm, None)
+        err = error_report(ref, S, hphi, ek, ep, Hm, Sm)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "support_functions/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "fp32": "f32", "bf16x": "f32+bf16x3"}[prec], "data": "synthetic",
-                "config": {"workload": wl.name, "atoms": len(wl.pos), "support_functions": S.n_sf,
-                           "pattern_nnz": nnz, "grid": list(wl.N), "h_bohr": wl.h,
-                           "precision": prec, "l2": "flushed (512 MB write) before every timed step",
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "options": (tune or {}).get("chosen", {"batch": args.batch or None, "tile": args.tile or None}),
-                           "autotune_ms": {k: v for k, v in (tune or {}).items() if k != "chosen"}},
-                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "error_vs_oracle": err, "peaks_measured": peaks, "clocks": clocks,
+                "config": canonical_config(wl, prec, S.n_sf),
+                "e2e": e2e, "e2e_with_hphi": e2e_h, "roofline": roof, "cpu_baseline": cpu,
+                "error_vs_oracle": err, "clocks": clocks,
                 "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
-                "kernel_share": kshare,
-                "algorithmic_tflop_per_step": {k: v / 1e12 for k, v in flops.items()},
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+                "parallelism": "replicas" if world > 1 else "single",
+                "pattern_nnz": nnz,
+                "tuning": {"options": (tune or {}).get("chosen", {"batch": args.batch or None, "tile": args.tile or None}),
+                           "autotune_ms": {k: v for k, v in (tune or {}).items() if k != "chosen"}},
+                "kernels": per_kernel, "kernel_share": kshare, "work_count": wnote,
+                "dense_box_tflop_per_step": {k: v / 1e12 for k, v in dense.items()},
                 "compulsory_gb_per_step": comp_bytes / 1e9,
-                "setup_s": t_setup, "step_ms": step_ms}
+                "compulsory_hbm_frac": comp_bytes / (total_ms / args.steps / 1e3) / 1e9 / hbm_peak,
+                "peaks_measured": peaks, "setup_s": t_setup, "step_ms": step_ms}
         print(json.dumps(line))
     S.close()
     if world > 1:

@@ -173,10 +173,9 @@ lsw_status lsw_apply_hamiltonian(lsw_system sys, const void* phi_dev, void* hphi
 
 /* Allocation-free H phi.  The paper has no counterpart: this entry point exists for
  * callers that must not allocate device memory while they work - a serving process
- * that reserves its HBM budget up front and forbids allocation on the request path,
- * an application whose device memory belongs to another allocator's pool (where a
- * stray cudaMalloc bypasses the pool's accounting and fails once the pool holds the
- * memory), or code issuing work inside a stream capture it does not own.
+ * that reserves its HBM budget up front and forbids allocation on the request path, or
+ * an application whose device memory belongs to another allocator's pool (where a stray
+ * cudaMalloc bypasses the pool's accounting and fails once the pool holds the memory).
  * Same arguments, layouts and results as lsw_apply_hamiltonian (tolerance of the
  * precision), computed batch by batch in a fixed 32 MiB device array that the library
  * defines at file scope: it calls no cudaMalloc, cudaFree or other allocating routine.
@@ -187,9 +186,13 @@ lsw_status lsw_apply_hamiltonian(lsw_system sys, const void* phi_dev, void* hphi
  * - All calls share the one array and leave the last call's contents in it; calls
  *   whose work overlaps on the GPU (other streams, other systems, other threads) race
  *   and produce wrong results: serialize them.
- * - A support function whose workspace exceeds the array returns LSW_ERR_UNSUPPORTED.
- * Asynchronous on the context stream (the per-batch records are copied from host
- * stack memory, which may wait for earlier work on the stream).
+ * - Every support function is checked before anything is enqueued: one whose
+ *   workspace (its dense L box, the two z-stage intermediates and its dense L' box)
+ *   exceeds the array, or whose box exceeds the on-chip tiles, makes the call return
+ *   LSW_ERR_UNSUPPORTED with nothing enqueued and the outputs untouched.
+ * - Each batch's records are written into the array by a kernel from the system's
+ *   resident records; the call reads no host memory on the device.
+ * Asynchronous on the system's stream.
  * Errors: LSW_ERR_ARG (NULL buffers), LSW_ERR_STATE (no potential, host-only context),
  * LSW_ERR_UNSUPPORTED, LSW_ERR_CUDA. */
 lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi_dev, void* hphi_dev,

@@ -271,3 +271,19 @@ def apply_hamiltonian(geo, f, phi_f, V, V_lo, F=None, parts=False):
         return (compress(N, Lp, tot_pot, blo), compress(N, Lp, tot_kin, blo), e_kin, e_pot)
     hphi = compress(N, Lp, tot_pot + tot_kin, blo)
     return hphi, e_kin, e_pot
+
+
+def hphi_abs_bound(geo, f, phi_f, V, V_lo, F=None):
+    """Absolute-term bound of every element of H phi_f on L'(f): the steps of
+    ``apply_hamiltonian`` taken with |phi|, |V| and every filter tap (h, g, magic,
+    kinetic blocks) replaced by its absolute value, the kinetic and potential parts
+    added in absolute value.  Each element is the sum of the magnitudes of the terms
+    whose sum is that element, so any order of evaluation rounds it by at most a
+    multiple of the unit roundoff times this bound."""
+    import dataclasses
+    F = F or _filters.load()
+    Fa = dataclasses.replace(F, h=np.abs(F.h), g=np.abs(F.g), magic=np.abs(F.magic),
+                             kin={k: np.abs(v) for k, v in F.kin.items()})
+    pot, kin, _, _ = apply_hamiltonian(geo, f, np.abs(np.asarray(phi_f, np.float64)), np.abs(V), V_lo, Fa,
+                                       parts=True)
+    return np.abs(pot) + np.abs(kin)

@@ -930,6 +930,68 @@ lsw_status run_maybe_graph(lsw_system_s* s, std::map<GraphKey, lsw_system_s::Gra
     return LSW_OK;
 }
 
+// Workspace elements of one function (D box; Bf, Bb, G and the z-arm flags), as laid out
+// by k_noalloc_records.
+void noalloc_sizes(const lsw_system_s* s, const FnRec& r, int64_t* sD, int64_t* sR) {
+    const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+    const int64_t es = static_cast<int64_t>(s->esize);
+    *sD = align64(8LL * r.n[0] * r.n[1] * r.n[2]);
+    *sR = align64(2LL * r.n[2] * Y * X) + align64(2LL * r.np[2] * Y * X) + align64(8LL * r.np[0] * r.np[1] * r.np[2]) +
+          align64((4LL * r.n[0] * r.n[1] + es - 1) / es);
+}
+FnRec noalloc_record(const lsw_system_s* s, int64_t f) {
+    FnRec r;
+    std::memset(&r, 0, sizeof(r));
+    const int a = s->sf_atom[f];
+    r.f = static_cast<int32_t>(f);
+    r.atom = a;
+    for (int d = 0; d < 3; ++d) {
+        r.lo[d] = s->L[a].lo[d];
+        r.n[d] = s->L[a].n[d];
+        r.lop[d] = s->Lp[a].lo[d];
+        r.np[d] = s->Lp[a].n[d];
+    }
+    r.off_phi = s->off_L[f];
+    r.off_hphi = s->off_Lp[f];
+    return r;
+}
+// Fold one function into a batch's launch extents and shared-memory sizes.
+void noalloc_fold(const lsw_system_s* s, const FnRec& r, int zcols, HphiLaunch* p, size_t* smem_bwd_plain) {
+    const LocregHost& Lh = s->L[r.atom];
+    const LocregHost& Ph = s->Lp[r.atom];
+    p->max_nz = std::max(p->max_nz, r.n[2]);
+    p->max_nzp = std::max(p->max_nzp, r.np[2]);
+    p->max_cols = std::max<int>(p->max_cols, (2 * r.n[1] + 29) * (2 * r.n[0] + 29));
+    p->max_rowsP = std::max(p->max_rowsP, r.np[1] * r.np[2]);
+    p->max_ptsP = std::max<int64_t>(p->max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
+    p->max_colsP = std::max(p->max_colsP, r.np[0] * r.np[1]);
+    p->max_colsL = std::max(p->max_colsL, r.n[0] * r.n[1]);
+    p->max_rowsL = std::max(p->max_rowsL, r.n[1] * r.n[2]);
+    p->max_segL = std::max<int>(p->max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
+    p->max_segP = std::max<int>(p->max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
+    size_t a1, a2, a3, a4;
+    pass_smem(r, s->esize, zcols, &a1, &a2, &a3, &a4);
+    p->smem_fwd = std::max(p->smem_fwd, a1);
+    p->smem_z = std::max(p->smem_z, a2);
+    p->smem_kin = std::max(p->smem_kin, static_cast<size_t>(2 * r.n[2] * 128) * (p->prec == 0 ? 8 : 4));
+    p->smem_bwd = std::max(p->smem_bwd, a3);
+    *smem_bwd_plain = std::max(*smem_bwd_plain, a4);
+    if (s->zsplit) {
+        p->smem_ztc = std::max(p->smem_ztc, ztc_smem(r, s->zsplit));
+        if (s->xy_tc) {
+            p->smem_bwd_tc = std::max(p->smem_bwd_tc, bwd_tc_smem(r, s->zsplit));
+            p->smem_fwd_tc = std::max(p->smem_fwd_tc, fwd_tc_smem(r, s->zsplit));
+        }
+    }
+}
+// Choose the plane kernel's staging and check the tiles against the shared memory.
+bool noalloc_finish(const lsw_system_s* s, HphiLaunch* p, size_t smem_bwd_plain) {
+    const size_t mx = s->ctx->max_smem;
+    p->gstage = p->smem_bwd + BWD_STATIC_SMEM <= mx ? 1 : 0;
+    if (!p->gstage) p->smem_bwd = smem_bwd_plain;
+    return !(p->smem_fwd > mx || p->smem_z > mx || p->smem_bwd + BWD_STATIC_SMEM > mx || p->smem_ztc > mx ||
+             p->smem_kin > mx || p->smem_bwd_tc + BWD_STATIC_SMEM > mx || p->smem_fwd_tc > mx);
+}
 }  // namespace
 
 // ============================================================================ C ABI
@@ -1240,130 +1302,75 @@ lsw_status lsw_build_density(lsw_system sys, const void* phi, const double* K, d
 
 // Allocation-free variant of lsw_apply_hamiltonian.  Works like it, batch by batch, but
 // every batch's workspace and its function records live in the library's fixed device
-// array (noalloc_scratch); the batches are planned here on the stack, the records are
-// copied into the head of the array, and the existing batch kernels run on the rest.
+// array (noalloc_scratch).  Every function is checked against the array and the on-chip
+// tiles before anything is enqueued; then, per batch, a one-thread kernel writes the
+// batch's records into the head of the array from the system's resident records (no
+// host memory is read by the device), and the existing batch kernels run on the rest.
 lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* hphi, double* ek, double* ep) {
     g_err.clear();
     if (!sys || !phi || !hphi) return fail(LSW_ERR_ARG, "lsw_apply_hamiltonian_noalloc: NULL buffer");
     if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys->V) return fail(LSW_ERR_STATE, "lsw_apply_hamiltonian_noalloc: no potential (lsw_set_potential)");
-    CUDA_TRY(cudaSetDevice(sys->ctx->device));
-    void* scratch = nullptr;
-    CUDA_TRY(noalloc_scratch(sys->ctx->device, &scratch));
     const size_t head = (NOALLOC_MAX_BATCH * sizeof(FnRec) + 255) / 256 * 256;
     const int64_t cap = static_cast<int64_t>((NOALLOC_SCRATCH_BYTES - head) / sys->esize);
     const int zcols = sys->prec == LSW_FP64 ? ZCOLS_F64 : ZCOLS_F32;
-    cudaStream_t st = sys->stream;
     const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
+    // every function on its own must fit the array and the tiles: checked before any work
+    for (int64_t f = 0; f < nf; ++f) {
+        const FnRec r = noalloc_record(sys, f);
+        int64_t sD, sR;
+        noalloc_sizes(sys, r, &sD, &sR);
+        if (sD + sR > cap)
+            return fail(LSW_ERR_UNSUPPORTED,
+                        "lsw_apply_hamiltonian_noalloc: support function %lld needs %lld bytes of workspace, more than "
+                        "the %lld bytes the fixed device array leaves after its record head",
+                        static_cast<long long>(f), static_cast<long long>((sD + sR) * static_cast<int64_t>(sys->esize)),
+                        static_cast<long long>(cap * static_cast<int64_t>(sys->esize)));
+        if (sys->zsplit && (!ztc_fits(r) || (sys->xy_tc && !xytc_fits(r))))
+            return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core kernels");
+        HphiLaunch p;
+        std::memset(&p, 0, sizeof(p));
+        p.prec = sys->prec;
+        size_t plain = 0;
+        noalloc_fold(sys, r, zcols, &p, &plain);
+        if (!noalloc_finish(sys, &p, plain))
+            return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
+    }
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    void* scratch = nullptr;
+    CUDA_TRY(noalloc_scratch(sys->ctx->device, &scratch));
+    cudaStream_t st = sys->stream;
     double* e0 = static_cast<double*>(sys->d_escratch.p);
     if (!ek) ek = e0;
     if (!ep) ep = e0 + nf;
     CUDA_TRY(cudaMemsetAsync(ek, 0, nf * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(ep, 0, nf * sizeof(double), st));
-    FnRec recs[NOALLOC_MAX_BATCH];
-    int64_t sizeD[NOALLOC_MAX_BATCH], sizeR[NOALLOC_MAX_BATCH];
     int64_t f = 0;
     while (f < nf) {
-        int nb = 0;
-        int64_t needD = 0, needR = 0;
-        while (f + nb < nf && nb < NOALLOC_MAX_BATCH) {
-            FnRec r;
-            std::memset(&r, 0, sizeof(r));
-            const int a = sys->sf_atom[f + nb];
-            r.f = static_cast<int32_t>(f + nb);
-            r.atom = a;
-            for (int d = 0; d < 3; ++d) {
-                r.lo[d] = sys->L[a].lo[d];
-                r.n[d] = sys->L[a].n[d];
-                r.lop[d] = sys->Lp[a].lo[d];
-                r.np[d] = sys->Lp[a].n[d];
-            }
-            r.off_phi = sys->off_L[f + nb];
-            r.off_hphi = sys->off_Lp[f + nb];
-            const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
-            const int64_t sD = align64(8LL * r.n[0] * r.n[1] * r.n[2]);
-            const int64_t sR = align64(2LL * r.n[2] * Y * X) + align64(2LL * r.np[2] * Y * X) +
-                               align64(8LL * r.np[0] * r.np[1] * r.np[2]) +
-                               align64((4LL * r.n[0] * r.n[1] + static_cast<int64_t>(sys->esize) - 1) /
-                                       static_cast<int64_t>(sys->esize));
-            if (needD + sD + needR + sR > cap) break;
-            recs[nb] = r;
-            sizeD[nb] = sD;
-            sizeR[nb] = sR;
-            needD += sD;
-            needR += sR;
-            ++nb;
-        }
-        if (nb == 0)
-            return fail(LSW_ERR_UNSUPPORTED,
-                        "lsw_apply_hamiltonian_noalloc: support function %lld needs more workspace than the %zu-byte "
-                        "fixed device scratch",
-                        static_cast<long long>(f), NOALLOC_SCRATCH_BYTES);
         HphiLaunch p;
         std::memset(&p, 0, sizeof(p));
         p.prec = sys->prec;
-        p.nfn = nb;
         p.zcols = zcols;
         size_t smem_bwd_plain = 0;
-        int64_t o = 0;
-        for (int k = 0; k < nb; ++k) {
-            recs[k].ws_D = o;
-            o += sizeD[k];
+        int nb = 0;
+        int64_t need = 0;
+        while (f + nb < nf && nb < NOALLOC_MAX_BATCH) {
+            const FnRec r = noalloc_record(sys, f + nb);
+            int64_t sD, sR;
+            noalloc_sizes(sys, r, &sD, &sR);
+            if (need + sD + sR > cap) break;
+            need += sD + sR;
+            p.ws_D_elems += sD;
+            noalloc_fold(sys, r, zcols, &p, &smem_bwd_plain);
+            ++nb;
         }
-        p.ws_D_elems = o;
-        for (int k = 0; k < nb; ++k) {
-            const FnRec& r = recs[k];
-            const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
-            recs[k].ws_Bf = o;
-            o += align64(2LL * r.n[2] * Y * X);
-            recs[k].ws_Bb = o;
-            o += align64(2LL * r.np[2] * Y * X);
-            recs[k].ws_G = o;
-            o += align64(8LL * r.np[0] * r.np[1] * r.np[2]);
-            recs[k].ws_Gf = o;
-            o += align64((4LL * r.n[0] * r.n[1] + static_cast<int64_t>(sys->esize) - 1) / static_cast<int64_t>(sys->esize));
-            const LocregHost& Lh = sys->L[r.atom];
-            const LocregHost& Ph = sys->Lp[r.atom];
-            p.max_nz = std::max(p.max_nz, r.n[2]);
-            p.max_nzp = std::max(p.max_nzp, r.np[2]);
-            p.max_cols = std::max<int>(p.max_cols, (2 * r.n[1] + 29) * (2 * r.n[0] + 29));
-            p.max_rowsP = std::max(p.max_rowsP, r.np[1] * r.np[2]);
-            p.max_ptsP = std::max<int64_t>(p.max_ptsP, static_cast<int64_t>(r.np[0]) * r.np[1] * r.np[2]);
-            p.max_colsP = std::max(p.max_colsP, r.np[0] * r.np[1]);
-            p.max_colsL = std::max(p.max_colsL, r.n[0] * r.n[1]);
-            p.max_rowsL = std::max(p.max_rowsL, r.n[1] * r.n[2]);
-            p.max_segL = std::max<int>(p.max_segL, static_cast<int>((Lh.c.keys.size() + Lh.f.keys.size()) / 3));
-            p.max_segP = std::max<int>(p.max_segP, static_cast<int>((Ph.c.keys.size() + Ph.f.keys.size()) / 3));
-            size_t a1, a2, a3, a4;
-            pass_smem(r, sys->esize, zcols, &a1, &a2, &a3, &a4);
-            p.smem_fwd = std::max(p.smem_fwd, a1);
-            p.smem_z = std::max(p.smem_z, a2);
-            p.smem_kin = std::max(p.smem_kin, static_cast<size_t>(2 * r.n[2] * 128) * (p.prec == 0 ? 8 : 4));
-            p.smem_bwd = std::max(p.smem_bwd, a3);
-            smem_bwd_plain = std::max(smem_bwd_plain, a4);
-            if (sys->zsplit) {
-                if (!ztc_fits(r))
-                    return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core kernels");
-                p.smem_ztc = std::max(p.smem_ztc, ztc_smem(r, sys->zsplit));
-                if (sys->xy_tc) {
-                    if (!xytc_fits(r))
-                        return fail(LSW_ERR_UNSUPPORTED, "locreg extents too large for the tensor-core plane kernels");
-                    p.smem_bwd_tc = std::max(p.smem_bwd_tc, bwd_tc_smem(r, sys->zsplit));
-                    p.smem_fwd_tc = std::max(p.smem_fwd_tc, fwd_tc_smem(r, sys->zsplit));
-                }
-            }
-        }
-        // stage the z-arm plane and flags when they fit beside the plane kernel's tiles
-        p.gstage = p.smem_bwd + BWD_STATIC_SMEM <= sys->ctx->max_smem ? 1 : 0;
-        if (!p.gstage) p.smem_bwd = smem_bwd_plain;
+        if (nb == 0 || !noalloc_finish(sys, &p, smem_bwd_plain))   // excluded by the checks above
+            return fail(LSW_ERR_STATE, "lsw_apply_hamiltonian_noalloc: inconsistent batch plan");
+        p.nfn = nb;
         p.zsplit = sys->zsplit;
         p.xy_tc = sys->zsplit ? sys->xy_tc : 0;
-        if (p.smem_fwd > sys->ctx->max_smem || p.smem_z > sys->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > sys->ctx->max_smem ||
-            p.smem_ztc > sys->ctx->max_smem || p.smem_kin > sys->ctx->max_smem || p.smem_bwd_tc + BWD_STATIC_SMEM > sys->ctx->max_smem ||
-            p.smem_fwd_tc > sys->ctx->max_smem)
-            return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
-        // records into the head of the scratch (pageable source: reusable on return)
-        CUDA_TRY(cudaMemcpyAsync(scratch, recs, nb * sizeof(FnRec), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(enqueue_noalloc_records(static_cast<const FnRec*>(sys->d_fn.p), f, nb,
+                                         static_cast<int64_t>(sys->esize), static_cast<FnRec*>(scratch), st));
         p.fn = static_cast<const FnRec*>(scratch);
         p.atoms = static_cast<const AtomRec*>(sys->d_atoms.p);
         p.seg = static_cast<const Seg*>(sys->d_seg.p);

@@ -191,6 +191,9 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(32) << 20;   // 32 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 constexpr int NOALLOC_MAX_BATCH = 64;      // functions per batch (records kept in the scratch)
 cudaError_t noalloc_scratch(int device, void** ptr);
+// Batch records of the allocation-free path, built on the device from the system's
+// resident records all[f0 .. f0 + nb) with the batch's own workspace offsets.
+cudaError_t enqueue_noalloc_records(const FnRec* all, int64_t f0, int nb, int64_t esize, FnRec* out, cudaStream_t s);
 
 // Support-function reuse across geometries (lsw_reformat).
 struct ReformatLaunch {

@@ -2217,6 +2217,42 @@ cudaError_t noalloc_scratch(int device, void** ptr) {
     return cudaSuccess;
 }
 
+// Records of one batch of the allocation-free path, built on the device: boxes and
+// offsets are copied from the system's resident per-function records (all[f0 ..
+// f0 + nb)), and the workspace offsets are laid out again, function after function, in
+// the order and sizes the host validated (D boxes first, then Bf, Bb, G and the z-arm
+// flags of each function; every region a multiple of 64 elements).  One thread: nb is
+// at most NOALLOC_MAX_BATCH.
+__global__ void k_noalloc_records(const FnRec* __restrict__ all, int64_t f0, int nb, int64_t esize,
+                                  FnRec* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    auto al = [](int64_t x) { return (x + ALIGN_ELEMS - 1) / ALIGN_ELEMS * ALIGN_ELEMS; };
+    int64_t o = 0;
+    for (int k = 0; k < nb; ++k) {
+        FnRec r = all[f0 + k];
+        r.ws_D = o;
+        o += al(8LL * r.n[0] * r.n[1] * r.n[2]);
+        out[k] = r;
+    }
+    for (int k = 0; k < nb; ++k) {
+        FnRec& r = out[k];
+        const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+        r.ws_Bf = o;
+        o += al(2LL * r.n[2] * Y * X);
+        r.ws_Bb = o;
+        o += al(2LL * r.np[2] * Y * X);
+        r.ws_G = o;
+        o += al(8LL * r.np[0] * r.np[1] * r.np[2]);
+        r.ws_Gf = o;
+        o += al((4LL * r.n[0] * r.n[1] + esize - 1) / esize);
+    }
+}
+
+cudaError_t enqueue_noalloc_records(const FnRec* all, int64_t f0, int nb, int64_t esize, FnRec* out, cudaStream_t s) {
+    k_noalloc_records<<<1, 32, 0, s>>>(all, f0, nb, esize, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- host entry points
 
 cudaError_t upload_filters(const FilterSet& fs, int device) {

@@ -171,3 +171,31 @@ def test_hamiltonian_symmetric_with_full_reach_margin():
             hba = Mx.hamiltonian_entry(geo, b, a, phi[b], hphi[a])
             scale = math.sqrt(np.dot(hphi[a], hphi[a]) * np.dot(hphi[b], hphi[b]))
             assert abs(hab - hba) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("seed,n,r_loc,r_fine", [(5, 6, 1.2, 0.6), (11, 5, 0.9, 0.5)])
+def test_hphi_abs_bound_equals_dense_absolute_matrices(seed, n, r_loc, r_fine):
+    # The absolute-term bound of every H phi element (the per-element scale of the GPU
+    # parity tests) against explicit dense matrices built entry by entry with absolute
+    # taps: |P_L'| (|K|/(2h^2) + |MS|^T |V| |MS|) |P_L| |phi|, kinetic and potential
+    # parts kept apart so that neither cancels the other.
+    import dataclasses
+    wl = tiny_workload(n=n, seed=seed, n_atoms=2, r_loc=r_loc, r_fine=r_fine)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    Fa = dataclasses.replace(FT, h=np.abs(FT.h), g=np.abs(FT.g), magic=np.abs(FT.magic),
+                             kin={k: np.abs(v) for k, v in FT.kin.items()})
+    F0 = dataclasses.replace(Fa, kin={k: np.zeros_like(v) for k, v in FT.kin.items()})
+    pot = B.full_hamiltonian(n, wl.h, np.abs(V), wl.V_lo, F0)
+    K = B.kinetic_matrix(n, Fa)
+    Id = np.eye(2 * n)
+    kin = (np.kron(np.kron(K, Id), Id) + np.kron(np.kron(Id, K), Id) + np.kron(np.kron(Id, Id), K)) / (2 * wl.h ** 2)
+    for f in range(2):
+        a = geo.sf_atom[f]
+        phi = I.phi_values(wl, f, a, geo.L[a].coarse.g, geo.L[a].fine.g)
+        bound = Hm.hphi_abs_bound(geo, f, phi, V, wl.V_lo)
+        ref = B.apply_dense(pot + kin, wl.N, geo.L[a], geo.Lp[a], np.abs(phi))
+        assert np.max(np.abs(bound - ref)) <= 1e-13 * np.max(ref)
+        hp, _, _ = Hm.apply_hamiltonian(geo, f, phi, V, wl.V_lo)
+        assert np.all(np.abs(hp) <= bound * (1 + 1e-12))
+        assert np.max(np.abs(hp) / np.maximum(bound, 1e-300)) > 0.3     # not a loose bound
