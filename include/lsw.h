@@ -199,11 +199,42 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi_dev, vo
                                          double* e_kin_dev, double* e_pot_dev);
 
 /* Sparse matrices on the pattern (Sec. II.A): H_dev[k] = <phi_a|H phi_b> (raw, not
- * symmetrized) and S_dev[k] = <phi_a|phi_b> for the k-th pattern entry (a, b); FP64
- * accumulation in both precisions.  Asynchronous.
+ * symmetrized) and S_dev[k] = <phi_a|phi_b> for the k-th pattern entry (a, b).  Computed
+ * in the transposed layout of App. D: per tile of T^3 coarse points (option "tile"),
+ * panels hold the coefficients of every function present there (phi on L, H phi on L'),
+ * and each tile's contributions are a small dense product in the system's precision,
+ * added to the FP64 values (FP64 accumulation across tiles in every precision).  The
+ * panels live in a library buffer of one slab of tiles (option "slab_mb").
+ * Asynchronous.
  * Errors: LSW_ERR_ARG (NULL), LSW_ERR_CUDA. */
 lsw_status lsw_build_matrices(lsw_system sys, const void* phi_dev, const void* hphi_dev,
                               double* H_dev, double* S_dev);
+
+/* Sparse combination of support functions (Sec. "Orthogonalization" and Sec. "Gradient
+ * and preconditioning", Eq. gradient: sums over overlapping functions, then localized
+ * onto each function's region):
+ *     (M Phi)_a = L(a) sum_b M_ab phi_b
+ * for M given as FP64 values on the pattern (lsw_pattern: M_dev[k] belongs to the k-th
+ * entry (a, b); entries outside the pattern count as 0; M need not be symmetric).  Each
+ * phi_b contributes its coefficients at its own members; the sum is read back at the
+ * members of L(a) (scaling and wavelet parts).  phi_in_dev and phi_out_dev: compressed
+ * support functions on L (layout off_L, system precision); they must not overlap.  Only
+ * the members of each function are written (the alignment gaps keep their contents).
+ * The work runs in the transposed layout of the H/S build (App. D): per tile of the
+ * grid, the functions present there are combined as a small dense product (FP32 with
+ * FP32 sums for reduced-precision systems, M rounded to FP32; FP64 otherwise).
+ * Asynchronous.  Errors: LSW_ERR_ARG (NULL, overlapping buffers), LSW_ERR_STATE
+ * (host-only context), LSW_ERR_CUDA. */
+lsw_status lsw_combine(lsw_system sys, const double* M_dev, const void* phi_in_dev, void* phi_out_dev);
+
+/* Loewdin re-orthonormalization with the first-order Taylor form of S^-1/2 (Sec.
+ * "Orthogonalization": the functions stay close to orthonormal, so S^-1/2 is replaced by
+ * (3 I - S) / 2):  phi'_a = L(a) sum_b (3 delta_ab - S_ab) / 2 phi_b, with S_dev the
+ * overlap values on the pattern (as lsw_build_matrices writes them).  Same layouts and
+ * rules as lsw_combine; the coefficients are formed on the device in a library buffer
+ * (allocated at the first call, counted by lsw_workspace_bytes).  Asynchronous.
+ * Errors: as lsw_combine. */
+lsw_status lsw_lowdin_taylor(lsw_system sys, const double* S_dev, const void* phi_in_dev, void* phi_out_dev);
 
 /* Electronic density (Sec. II.A, Eq. density; App. D forms it like the scalar
  * products): rho_j = sum_ab K_ab u_a(j) u_b(j) at every fine point x_j = j h/2 of the
@@ -314,6 +345,8 @@ lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev);
 
 /* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
  * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8),
+ * "slab_mb" (H/S and combination: panel budget of one slab of tiles, MiB; the panels of
+ * consecutive tile-z layers are built and consumed slab by slab, default 8192),
  * "zsplit" (LSW_FP32_BF16X systems only: 2 or 3 bfloat16 parts per FP32 operand of the
  * tensor-core z stage), "xy_tc" (LSW_FP32_BF16X systems only: 1 runs the x and y passes
  * of the plane kernels as split-bfloat16 tensor-core products as well; 0, the default,

@@ -1,6 +1,6 @@
 """In-tree build of the sm_103a library ``liblsw.so`` (nvcc + the host compiler).
 
-Three translation units compiled in parallel, one -gencode (sm_103a), static CUDA
+Four translation units compiled in parallel, one -gencode (sm_103a), static CUDA
 runtime, no cmake.  Host code is compiled without floating-point contraction so that
 the locreg membership tests and the filter derivation round exactly as specified.
 """
@@ -29,13 +29,13 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("lsw_kernels.cu", "lsw_host.cpp", "lsw_filters.cpp")]
+    return [os.path.join(CSRC, f) for f in ("lsw_kernels.cu", "lsw_panels.cu", "lsw_host.cpp", "lsw_filters.cpp")]
 
 
 def build(verbose: bool = False, force: bool = False) -> str:
     """Compile (if stale) and return the path of liblsw.so."""
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, "lsw_internal.h"), os.path.join(ROOT, "include", "lsw.h"),
+    deps = srcs + [os.path.join(CSRC, "lsw_internal.h"), os.path.join(CSRC, "lsw_device.h"), os.path.join(ROOT, "include", "lsw.h"),
                    os.path.abspath(__file__)]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

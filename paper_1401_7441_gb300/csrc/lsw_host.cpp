@@ -163,6 +163,8 @@ struct Batch {
     HphiLaunch proto;
 };
 
+constexpr int64_t PANEL_SLAB_MB = 8192;   // default panel budget of one H/S slab (option "slab_mb")
+
 struct lsw_system_s {
     lsw_ctx ctx = nullptr;
     cudaStream_t stream = nullptr;   // where this system's work is enqueued (ctx's by default)
@@ -185,7 +187,11 @@ struct lsw_system_s {
     std::vector<int32_t> col;
     // device state
     DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
-    DeviceBuf d_tile_org, d_tile_fine, d_listA, d_listB, d_work, d_ws, d_status, d_escratch;
+    DeviceBuf d_tile_fine, d_listA, d_listB, d_ws, d_status, d_escratch;
+    // H/S in the transposed layout: used tiles, per-atom tile tables, product items, the
+    // atoms of each slab and the panel buffers of one slab (reused slab after slab)
+    DeviceBuf d_ptiles, d_patoms, d_ttab, d_items, d_citems, d_slab_atoms, d_PA, d_PQ, d_mcoef;
+    std::vector<PanelSlab> slabs;
     DeviceBuf d_shift, d_fn_all;   // reformat: per-atom shifts, records of every function
     // density: real-space store, block records, tile lists (built for one grid)
     DeviceBuf d_U, d_dfn, d_tptr, d_tfn;
@@ -197,8 +203,8 @@ struct lsw_system_s {
     int64_t ws_elems = 0;
     int batch_size = 0;
     int tile = 4;
+    int64_t slab_mb = PANEL_SLAB_MB;
     int use_graph = 1;
-    int nwork = 0;
     // potential
     const void* V = nullptr;
     int64_t vlo[3] = {0, 0, 0}, vn[3] = {0, 0, 0};
@@ -547,6 +553,15 @@ lsw_status build_plans(lsw_system_s* s) {
     return LSW_OK;
 }
 
+// Plan of the H/S build in the transposed layout (App. D): tiles of T^3 coarse points;
+// per tile the functions whose L (A list) and L' (B list) touch it, atom by atom in
+// atom order (so an atom's functions sit in consecutive slots); the panel row length
+// T^3 + 7 (fine points of the tile), rounded up to 4; per atom, the tile boxes of L and
+// L' with the used-tile index and slot of each tile; product items of at most 64 A rows
+// by 128 columns of [A; B]; slabs of consecutive tile-z layers whose panels fit
+// the slab budget (option "slab_mb"; one layer at least), with the atoms whose L' meets
+// each slab.
+
 lsw_status build_hs_plan(lsw_system_s* s) {
     const int T = s->tile;
     const int32_t* N = s->N;
@@ -572,37 +587,45 @@ lsw_status build_hs_plan(lsw_system_s* s) {
     });
     std::vector<int64_t> first(na + 1, 0);
     for (int a = 0; a < na; ++a) first[a + 1] = first[a] + s->nsf[a];
-    // tile -> functions (through their atoms), counting sort
-    auto invert = [&](const std::vector<std::vector<int64_t>>& t, std::vector<int64_t>* ptr,
-                      std::vector<int32_t>* fl) {
+    // tile -> functions (atom by atom), and each (atom, tile)'s first slot
+    auto invert = [&](const std::vector<std::vector<int64_t>>& t, std::vector<int64_t>* ptr, std::vector<int32_t>* fl,
+                      std::vector<std::vector<int32_t>>* slot) {
         ptr->assign(ntiles + 1, 0);
         for (int a = 0; a < na; ++a)
             for (int64_t x : t[a]) (*ptr)[x + 1] += s->nsf[a];
         for (int64_t i = 0; i < ntiles; ++i) (*ptr)[i + 1] += (*ptr)[i];
         fl->resize((*ptr)[ntiles]);
+        slot->assign(na, {});
         std::vector<int64_t> fill(ptr->begin(), ptr->end() - 1);
-        for (int a = 0; a < na; ++a)
-            for (int64_t x : t[a])
+        for (int a = 0; a < na; ++a) {
+            (*slot)[a].resize(t[a].size());
+            for (size_t i = 0; i < t[a].size(); ++i) {
+                const int64_t x = t[a][i];
+                (*slot)[a][i] = static_cast<int32_t>(fill[x] - (*ptr)[x]);
                 for (int64_t f = first[a]; f < first[a + 1]; ++f) (*fl)[fill[x]++] = static_cast<int32_t>(f);
+            }
+        }
     };
     std::vector<int64_t> pA, pB;
     std::vector<int32_t> fA, fB;
-    invert(tA, &pA, &fA);
-    invert(tB, &pB, &fB);
-    std::vector<int32_t> org, fine;
-    std::vector<HSWork> work;
-    int32_t used = 0;
-    const int BLK = 64;   // functions per side of a work item (k_hs)
+    std::vector<std::vector<int32_t>> slotA, slotB;
+    invert(tA, &pA, &fA, &slotA);
+    invert(tB, &pB, &fB, &slotB);
+    // used tiles (L of some function touches them; then so does its L'), in tile order
+    std::vector<int64_t> used_of(ntiles, -1);
+    std::vector<PanelTile> tiles;
+    std::vector<int32_t> fine;
     for (int64_t t = 0; t < ntiles; ++t) {
-        int64_t na_t = pA[t + 1] - pA[t], nb_t = pB[t + 1] - pB[t];
-        if (na_t == 0 || nb_t == 0) continue;
-        int tx = static_cast<int>(t % nt[0]);
-        int ty = static_cast<int>((t / nt[0]) % nt[1]);
-        int tz = static_cast<int>(t / (static_cast<int64_t>(nt[0]) * nt[1]));
-        org.push_back(tx * T);
-        org.push_back(ty * T);
-        org.push_back(tz * T);
-        org.push_back(static_cast<int32_t>(fine.size()));
+        if (pA[t + 1] == pA[t]) continue;
+        PanelTile pt;
+        std::memset(&pt, 0, sizeof(pt));
+        const int tx = static_cast<int>(t % nt[0]);
+        const int ty = static_cast<int>((t / nt[0]) % nt[1]);
+        const int tz = static_cast<int>(t / (static_cast<int64_t>(nt[0]) * nt[1]));
+        pt.org[0] = tx * T;
+        pt.org[1] = ty * T;
+        pt.org[2] = tz * T;
+        pt.fine0 = static_cast<int32_t>(fine.size());
         for (int z = 0; z < T; ++z)
             for (int y = 0; y < T; ++y)
                 for (int x = 0; x < T; ++x) {
@@ -611,30 +634,163 @@ lsw_status build_hs_plan(lsw_system_s* s) {
                     int64_t g = gx + static_cast<int64_t>(N[0]) * (gy + static_cast<int64_t>(N[1]) * gz);
                     if (s->fine_mask[g]) fine.push_back(x | (y << 8) | (z << 16));
                 }
-        for (int64_t a0 = pA[t]; a0 < pA[t + 1]; a0 += BLK)
-            for (int64_t b0 = pB[t]; b0 < pB[t + 1]; b0 += BLK) {
-                HSWork w;
-                w.tile = used;
-                w.a0 = static_cast<int32_t>(a0);
-                w.na = static_cast<int32_t>(std::min<int64_t>(BLK, pA[t + 1] - a0));
-                w.b0 = static_cast<int32_t>(b0);
-                w.nb = static_cast<int32_t>(std::min<int64_t>(BLK, pB[t + 1] - b0));
-                w.pad = 0;
-                work.push_back(w);
-            }
-        ++used;
+        pt.nfine = static_cast<int32_t>(fine.size()) - pt.fine0;
+        pt.nA = static_cast<int32_t>(pA[t + 1] - pA[t]);
+        pt.nB = static_cast<int32_t>(pB[t + 1] - pB[t]);
+        pt.kp = (T * T * T + 7 * pt.nfine + 3) / 4 * 4;
+        pt.listA = pA[t];
+        pt.listB = pB[t];
+        used_of[t] = static_cast<int64_t>(tiles.size());
+        tiles.push_back(pt);
     }
-    org.push_back(0);
-    org.push_back(0);
-    org.push_back(0);
-    org.push_back(static_cast<int32_t>(fine.size()));  // sentinel: end of the last fine list
+    if (tiles.size() > static_cast<size_t>(INT32_MAX)) return fail(LSW_ERR_UNSUPPORTED, "too many H/S tiles");
+    // per-atom tile tables over the tile boxes of L and L'
+    std::vector<PanelAtom> patoms(na);
+    std::vector<int64_t> tab_off(na + 1, 0);
+    for (int a = 0; a < na; ++a) {
+        PanelAtom& q = patoms[a];
+        std::memset(&q, 0, sizeof(q));
+        int64_t nA = 1, nB = 1;
+        for (int d = 0; d < 3; ++d) {
+            q.tloA[d] = s->L[a].lo[d] / T;
+            q.tnA[d] = (s->L[a].lo[d] + s->L[a].n[d] - 1) / T - q.tloA[d] + 1;
+            q.tloB[d] = s->Lp[a].lo[d] / T;
+            q.tnB[d] = (s->Lp[a].lo[d] + s->Lp[a].n[d] - 1) / T - q.tloB[d] + 1;
+            nA *= q.tnA[d];
+            nB *= q.tnB[d];
+        }
+        if (tA[a].empty()) nA = 0, q.tnA[0] = q.tnA[1] = q.tnA[2] = 0;   // no table: nothing to pack
+        if (tB[a].empty()) nB = 0, q.tnB[0] = q.tnB[1] = q.tnB[2] = 0;
+        q.f0 = static_cast<int32_t>(first[a]);
+        q.nsf = s->nsf[a];
+        tab_off[a + 1] = tab_off[a] + nA + nB;
+    }
+    std::vector<int2> ttab(tab_off[na], make_int2(-1, 0));
+    parallel_for(na, [&](int a) {
+        PanelAtom& q = patoms[a];
+        q.tabA = tab_off[a];
+        q.tabB = tab_off[a] + static_cast<int64_t>(q.tnA[0]) * q.tnA[1] * q.tnA[2];
+        auto put = [&](const std::vector<int64_t>& tl, const std::vector<int32_t>& sl, const int32_t* lo,
+                       const int32_t* n, int64_t base) {
+            for (size_t i = 0; i < tl.size(); ++i) {
+                const int64_t t = tl[i];
+                const int tx = static_cast<int>(t % nt[0]) - lo[0];
+                const int ty = static_cast<int>((t / nt[0]) % nt[1]) - lo[1];
+                const int tz = static_cast<int>(t / (static_cast<int64_t>(nt[0]) * nt[1])) - lo[2];
+                ttab[base + tx + static_cast<int64_t>(n[0]) * (ty + static_cast<int64_t>(n[1]) * tz)] =
+                    make_int2(static_cast<int32_t>(used_of[t]), sl[i]);
+            }
+        };
+        put(tA[a], slotA[a], q.tloA, q.tnA, q.tabA);
+        put(tB[a], slotB[a], q.tloB, q.tnB, q.tabB);
+    });
+    // slabs of tile-z layers and their panel offsets; product items
+    s->slabs.clear();
+    std::vector<PanelItem> items, citems;
+    const size_t es = s->esize;
+    size_t maxA = 0, maxQ = 0;
+    {
+        size_t u = 0;
+        while (u < tiles.size()) {
+            PanelSlab sl;
+            std::memset(&sl, 0, sizeof(sl));
+            sl.tz0 = tiles[u].org[2] / T;
+            sl.u0 = static_cast<int64_t>(u);
+            sl.i0 = static_cast<int64_t>(items.size());
+            sl.ci0 = static_cast<int64_t>(citems.size());
+            int64_t eA = 0, eQ = 0;
+            int tz = sl.tz0;
+            while (u < tiles.size()) {
+                // take the whole next layer
+                size_t v = u;
+                int64_t lA = 0, lQ = 0;
+                while (v < tiles.size() && tiles[v].org[2] / T == tz) {
+                    lA += static_cast<int64_t>(tiles[v].nA) * tiles[v].kp;
+                    lQ += static_cast<int64_t>(tiles[v].nB) * tiles[v].kp;
+                    ++v;
+                }
+                if (u > static_cast<size_t>(sl.u0) &&
+                    static_cast<size_t>(eA + lA + eQ + lQ) * es > static_cast<size_t>(s->slab_mb) << 20)
+                    break;
+                for (size_t w = u; w < v; ++w) {
+                    PanelTile& pt = tiles[w];
+                    pt.pA = eA;
+                    pt.pQ = eQ;
+                    eA += static_cast<int64_t>(pt.nA) * pt.kp;
+                    eQ += static_cast<int64_t>(pt.nB) * pt.kp;
+                    const int ncol = pt.nA + pt.nB;
+                    for (int a0 = 0; a0 < pt.nA; a0 += 64)
+                        for (int c0 = 0; c0 < ncol; c0 += 128) {
+                            PanelItem it;
+                            it.tile = static_cast<int32_t>(w);
+                            it.a0 = a0;
+                            it.na = std::min(64, pt.nA - a0);
+                            it.c0 = c0;
+                            it.nc = std::min(128, ncol - c0);
+                            it.pad = 0;
+                            items.push_back(it);
+                        }
+                    for (int a0 = 0; a0 < pt.nA; a0 += 64)
+                        for (int c0 = 0; c0 < pt.kp; c0 += 128) {
+                            PanelItem it;
+                            it.tile = static_cast<int32_t>(w);
+                            it.a0 = a0;
+                            it.na = std::min(64, pt.nA - a0);
+                            it.c0 = c0;
+                            it.nc = std::min(128, pt.kp - c0);
+                            it.pad = 0;
+                            citems.push_back(it);
+                        }
+                }
+                u = v;
+                if (u < tiles.size()) tz = tiles[u].org[2] / T;
+                else break;
+            }
+            sl.tz1 = u < tiles.size() ? tiles[u].org[2] / T : nt[2];
+            sl.u1 = static_cast<int64_t>(u);
+            sl.i1 = static_cast<int64_t>(items.size());
+            sl.ci1 = static_cast<int64_t>(citems.size());
+            sl.elemsA = eA;
+            sl.elemsQ = eQ;
+            maxA = std::max(maxA, static_cast<size_t>(eA));
+            maxQ = std::max(maxQ, static_cast<size_t>(eQ));
+            s->slabs.push_back(sl);
+        }
+    }
+    // atoms of each slab (their L' tile box meets the slab's layers) and the pack kernel's
+    // shared memory (the largest region tables of those atoms; 0 when they do not fit)
+    std::vector<int32_t> slab_atoms;
+    const size_t smem_cap = std::min<size_t>(s->ctx->max_smem, 100 * 1024);
+    for (PanelSlab& sl : s->slabs) {
+        sl.s0 = static_cast<int64_t>(slab_atoms.size());
+        size_t need = 0;
+        for (int a = 0; a < na; ++a) {
+            if (tB[a].empty() || s->nsf[a] == 0) continue;   // no functions: no panel rows
+            const PanelAtom& q = patoms[a];
+            if (q.tloB[2] + q.tnB[2] <= sl.tz0 || q.tloB[2] >= sl.tz1) continue;
+            slab_atoms.push_back(a);
+            for (int side = 0; side < 2; ++side) {
+                const LocregHost& R = side ? s->Lp[a] : s->L[a];
+                const size_t rows = static_cast<size_t>(R.n[1]) * R.n[2];
+                const size_t segs = (R.c.keys.size() + R.f.keys.size()) / 3;
+                need = std::max(need, (8 * (rows + 1) + 15) / 16 * 16 + sizeof(Seg) * segs);
+            }
+        }
+        sl.s1 = static_cast<int64_t>(slab_atoms.size());
+        sl.smem_pack = need <= smem_cap ? need : 0;
+    }
     cudaStream_t st = s->stream;
-    CUDA_TRY(s->d_tile_org.upload(org, st));
+    CUDA_TRY(s->d_ptiles.upload(tiles, st));
+    CUDA_TRY(s->d_patoms.upload(patoms, st));
+    CUDA_TRY(s->d_ttab.upload(ttab, st));
+    CUDA_TRY(s->d_items.upload(items, st));
+    CUDA_TRY(s->d_citems.upload(citems, st));
+    CUDA_TRY(s->d_slab_atoms.upload(slab_atoms, st));
     CUDA_TRY(s->d_tile_fine.upload(fine, st));
     CUDA_TRY(s->d_listA.upload(fA, st));
     CUDA_TRY(s->d_listB.upload(fB, st));
-    CUDA_TRY(s->d_work.upload(work, st));
-    s->nwork = static_cast<int>(work.size());
+    CUDA_TRY(s->d_PA.alloc(std::max<size_t>(maxA, 4) * es));
+    CUDA_TRY(s->d_PQ.alloc(std::max<size_t>(maxQ, 4) * es));
     return LSW_OK;
 }
 
@@ -730,48 +886,99 @@ lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hph
     return LSW_OK;
 }
 
+PackLaunch pack_launch(lsw_system_s* s, Tracer* tr, const PanelSlab& sl, const void* phi, const void* hphi, void* out) {
+    PackLaunch k;
+    std::memset(&k, 0, sizeof(k));
+    k.tr = tr;
+    k.prec = s->prec;
+    k.tiles = static_cast<const PanelTile*>(s->d_ptiles.p);
+    k.patoms = static_cast<const PanelAtom*>(s->d_patoms.p);
+    k.ttab = static_cast<const int2*>(s->d_ttab.p);
+    k.slab_atoms = static_cast<const int32_t*>(s->d_slab_atoms.p) + sl.s0;
+    k.n_slab_atoms = static_cast<int>(sl.s1 - sl.s0);
+    k.tz0 = sl.tz0;
+    k.tz1 = sl.tz1;
+    k.tile = s->tile;
+    k.u0 = sl.u0;
+    k.tile_fine = static_cast<const int32_t*>(s->d_tile_fine.p);
+    k.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
+    k.seg = static_cast<const Seg*>(s->d_seg.p);
+    k.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
+    k.off_L = static_cast<const int64_t*>(s->d_offL.p);
+    k.off_Lp = static_cast<const int64_t*>(s->d_offLp.p);
+    k.phi = phi;
+    k.hphi = hphi;
+    k.PA = s->d_PA.p;
+    k.PQ = s->d_PQ.p;
+    k.smem = sl.smem_pack;
+    k.out = out;
+    k.status = static_cast<int*>(s->d_status.p);
+    k.phi_n = s->off_L.back();
+    k.hphi_n = s->off_Lp.back();
+    k.out_n = s->off_L.back();
+    k.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
+    k.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
+    k.fine_n = static_cast<int64_t>(s->d_tile_fine.bytes / sizeof(int32_t));
+    k.ttab_n = static_cast<int64_t>(s->d_ttab.bytes / sizeof(int2));
+    k.PA_n = static_cast<int64_t>(s->d_PA.bytes / s->esize);
+    k.PQ_n = static_cast<int64_t>(s->d_PQ.bytes / s->esize);
+    k.n_atoms = s->n_atoms;
+    k.n_tiles = static_cast<int>(s->d_ptiles.bytes / sizeof(PanelTile));
+    k.n_sf = static_cast<int>(s->sf_atom.size());
+    return k;
+}
+
+PanelHSLaunch product_launch(lsw_system_s* s, Tracer* tr, const PanelSlab& sl, bool combine) {
+    PanelHSLaunch p;
+    std::memset(&p, 0, sizeof(p));
+    p.tr = tr;
+    p.prec = s->prec;
+    p.tiles = static_cast<const PanelTile*>(s->d_ptiles.p);
+    p.items = static_cast<const PanelItem*>(combine ? s->d_citems.p : s->d_items.p) + (combine ? sl.ci0 : sl.i0);
+    p.nitems = combine ? sl.ci1 - sl.ci0 : sl.i1 - sl.i0;
+    p.listA = static_cast<const int32_t*>(s->d_listA.p);
+    p.listB = static_cast<const int32_t*>(s->d_listB.p);
+    p.row_ptr = static_cast<const int64_t*>(s->d_rowp.p);
+    p.col = static_cast<const int32_t*>(s->d_col.p);
+    p.PA = s->d_PA.p;
+    p.PQ = s->d_PQ.p;
+    p.status = static_cast<int*>(s->d_status.p);
+    p.listA_n = static_cast<int64_t>(s->d_listA.bytes / sizeof(int32_t));
+    p.listB_n = static_cast<int64_t>(s->d_listB.bytes / sizeof(int32_t));
+    p.nnz = static_cast<int64_t>(s->col.size());
+    p.PA_n = static_cast<int64_t>(s->d_PA.bytes / s->esize);
+    p.PQ_n = static_cast<int64_t>(s->d_PQ.bytes / s->esize);
+    p.n_tiles = static_cast<int64_t>(s->d_ptiles.bytes / sizeof(PanelTile));
+    p.n_sf = static_cast<int>(s->sf_atom.size());
+    return p;
+}
+
 lsw_status enqueue_matrices(lsw_system_s* s, Tracer* tr, const void* phi, const void* hphi, double* H, double* S) {
     cudaStream_t st = s->stream;
     const int64_t nnz = static_cast<int64_t>(s->col.size());
     CUDA_TRY(cudaMemsetAsync(H, 0, nnz * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(S, 0, nnz * sizeof(double), st));
-    if (s->nwork == 0) return LSW_OK;
-    HSLaunch p;
-    std::memset(&p, 0, sizeof(p));
-    p.tr = tr;
-    p.prec = s->prec;
-    p.work = static_cast<const HSWork*>(s->d_work.p);
-    p.nwork = s->nwork;
-    p.tile_org = static_cast<const int32_t*>(s->d_tile_org.p);
-    p.tile_fine = static_cast<const int32_t*>(s->d_tile_fine.p);
-    p.listA = static_cast<const int32_t*>(s->d_listA.p);
-    p.listB = static_cast<const int32_t*>(s->d_listB.p);
-    p.sf_atom = static_cast<const int32_t*>(s->d_sfatom.p);
-    p.off_L = static_cast<const int64_t*>(s->d_offL.p);
-    p.off_Lp = static_cast<const int64_t*>(s->d_offLp.p);
-    p.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
-    p.seg = static_cast<const Seg*>(s->d_seg.p);
-    p.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
-    p.row_ptr = static_cast<const int64_t*>(s->d_rowp.p);
-    p.col = static_cast<const int32_t*>(s->d_col.p);
-    p.phi = phi;
-    p.hphi = hphi;
-    p.H = H;
-    p.S = S;
-    p.tile = s->tile;
-    p.status = static_cast<int*>(s->d_status.p);
-    p.phi_n = s->off_L.back();
-    p.hphi_n = s->off_Lp.back();
-    p.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
-    p.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
-    p.fine_n = static_cast<int64_t>(s->d_tile_fine.bytes / sizeof(int32_t));
-    p.listA_n = static_cast<int64_t>(s->d_listA.bytes / sizeof(int32_t));
-    p.listB_n = static_cast<int64_t>(s->d_listB.bytes / sizeof(int32_t));
-    p.nnz = nnz;
-    p.org_n = static_cast<int64_t>(s->d_tile_org.bytes / sizeof(int32_t));
-    p.n_atoms = s->n_atoms;
-    p.n_sf = static_cast<int>(s->sf_atom.size());
-    CUDA_TRY(enqueue_hs(p, st));
+    for (const PanelSlab& sl : s->slabs) {
+        CUDA_TRY(enqueue_pack(pack_launch(s, tr, sl, phi, hphi, nullptr), st));
+        PanelHSLaunch p = product_launch(s, tr, sl, false);
+        p.H = H;
+        p.S = S;
+        CUDA_TRY(enqueue_panel_hs(p, st));
+    }
+    return LSW_OK;
+}
+
+// (M Phi)_a = P_L(a) sum_b M_ab phi_b, slab by slab: pack phi on L, combine the panels,
+// unpack onto the members of L.
+lsw_status enqueue_combine(lsw_system_s* s, Tracer* tr, const double* M, const void* phi, void* out) {
+    cudaStream_t st = s->stream;
+    for (const PanelSlab& sl : s->slabs) {
+        CUDA_TRY(enqueue_pack(pack_launch(s, tr, sl, phi, nullptr, nullptr), st));
+        PanelHSLaunch p = product_launch(s, tr, sl, true);
+        p.M = M;
+        CUDA_TRY(enqueue_panel_combine(p, st));
+        CUDA_TRY(enqueue_pack(pack_launch(s, tr, sl, nullptr, nullptr, out), st));
+    }
     return LSW_OK;
 }
 
@@ -1030,6 +1237,7 @@ lsw_status lsw_ctx_create(int device, void* stream, lsw_ctx* out) {
     c->stream = static_cast<cudaStream_t>(stream);  // NULL: the legacy default stream
     CUDA_TRY(upload_filters(c->filters, device));
     CUDA_TRY(configure_kernels(c->max_smem));
+    CUDA_TRY(configure_panel_kernels(c->max_smem));
     *out = c.release();
     return LSW_OK;
 }
@@ -1274,6 +1482,32 @@ lsw_status lsw_build_matrices(lsw_system sys, const void* phi, const void* hphi,
     return run_maybe_graph(sys, &sys->graphs_m, key, [&](Tracer* tr) { return enqueue_matrices(sys, tr, phi, hphi, H, S); });
 }
 
+lsw_status lsw_combine(lsw_system sys, const double* M, const void* phi_in, void* phi_out) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !M || !phi_in || !phi_out) return fail(LSW_ERR_ARG, "lsw_combine: NULL buffer");
+    if (phi_in == phi_out) return fail(LSW_ERR_ARG, "lsw_combine: input and output must not overlap");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    return enqueue_combine(sys, nullptr, M, phi_in, phi_out);
+}
+
+lsw_status lsw_lowdin_taylor(lsw_system sys, const double* S, const void* phi_in, void* phi_out) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !S || !phi_in || !phi_out) return fail(LSW_ERR_ARG, "lsw_lowdin_taylor: NULL buffer");
+    if (phi_in == phi_out) return fail(LSW_ERR_ARG, "lsw_lowdin_taylor: input and output must not overlap");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    const int64_t nnz = static_cast<int64_t>(sys->col.size());
+    if (sys->d_mcoef.bytes < static_cast<size_t>(std::max<int64_t>(nnz, 1)) * sizeof(double)) {
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        CUDA_TRY(sys->d_mcoef.alloc(static_cast<size_t>(std::max<int64_t>(nnz, 1)) * sizeof(double)));
+    }
+    double* T = static_cast<double*>(sys->d_mcoef.p);
+    CUDA_TRY(enqueue_lowdin_coeffs(static_cast<const int64_t*>(sys->d_rowp.p), static_cast<const int32_t*>(sys->d_col.p),
+                                   S, T, static_cast<int>(sys->sf_atom.size()), sys->stream));
+    return enqueue_combine(sys, nullptr, T, phi_in, phi_out);
+}
+
 lsw_status lsw_build_density(lsw_system sys, const void* phi, const double* K, double* rho, const int64_t fine_lo[3],
                              const int64_t fine_dims[3]) {
     g_err.clear();
@@ -1475,8 +1709,10 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
     g_err.clear();
     if (!sys || !bytes) return fail(LSW_ERR_ARG, "lsw_workspace_bytes: NULL argument");
     const DeviceBuf* bufs[] = {&sys->d_atoms, &sys->d_seg, &sys->d_rowptr, &sys->d_fn, &sys->d_offL, &sys->d_offLp,
-                               &sys->d_sfatom, &sys->d_rowp, &sys->d_col, &sys->d_tile_org, &sys->d_tile_fine,
-                               &sys->d_listA, &sys->d_listB, &sys->d_work, &sys->d_ws, &sys->d_status,
+                               &sys->d_sfatom, &sys->d_rowp, &sys->d_col, &sys->d_tile_fine,
+                               &sys->d_listA, &sys->d_listB, &sys->d_ptiles, &sys->d_patoms, &sys->d_ttab,
+                               &sys->d_items, &sys->d_citems, &sys->d_slab_atoms, &sys->d_PA, &sys->d_PQ, &sys->d_mcoef,
+                               &sys->d_ws, &sys->d_status,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
                                &sys->d_ep, &sys->d_shift, &sys->d_fn_all, &sys->d_U, &sys->d_dfn,
                                &sys->d_tptr, &sys->d_tfn};
@@ -1639,6 +1875,13 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
             return fail(e, "%s", msg.c_str());
         }
         return LSW_OK;
+    }
+    if (std::strcmp(name, "slab_mb") == 0) {
+        if (value < 1 || value > (int64_t(1) << 22)) return fail(LSW_ERR_ARG, "lsw_set_option: slab_mb %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        sys->slab_mb = value;
+        return build_hs_plan(sys);
     }
     if (std::strcmp(name, "tile") == 0) {
         if (value < 2 || value > 8) return fail(LSW_ERR_ARG, "lsw_set_option: tile %lld", static_cast<long long>(value));

@@ -74,14 +74,48 @@ struct FnRec {
                                          // [4][n_x n_y]: 1 where the D column pair is nonzero)
 };
 
-// One H/S work item: tile `tile`, functions listA[a0 .. a0+na) x listB[b0 .. b0+nb).
-struct HSWork {
-    int32_t tile, a0, na, b0, nb, pad;
+// The "transposed" layout of the scalar products (App. D) on one GPU: the grid is cut
+// into tiles of T^3 coarse points; every function whose region touches a tile gets a
+// panel row there holding its coefficients on the tile's points (T^3 scaling values,
+// then the 7 wavelet values of each of the tile's fine points, zero where the function
+// has no member, padded to a multiple of 4).  Panels of phi on L (the "A" side) and of
+// H phi on L' (the "Q" side) turn S_ab and H_ab into small dense products per tile.
+struct PanelTile {
+    int32_t org[3];              // tile origin (coarse grid)
+    int32_t fine0, nfine;        // the tile's fine points: tile_fine[fine0 .. fine0 + nfine)
+    int32_t nA, nB;              // functions whose L (A) / L' (Q) touch the tile
+    int32_t kp;                  // panel row length
+    int64_t listA, listB;        // first entry of the tile's functions in listA / listB
+    int64_t pA, pQ;              // element offsets of the tile's panels in its slab's buffers
+};
+// Per atom: its tile boxes (tiles its L and L' touch) and, per tile of each box, the
+// used-tile index and the slot of the atom's first function in that tile's list
+// (int2 {tile, slot}, tile = -1 where the region does not touch the tile).
+struct PanelAtom {
+    int32_t tloA[3], tnA[3];     // tile box of L
+    int32_t tloB[3], tnB[3];     // tile box of L'
+    int64_t tabA, tabB;          // first entry of the boxes' tables in the tile-table array
+    int32_t f0, nsf;             // the atom's functions f0 .. f0 + nsf - 1
+};
+// One product work item: tile, rows a0 .. a0+na of its A list, columns c0 .. c0+nc of
+// the concatenated column list [A list (S_ab); B list (H_ab)].
+struct PanelItem {
+    int32_t tile, a0, na, c0, nc, pad;
+};
+// One slab of tiles (consecutive tile-z layers) whose panels fit the panel buffers.
+struct PanelSlab {
+    int32_t tz0, tz1;            // tile-z layers tz0 .. tz1 - 1
+    int64_t u0, u1;              // used tiles
+    int64_t i0, i1;              // product items
+    int64_t ci0, ci1;            // combination items (tile, A rows, panel entries)
+    int64_t s0, s1;              // entries of the slab-atom list (atoms whose L' meets the slab)
+    int64_t elemsA, elemsQ;      // panel elements of the slab
+    size_t smem_pack;            // dynamic shared memory of the pack kernel (0: tables read from global)
 };
 
 // Kernel kinds of the per-launch device trace (lsw_profile / lsw_profile_read).
 enum TraceKind : int {
-    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_RESERVED, TK_HS,
+    TK_MEMSET = 0, TK_UNCOMPRESS, TK_FWD_XY, TK_Z, TK_BWD_XY, TK_KINETIC, TK_PACK, TK_HS,
     TK_DENS_U, TK_DENSITY, TK_COUNT
 };
 
@@ -158,32 +192,55 @@ struct DensLaunch {
     int64_t U_n, tfn_n, nnz, rho_n, fn_n, tptr_n, rowp_n;
 };
 
-struct HSLaunch {
+// Pack: panels of one slab (grid: slab atoms x 2 sides).
+struct PackLaunch {
     Tracer* tr;
     int prec;
-    const HSWork* work;
-    int nwork;
-    const int32_t* tile_org;     // [ntiles][4]: x0, y0, z0, first fine point
-    const int32_t* tile_fine;    // fine points: local x | y << 8 | z << 16
-    const int32_t* listA;
-    const int32_t* listB;
-    const int32_t* sf_atom;
-    const int64_t* off_L;
-    const int64_t* off_Lp;
+    const PanelTile* tiles;
+    const PanelAtom* patoms;
+    const int2* ttab;            // per-atom tile tables
+    const int32_t* slab_atoms;   // atoms of this slab
+    int n_slab_atoms;
+    int tz0, tz1;
+    int tile;                    // tile edge T
+    int64_t u0;                  // first used tile of the slab
+    const int32_t* tile_fine;    // fine points of the tiles: local x | y << 8 | z << 16
     const AtomRec* atoms;
     const Seg* seg;
     const int32_t* rowptr;
+    const int64_t* off_L;
+    const int64_t* off_Lp;
+    const void* phi;
+    const void* hphi;            // NULL: pack the A side only
+    void* PA;
+    void* PQ;
+    size_t smem;                 // dynamic shared memory: 0 = region tables read from global
+    void* out;                   // unpack (combination): compressed output on L; NULL: pack
+    int* status;
+    int64_t phi_n, hphi_n, seg_n, rowptr_n, fine_n, ttab_n, PA_n, PQ_n, out_n;
+    int n_atoms, n_tiles, n_sf;
+};
+
+// Product: S_ab and H_ab contributions of one slab's tiles, added to the CSR values
+// (or, for the combination, the output panels of one slab's tiles).
+struct PanelHSLaunch {
+    Tracer* tr;
+    int prec;
+    const PanelTile* tiles;
+    const PanelItem* items;
+    int64_t nitems;
+    const int32_t* listA;
+    const int32_t* listB;
     const int64_t* row_ptr;      // pattern CSR
     const int32_t* col;
-    const void* phi;
-    const void* hphi;
+    const void* PA;
+    const void* PQ;              // combination: the output panels (A layout) in the Q buffer
     double* H;
     double* S;
-    int tile;                    // tile edge (coarse points)
+    const double* M;             // combination: coefficients on the pattern
     int* status;
-    // extents used by the self-checking build (-DLSW_CHECKED)
-    int64_t phi_n, hphi_n, seg_n, rowptr_n, fine_n, listA_n, listB_n, nnz, org_n;
-    int n_atoms, n_sf;
+    int64_t listA_n, listB_n, nnz, PA_n, PQ_n, n_tiles;
+    int n_sf;
 };
 
 // Fixed device scratch of the allocation-free Hamiltonian entry point (lsw_kernels.cu).
@@ -220,7 +277,13 @@ cudaError_t upload_filters(const FilterSet& fs, int device);
 cudaError_t measure_peaks(int n_sm, double* fp32_tflops, double* fp64_tflops, double* copy_gbs);
 cudaError_t configure_kernels(size_t max_smem);
 cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s);
-cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s);
+cudaError_t enqueue_pack(const PackLaunch& a, cudaStream_t s);     // panels of a slab (lsw_panels.cu)
+cudaError_t enqueue_panel_hs(const PanelHSLaunch& a, cudaStream_t s);   // S, H from the panels
+cudaError_t enqueue_panel_combine(const PanelHSLaunch& a, cudaStream_t s);   // M Phi panels
+cudaError_t enqueue_lowdin_coeffs(const int64_t* row_ptr, const int32_t* col, const double* S, double* T, int n_sf,
+                                  cudaStream_t s);
+cudaError_t configure_panel_kernels(size_t max_smem);
+size_t panel_hs_smem(int prec);
 cudaError_t enqueue_dens_batch(const HphiLaunch& a, cudaStream_t s);   // real-space values
 cudaError_t enqueue_density(const DensLaunch& a, cudaStream_t s);      // pair products
 

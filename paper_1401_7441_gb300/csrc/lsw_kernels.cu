@@ -13,9 +13,7 @@
 //   k_bwd_xy      per coarse z plane of L': transposed filters along y then x, plus
 //                 the kinetic arms along x and y, plus G; written straight into the
 //                 compressed H phi on the members of L'; E_kin partials
-//   k_hs          per grid tile (App. D "transposed" layout): panels of phi and
-//                 H phi of the functions touching the tile; S_ab += <phi_a|phi_b>,
-//                 H_ab += <phi_a|H phi_b> over the tile; FP64 accumulation
+// (the sparse S_ab, H_ab build is in lsw_panels.cu)
 //
 // Density rho = sum_ab K_ab phi_a phi_b on the fine grid (Sec. II.A Eq. density):
 //   k_z_dens      the forward half of k_z: real-space values u of every function into
@@ -33,6 +31,7 @@
 #include <mutex>
 
 #include "lsw_internal.h"
+#include "lsw_device.h"
 
 namespace lsw {
 
@@ -64,42 +63,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Checked accesses: plain loads/stores in the normal build; with -DLSW_CHECKED an
-// index outside [0, n) records (kernel, line, block, index, bound) in the status
-// block and the access is skipped (a load returns 0).  Never traps, never returns
-// early, so barriers stay balanced.
-__device__ __noinline__ void lsw_report(int* st, int kid, int line, int64_t idx, int64_t n) {
-    if ((atomicOr(st, ST_BAD_INDEX) & ST_BAD_INDEX) == 0) {
-        st[1] = kid;
-        st[2] = line;
-        st[3] = static_cast<int>(blockIdx.x + 65536u * blockIdx.y);
-        reinterpret_cast<long long*>(st + 4)[0] = idx;
-        reinterpret_cast<long long*>(st + 4)[1] = n;
-    }
-}
-#ifdef LSW_CHECKED
-#define LD(p, i, n) ld_chk(p, static_cast<int64_t>(i), static_cast<int64_t>(n), ST_, KID, __LINE__)
-#define ST(p, i, n, v) st_chk(p, static_cast<int64_t>(i), static_cast<int64_t>(n), v, ST_, KID, __LINE__)
-#else
-#define LD(p, i, n) ((p)[i])
-#define ST(p, i, n, v) ((p)[i] = (v))
-#endif
-template <class T>
-__device__ __forceinline__ T ld_chk(const T* p, int64_t i, int64_t n, int* st, int kid, int line) {
-    if (i < 0 || i >= n) {
-        lsw_report(st, kid, line, i, n);
-        return T{};
-    }
-    return p[i];
-}
-template <class T, class V>
-__device__ __forceinline__ void st_chk(T* p, int64_t i, int64_t n, V v, int* st, int kid, int line) {
-    if (i < 0 || i >= n) {
-        lsw_report(st, kid, line, i, n);
-        return;
-    }
-    p[i] = static_cast<T>(v);
-}
 #define FWD(b, m) Tab<T>::fwd(b, m)
 #ifdef LSW_CHECKED
 #undef FWD
@@ -1661,254 +1624,6 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     }
 }
 
-// ---------------------------------------------------------------- sparse H / S
-
-constexpr int HS_BLK = 64;     // functions per side of one work item
-constexpr int HS_KC = 64;      // panel columns per chunk
-constexpr int HS_LD = HS_KC + 1;
-
-// offset (within its part) of the member at global (gx, gy, gz) of one region part, -1 if
-// the point is not a member
-__device__ __forceinline__ int64_t seg_find(const HSLaunch& a, int64_t seg0, int64_t row0, const int32_t* lo,
-                                            const int32_t* n, int gx, int gy, int gz) {
-    [[maybe_unused]] int* ST_ = a.status;
-    [[maybe_unused]] constexpr int KID = 8;
-    const int x = gx - lo[0], y = gy - lo[1], z = gz - lo[2];
-    if (x < 0 || y < 0 || z < 0 || x >= n[0] || y >= n[1] || z >= n[2]) return -1;
-    const int row = y + n[1] * z;
-    const int s0 = LD(a.rowptr, row0 + row, a.rowptr_n), s1 = LD(a.rowptr, row0 + row + 1, a.rowptr_n);
-    for (int s = s0; s < s1; ++s) {
-        const Seg sg = LD(a.seg, seg0 + s, a.seg_n);
-        if (x >= sg.x0 && x <= sg.x1) return sg.off + (x - sg.x0);
-    }
-    return -1;
-}
-
-// One tile row (x = ox .. ox+T-1 at fixed gy, gz) of a region part: dst[i] = the value
-// of the member at x = ox + i, or 0.  One row lookup, then contiguous copies.
-template <class T>
-__device__ __forceinline__ void row_gather(const HSLaunch& a, int64_t seg0, int64_t row0, const int32_t* lo,
-                                           const int32_t* n, int ox, int gy, int gz, int tile, const T* base,
-                                           int64_t base_room, T* dst, int dst_room) {
-    [[maybe_unused]] int* ST_ = a.status;
-    [[maybe_unused]] constexpr int KID = 9;
-    for (int i = 0; i < tile; ++i) ST(dst, i, dst_room, T(0));
-    const int y = gy - lo[1], z = gz - lo[2];
-    if (y < 0 || z < 0 || y >= n[1] || z >= n[2]) return;
-    const int row = y + n[1] * z;
-    const int s0 = LD(a.rowptr, row0 + row, a.rowptr_n), s1 = LD(a.rowptr, row0 + row + 1, a.rowptr_n);
-    const int xl0 = ox - lo[0];
-    for (int s = s0; s < s1; ++s) {
-        const Seg sg = LD(a.seg, seg0 + s, a.seg_n);
-        const int x0 = max(sg.x0, xl0), x1 = min(sg.x1, xl0 + tile - 1);
-        for (int x = x0; x <= x1; ++x) ST(dst, x - xl0, dst_room, LD(base, sg.off + (x - sg.x0), base_room));
-    }
-}
-
-// Tile-panel H/S (the "transposed" layout of App. D on one GPU): a work item takes one
-// grid tile and up to 64 functions a whose L touches it and 64 functions b whose L'
-// touches it; it gathers their coefficients on the tile's points into shared panels
-// chunk by chunk and accumulates S_ab (phi_a . phi_b) and H_ab (phi_a . H phi_b) for
-// all 64 x 64 pairs, 4 x 4 per thread; pattern pairs are added to the CSR in FP64.
-template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_hs(HSLaunch a) {
-    [[maybe_unused]] int* ST_ = a.status;
-    [[maybe_unused]] constexpr int KID = 7;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [3][BLK][LD] = phi_a panel, phi_b panel, H phi_b panel
-    T* P = reinterpret_cast<T*>(smem_raw);
-    constexpr int PN = 3 * HS_BLK * HS_LD;
-    T* PA = P;
-    T* PB = P + HS_BLK * HS_LD;
-    T* PQ = P + 2 * HS_BLK * HS_LD;
-    const HSWork w = a.work[blockIdx.x];
-    const int* org = a.tile_org;
-    const int64_t o4 = 4LL * w.tile;
-    const int ox = LD(org, o4, a.org_n), oy = LD(org, o4 + 1, a.org_n), oz = LD(org, o4 + 2, a.org_n);
-    const int f0 = LD(org, o4 + 3, a.org_n), f1 = LD(org, o4 + 7, a.org_n);
-    const int TL = a.tile;
-    const int rows_per_chunk = HS_KC / TL;                 // tile rows per coarse chunk
-    const int n_rows = TL * TL;
-    const int n_coarse_chunks = (n_rows + rows_per_chunk - 1) / rows_per_chunk;
-    const int nfine = f1 - f0;
-    const int fpc = HS_KC / 7;
-    const int n_fine_chunks = (nfine + fpc - 1) / fpc;
-    const int tid = threadIdx.x;
-    const int ti = tid >> 4, tj = tid & 15;                // pairs (ti + 16u, tj + 16v)
-    // per-work-item sums in the panel precision (<= T^3 + 7 * fine points terms);
-    // the sums over tiles are FP64 (the atomic adds into the CSR values)
-    T sacc[4][4], hacc[4][4];
-    [[maybe_unused]] float2 sh2[4][4];     // FP32: (S, H) sums of pair (u, v), packed
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) sacc[u][v] = T(0), hacc[u][v] = T(0), sh2[u][v] = make_float2(0.f, 0.f);
-    const T* phi = static_cast<const T*>(a.phi);
-    const T* hphi = static_cast<const T*>(a.hphi);
-    const int nslot = w.na + w.nb;
-    const int UA = (w.na + 15) >> 4, UB = (w.nb + 15) >> 4;   // 16-row groups in use
-    for (int ch = 0; ch < n_coarse_chunks + n_fine_chunks; ++ch) {
-        const bool coarse = ch < n_coarse_chunks;
-        int kcount;
-        if (coarse) {
-            const int r0 = ch * rows_per_chunk;
-            const int nr = min(rows_per_chunk, n_rows - r0);
-            kcount = nr * TL;
-            // task = (slot, tile row)
-            const FastDiv fd_nr(nr), fd_TL(TL);
-            for (int task = tid; task < nslot * nr; task += blockDim.x) {
-                const int slot = fd_nr.div(task), rr = r0 + (task - slot * nr);
-                const int rz = fd_TL.div(rr);
-                const int gy = oy + (rr - rz * TL), gz = oz + rz;
-                const int col0 = (rr - r0) * TL;
-                const bool isA = slot < w.na;
-                const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
-                const AtomRec& at = a.atoms[LD(a.sf_atom, f, a.n_sf)];
-                const int64_t oL = LD(a.off_L, f, a.n_sf + 1);
-                if (isA) {
-                    row_gather<T>(a, at.segLc, at.rowLc, at.lo, at.n, ox, gy, gz, TL, phi + oL, a.phi_n - oL,
-                                  PA + slot * HS_LD + col0, PN - slot * HS_LD - col0);
-                } else {
-                    const int sb = slot - w.na;
-                    const int64_t oP = LD(a.off_Lp, f, a.n_sf + 1);
-                    row_gather<T>(a, at.segLc, at.rowLc, at.lo, at.n, ox, gy, gz, TL, phi + oL, a.phi_n - oL,
-                                  PB + sb * HS_LD + col0, PN - HS_BLK * HS_LD - sb * HS_LD - col0);
-                    row_gather<T>(a, at.segPc, at.rowPc, at.lop, at.np, ox, gy, gz, TL, hphi + oP, a.hphi_n - oP,
-                                  PQ + sb * HS_LD + col0, PN - 2 * HS_BLK * HS_LD - sb * HS_LD - col0);
-                }
-            }
-        } else {
-            const int q0 = (ch - n_coarse_chunks) * fpc;
-            const int npts = min(fpc, nfine - q0);
-            kcount = 7 * npts;
-            const FastDiv fd_np(npts);
-            for (int task = tid; task < nslot * npts; task += blockDim.x) {
-                const int slot = fd_np.div(task), kp = task - slot * npts;
-                const int code = LD(a.tile_fine, f0 + q0 + kp, a.fine_n);
-                const int gx = ox + (code & 255), gy = oy + ((code >> 8) & 255), gz = oz + (code >> 16);
-                const bool isA = slot < w.na;
-                const int f = isA ? LD(a.listA, w.a0 + slot, a.listA_n) : LD(a.listB, w.b0 + slot - w.na, a.listB_n);
-                const AtomRec& at = a.atoms[LD(a.sf_atom, f, a.n_sf)];
-                const int64_t oL = LD(a.off_L, f, a.n_sf + 1);
-                const int dst0 = isA ? slot * HS_LD : HS_BLK * HS_LD + (slot - w.na) * HS_LD;
-                const int64_t v = seg_find(a, at.segLf, at.rowLf, at.lo, at.n, gx, gy, gz);
-#pragma unroll
-                for (int t = 0; t < 7; ++t)
-                    ST(P, dst0 + 7 * kp + t, PN,
-                       v >= 0 ? LD(phi, oL + at.ncL + v + static_cast<int64_t>(t) * at.nfL, a.phi_n) : T(0));
-                if (!isA) {
-                    const int64_t oP = LD(a.off_Lp, f, a.n_sf + 1);
-                    const int q0b = 2 * HS_BLK * HS_LD + (slot - w.na) * HS_LD;
-                    const int64_t hv = seg_find(a, at.segPf, at.rowPf, at.lop, at.np, gx, gy, gz);
-#pragma unroll
-                    for (int t = 0; t < 7; ++t)
-                        ST(P, q0b + 7 * kp + t, PN,
-                           hv >= 0 ? LD(hphi, oP + at.ncP + hv + static_cast<int64_t>(t) * at.nfP, a.hphi_n) : T(0));
-                }
-            }
-        }
-        __syncthreads();
-        // 4 x 4 pairs per thread over this chunk (rows ti + 16u of A, tj + 16v of B);
-        // only the 16-row groups holding functions (u < UA, v < UB, block-uniform)
-        for (int k = 0; k < kcount; ++k) {
-            T va[4], vb[4], vq[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (u < UA) va[u] = LD(PA, (ti + 16 * u) * HS_LD + k, PN);
-                if (u < UB) {
-                    vb[u] = LD(PB, (tj + 16 * u) * HS_LD + k, PN - HS_BLK * HS_LD);
-                    vq[u] = LD(PQ, (tj + 16 * u) * HS_LD + k, PN - 2 * HS_BLK * HS_LD);
-                }
-            }
-            if constexpr (sizeof(T) == 4) {
-                // (S, H) of a pair as the two lanes of one packed FMA (same bits as below)
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (u < UA && v < UB)
-                            sh2[u][v] = __ffma2_rn(make_float2(va[u], va[u]), make_float2(vb[v], vq[v]), sh2[u][v]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (u < UA && v < UB) {
-                            sacc[u][v] += va[u] * vb[v];
-                            hacc[u][v] += va[u] * vq[v];
-                        }
-            }
-        }
-        __syncthreads();
-    }
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sacc[u][v] = sh2[u][v].x, hacc[u][v] = sh2[u][v].y;
-    }
-    // Pattern positions: the CSR rows of this item's a-functions are copied into the (now
-    // free) panel memory, so each pair's binary search runs in shared memory; rows that do
-    // not fit search global memory.
-    __shared__ int rofs[HS_BLK + 1];
-    __shared__ int rlen[HS_BLK];
-    __shared__ long long rbase[HS_BLK];
-    int* rcols = reinterpret_cast<int*>(smem_raw);
-    const int rcap = static_cast<int>(PN * sizeof(T) / sizeof(int));
-    if (tid < w.na) {
-        const int fa = LD(a.listA, w.a0 + tid, a.listA_n);
-        const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
-        rbase[tid] = r0;
-        rlen[tid] = static_cast<int>(r1 - r0);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int o = 0;
-        for (int i = 0; i < w.na; ++i) {
-            rofs[i] = o;
-            if (o + rlen[i] <= rcap) o += rlen[i];
-            else rofs[i] = -1;                                   // searched in global memory
-        }
-    }
-    __syncthreads();
-    for (int i = tid >> 5; i < w.na; i += blockDim.x >> 5) {
-        if (rofs[i] < 0) continue;
-        for (int k = tid & 31; k < rlen[i]; k += 32)
-            ST(rcols, rofs[i] + k, rcap, LD(a.col, rbase[i] + k, a.nnz));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int i = ti + 16 * u;
-        if (i >= w.na) continue;
-        const int64_t r0 = rbase[i];
-        const int ro = rofs[i], rl = rlen[i];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int j = tj + 16 * v;
-            if (j >= w.nb) continue;
-            const int fb = LD(a.listB, w.b0 + j, a.listB_n);
-            int lo = 0, hi = rl - 1;
-            int64_t pos = -1;
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const int cm = ro >= 0 ? LD(rcols, ro + mid, rcap) : LD(a.col, r0 + mid, a.nnz);
-                if (cm == fb) {
-                    pos = r0 + mid;
-                    break;
-                }
-                if (cm < fb)
-                    lo = mid + 1;
-                else
-                    hi = mid - 1;
-            }
-            if (pos < 0) continue;
-            if (hacc[u][v] != T(0)) atomicAdd(a.H + pos, static_cast<double>(hacc[u][v]));
-            if (sacc[u][v] != T(0)) atomicAdd(a.S + pos, static_cast<double>(sacc[u][v]));
-        }
-    }
-}
-
 // ---------------------------------------------------------------- density: pair products
 //
 // rho_j = sum_ab K_ab u_a(j) u_b(j) (Eq. density) per tile of DT_X x DT_Y x DT_Z grid
@@ -2299,7 +2014,6 @@ cudaError_t configure_kernels(size_t max_smem) {
     SETMAX(k_fwd_xy_tc<2>) SETMAX(k_fwd_xy_tc<3>)
     SETMAX((k_bwd_xy<double, 0>)) SETMAX((k_bwd_xy<float, 0>))
     SETMAX((k_bwd_xy<float, 2>)) SETMAX((k_bwd_xy<float, 3>))
-    SETMAX(k_hs<double>) SETMAX(k_hs<float>)
     SETMAX(k_z_dens<double>) SETMAX(k_z_dens<float>)
 #undef SETMAX
     return cudaSuccess;
@@ -2386,14 +2100,5 @@ cudaError_t enqueue_density(const DensLaunch& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_hs(const HSLaunch& a, cudaStream_t s) {
-    const size_t es = a.prec == 0 ? sizeof(double) : sizeof(float);
-    const size_t smem = 3 * HS_BLK * HS_LD * es;
-    if (a.prec == 0)
-        TRACED(a.tr, TK_HS, s, (k_hs<double><<<a.nwork, 256, smem, s>>>(a)));
-    else
-        TRACED(a.tr, TK_HS, s, (k_hs<float><<<a.nwork, 256, smem, s>>>(a)));
-    return cudaGetLastError();
-}
 
 }  // namespace lsw

@@ -67,6 +67,8 @@ _SIGS = {
     "lsw_build_matrices": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_build_density": (C.c_int, [_P, _P, _P, _P, _I64P, _I64P]),
     "lsw_apply_hamiltonian_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lsw_combine": (C.c_int, [_P, _P, _P, _P]),
+    "lsw_lowdin_taylor": (C.c_int, [_P, _P, _P, _P]),
     "lsw_reformat": (C.c_int, [_P, _P, _I32P, _P, _P]),
     "lsw_workspace_bytes": (C.c_int, [_P, _I64P]),
     "lsw_sync": (C.c_int, [_P, C.c_double]),
@@ -81,7 +83,7 @@ _SIGS = {
     "lsw_load_phi": (C.c_int, [_P, C.c_char_p, _P]),
 }
 
-TRACE_KINDS = ["memset", "uncompress", "fwd_xy", "z_stage", "bwd_xy", "kinetic", "unused", "hs_tiles",
+TRACE_KINDS = ["memset", "uncompress", "fwd_xy", "z_stage", "bwd_xy", "kinetic", "hs_pack", "hs_tiles",
                "dens_realspace", "dens_products"]
 
 
@@ -187,6 +189,16 @@ def lsw_set_potential(sys, V, fine_lo, fine_dims):
 
 def lsw_apply_hamiltonian(sys, phi, hphi, e_kin=None, e_pot=None):
     check(lib().lsw_apply_hamiltonian(sys, _ptr(phi), _ptr(hphi), _ptr(e_kin), _ptr(e_pot)))
+
+
+def lsw_combine(sys, M, phi_in, phi_out):
+    """(M Phi)_a = L(a) sum_b M_ab phi_b for M on the pattern (FP64 device values)."""
+    check(lib().lsw_combine(sys, _ptr(M), _ptr(phi_in), _ptr(phi_out)))
+
+
+def lsw_lowdin_taylor(sys, S, phi_in, phi_out):
+    """phi'_a = L(a) sum_b (3 delta_ab - S_ab) / 2 phi_b (first-order Taylor Loewdin step)."""
+    check(lib().lsw_lowdin_taylor(sys, _ptr(S), _ptr(phi_in), _ptr(phi_out)))
 
 
 def lsw_apply_hamiltonian_noalloc(sys, phi, hphi, e_kin=None, e_pot=None):
