@@ -83,7 +83,12 @@ typedef enum {
     LSW_FILTER_KIN_GH = 7,
     LSW_FILTER_KIN_GG = 8,
     LSW_FILTER_FWD_H = 9,    /* (w * h)_m = sum_k w_{m-k} h_k, m = -14..16           */
-    LSW_FILTER_FWD_G = 10    /* (w * g)_m, m = -14..16                               */
+    LSW_FILTER_FWD_G = 10,   /* (w * g)_m, m = -14..16                               */
+    LSW_FILTER_MOVL_0 = 11,  /* F^p(l) = int x^p phi(x) phi(x - l) dx, l = -14..14,   */
+    LSW_FILTER_MOVL_1 = 12,  /* p = 0..4 (moment overlaps of the quartic confinement) */
+    LSW_FILTER_MOVL_2 = 13,
+    LSW_FILTER_MOVL_3 = 14,
+    LSW_FILTER_MOVL_4 = 15
 } lsw_filter;
 
 typedef struct lsw_ctx_s* lsw_ctx;
@@ -235,6 +240,34 @@ lsw_status lsw_combine(lsw_system sys, const double* M_dev, const void* phi_in_d
  * (allocated at the first call, counted by lsw_workspace_bytes).  Asynchronous.
  * Errors: as lsw_combine. */
 lsw_status lsw_lowdin_taylor(lsw_system sys, const double* S_dev, const void* phi_in_dev, void* phi_out_dev);
+
+/* Fermi operator expansion of the density kernel (App. "Fermi operator expansion";
+ * Sec. "Density kernel optimization"), on the pattern of lsw_pattern (symmetric, with the
+ * diagonal), FP64 throughout:
+ *   H~ = sigma (H - tau S), sigma = 2 / (e_max - e_min), tau = (e_min + e_max) / 2;
+ *   H~' = X H~ X restricted to the pattern, X = (3 I - S) / 2 (first-order Taylor S^-1/2);
+ *   K' = c_0/2 I + sum_{j=1}^{n_pl} c_j T_j(H~'), column by column with the recursion
+ *   t^{j+1} = 2 H~' t^j - t^{j-1}, every column cut to its pattern column after each
+ *   product (the linear-scaling evaluation); the c_j are those of the polynomial
+ *   interpolating f(x) = 1/2 [1 - erf((x - sigma (mu - tau)) / (sigma de))] at the n_pl + 1
+ *   Chebyshev nodes;
+ *   mu by bisection on [e_min, e_max] until |Tr K' - n_el| <= tol (at most max_bisect
+ *   steps; Tr K' for a trial mu comes from the traces of the T_j, computed once);
+ *   K = X K' X restricted to the pattern; E_BS = Tr(K H~) / sigma + tau Tr(K S).
+ * - H_dev, S_dev: FP64 values on the pattern (as lsw_build_matrices writes them);
+ *   e_min, e_max: bounds of the spectrum of H c = e S c (the library does not compute
+ *   them); n_el: the target of Tr K' (occupied orbitals, occupations in [0, 1]); de: the
+ *   smearing width in the units of H.
+ * - Kp_dev, K_dev: FP64 outputs on the pattern (nnz each).  *mu_out, *ebs_out, *trace_out
+ *   (host, may be NULL) receive mu, E_BS and the final Tr K'.
+ * Synchronous (the search of mu runs on the host from the device traces).  Work buffers
+ * are allocated at the first call (lsw_workspace_bytes).
+ * Errors: LSW_ERR_ARG (NULL, e_max <= e_min, de <= 0, n_pl < 1), LSW_ERR_STATE (host-only),
+ * LSW_ERR_UNSUPPORTED (pattern not symmetric or without the diagonal; more functions than
+ * the shared-memory column map holds), LSW_ERR_CUDA. */
+lsw_status lsw_foe(lsw_system sys, const double* H_dev, const double* S_dev, double e_min, double e_max, double n_el,
+                   int32_t n_pl, double de, double tol, int32_t max_bisect, double* Kp_dev, double* K_dev,
+                   double* mu_out, double* ebs_out, double* trace_out);
 
 /* Electronic density (Sec. II.A, Eq. density; App. D forms it like the scalar
  * products): rho_j = sum_ab K_ab u_a(j) u_b(j) at every fine point x_j = j h/2 of the

@@ -13,6 +13,7 @@
 //    of h), sum l^2 r_l = 2; blocks T_XY(l) = 4 sum X_k Y_k' r_{2l+k'-k}.
 //  * forward filters (w*h)_m, (w*g)_m: synthesis to h/2 followed by the magic filter,
 //    u_j = sum_i (w*h)_{j-2i} s_i + (w*g)_{j-2i} d_i.
+//  * moment overlaps F^p(l) = int x^p phi phi(. - l), p <= 4, for the quartic confinement.
 //
 // Method: complex roots of P by the Durand-Kerner iteration in double, candidate
 // filters in double, selection by the phase criterion, then Newton's method in
@@ -425,6 +426,42 @@ bool derive_filters(FilterSet* out, std::string* err) {
                 T[bx * 2 + by][l + L] = mul_d(s, 4.0);
             }
 
+    // moment overlaps F^p(l) = int x^p phi(x) phi(x - l) dx, p = 0..4, |l| <= 14 (the 1D
+    // Galerkin entries of the multiplication operators x^p, which the quartic confining
+    // potential needs): the refinement equation in both factors and x = (y + k) / 2 give
+    //   F^p(l) = 2^-p sum_{k,k'} h_k h_k' sum_{q<=p} C(p,q) k^(p-q) F^q(2l + k' - k);
+    // F^0 = delta (orthonormal translates); for p >= 1 the q = p part moves to the left,
+    // (I - 2^-p A) F^p = 2^-p sum_{q<p} ..., A(l, m) = a_{m - 2l} (autocorrelation of h).
+    std::vector<std::vector<dd>> Fm(MOVL_P, std::vector<dd>(KIN_TAPS, mk(0.0)));
+    Fm[0][L] = mk(1.0);
+    for (int p = 1; p < MOVL_P; ++p) {
+        std::vector<dd> Am(KIN_TAPS * KIN_TAPS, mk(0.0)), bm(KIN_TAPS, mk(0.0));
+        const double sc = std::ldexp(1.0, -p);
+        for (int l = -L; l <= L; ++l) {
+            for (int m = -L; m <= L; ++m) {
+                const int d = m - 2 * l;
+                dd v = (d >= -(n - 1) && d <= n - 1) ? mul_d(ac[d + n - 1], -sc) : mk(0.0);
+                if (m == l) v = add(v, mk(1.0));
+                Am[(l + L) * KIN_TAPS + (m + L)] = v;
+            }
+            dd acc = mk(0.0);
+            for (int q = 0; q < p; ++q)
+                for (int k = 0; k < n; ++k)
+                    for (int kp = 0; kp < n; ++kp) {
+                        const int idx = 2 * l + (kp + H_LO) - (k + H_LO);
+                        if (idx < -L || idx > L) continue;
+                        dd t = mul(mul(h[k], h[kp]), Fm[q][idx + L]);
+                        for (int r = 0; r < p - q; ++r) t = mul_d(t, static_cast<double>(k + H_LO));
+                        acc = add(acc, mul_d(t, binom(p, q)));
+                    }
+            bm[l + L] = mul_d(acc, sc);
+        }
+        if (!solve(Am, bm, KIN_TAPS, &Fm[p])) {
+            *err = "singular moment-overlap system";
+            return false;
+        }
+    }
+
     // forward filters (w * X)_m, m = -14..16
     dd Fw[2][FWD_TAPS];
     for (int x = 0; x < 2; ++x)
@@ -450,6 +487,8 @@ bool derive_filters(FilterSet* out, std::string* err) {
     }
     for (int x = 0; x < 2; ++x)
         for (int i = 0; i < FWD_TAPS; ++i) out->fwd[x][i] = to_d(Fw[x][i]);
+    for (int p = 0; p < MOVL_P; ++p)
+        for (int i = 0; i < KIN_TAPS; ++i) out->movl[p][i] = to_d(Fm[p][i]);
     return true;
 }
 

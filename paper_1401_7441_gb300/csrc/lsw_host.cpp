@@ -191,6 +191,9 @@ struct lsw_system_s {
     // H/S in the transposed layout: used tiles, per-atom tile tables, product items, the
     // atoms of each slab and the panel buffers of one slab (reused slab after slab)
     DeviceBuf d_ptiles, d_patoms, d_ttab, d_items, d_citems, d_slab_atoms, d_PA, d_PQ, d_mcoef;
+    // Fermi operator expansion: transposed positions, diagonal positions, the identity on
+    // the pattern, work matrices and the dense row scratch of the triple products
+    DeviceBuf d_tpos, d_diag, d_ident, d_foe, d_foe_scratch;
     std::vector<PanelSlab> slabs;
     DeviceBuf d_shift, d_fn_all;   // reformat: per-atom shifts, records of every function
     // density: real-space store, block records, tile lists (built for one grid)
@@ -1238,6 +1241,7 @@ lsw_status lsw_ctx_create(int device, void* stream, lsw_ctx* out) {
     CUDA_TRY(upload_filters(c->filters, device));
     CUDA_TRY(configure_kernels(c->max_smem));
     CUDA_TRY(configure_panel_kernels(c->max_smem));
+    CUDA_TRY(configure_foe_kernels(c->max_smem));
     *out = c.release();
     return LSW_OK;
 }
@@ -1267,6 +1271,9 @@ lsw_status lsw_filter_table(lsw_ctx ctx, int32_t which, int32_t* first, int32_t*
             src = f.kin[which - LSW_FILTER_KIN_HH], lo = -KIN_HALF, n = KIN_TAPS; break;
         case LSW_FILTER_FWD_H: case LSW_FILTER_FWD_G:
             src = f.fwd[which - LSW_FILTER_FWD_H], lo = FWD_LO, n = FWD_TAPS; break;
+        case LSW_FILTER_MOVL_0: case LSW_FILTER_MOVL_1: case LSW_FILTER_MOVL_2: case LSW_FILTER_MOVL_3:
+        case LSW_FILTER_MOVL_4:
+            src = f.movl[which - LSW_FILTER_MOVL_0], lo = -KIN_HALF, n = KIN_TAPS; break;
         default: return fail(LSW_ERR_ARG, "lsw_filter_table: unknown table %d", which);
     }
     *first = lo;
@@ -1508,6 +1515,145 @@ lsw_status lsw_lowdin_taylor(lsw_system sys, const double* S, const void* phi_in
     return enqueue_combine(sys, nullptr, T, phi_in, phi_out);
 }
 
+lsw_status lsw_foe(lsw_system sys, const double* H, const double* S, double e_min, double e_max, double n_el,
+                   int32_t n_pl, double de, double tol, int32_t max_bisect, double* Kp_out, double* K_out,
+                   double* mu_out, double* ebs_out, double* trace_out) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !H || !S || !Kp_out || !K_out) return fail(LSW_ERR_ARG, "lsw_foe: NULL buffer");
+    if (!(e_max > e_min) || !(de > 0.0) || n_pl < 1 || max_bisect < 1 || !(tol >= 0.0))
+        return fail(LSW_ERR_ARG, "lsw_foe: need e_max > e_min, de > 0, n_pl >= 1, max_bisect >= 1, tol >= 0");
+    const int n = static_cast<int>(sys->sf_atom.size());
+    const int64_t nnz = static_cast<int64_t>(sys->col.size());
+    if (static_cast<size_t>(n) * sizeof(int) + 1024 > sys->ctx->max_smem)
+        return fail(LSW_ERR_UNSUPPORTED, "lsw_foe: %d functions exceed the shared-memory column map", n);
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    cudaStream_t st = sys->stream;
+    const int triple_ctas = std::max(1, std::min(n, 4 * sys->ctx->n_sm));
+    if (sys->d_tpos.bytes == 0) {
+        // transposed and diagonal positions of the pattern, the identity on it
+        std::vector<int64_t> tpos(nnz), diag(n, -1);
+        std::vector<double> ident(nnz, 0.0);
+        for (int a = 0; a < n; ++a)
+            for (int64_t k = sys->row_ptr[a]; k < sys->row_ptr[a + 1]; ++k) {
+                const int b = sys->col[k];
+                const int32_t* c0 = sys->col.data() + sys->row_ptr[b];
+                const int32_t* c1 = sys->col.data() + sys->row_ptr[b + 1];
+                const int32_t* it = std::lower_bound(c0, c1, a);
+                if (it == c1 || *it != a) return fail(LSW_ERR_UNSUPPORTED, "lsw_foe: the pattern is not symmetric");
+                tpos[k] = sys->row_ptr[b] + (it - c0);
+                if (b == a) diag[a] = k, ident[k] = 1.0;
+            }
+        for (int a = 0; a < n; ++a)
+            if (diag[a] < 0) return fail(LSW_ERR_UNSUPPORTED, "lsw_foe: the pattern lacks a diagonal entry");
+        CUDA_TRY(sys->d_tpos.upload(tpos, st));
+        CUDA_TRY(sys->d_diag.upload(diag, st));
+        CUDA_TRY(sys->d_ident.upload(ident, st));
+        CUDA_TRY(sys->d_foe.alloc(static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 9 * sizeof(double) +
+                                  static_cast<size_t>(n_pl + 1 + 2) * sizeof(double)));
+        CUDA_TRY(sys->d_foe_scratch.alloc(static_cast<size_t>(triple_ctas) * n * sizeof(double)));
+        CUDA_TRY(cudaMemsetAsync(sys->d_foe_scratch.p, 0, sys->d_foe_scratch.bytes, st));
+    }
+    if (sys->d_foe.bytes < static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 9 * sizeof(double) +
+                               static_cast<size_t>(n_pl + 3) * sizeof(double)) {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        CUDA_TRY(sys->d_foe.alloc(static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 9 * sizeof(double) +
+                                  static_cast<size_t>(n_pl + 3) * sizeof(double)));
+    }
+    FoeLaunch f;
+    f.n = n;
+    f.nnz = nnz;
+    f.row_ptr = static_cast<const int64_t*>(sys->d_rowp.p);
+    f.col = static_cast<const int32_t*>(sys->d_col.p);
+    f.tpos = static_cast<const int64_t*>(sys->d_tpos.p);
+    f.diag = static_cast<const int64_t*>(sys->d_diag.p);
+    f.scratch = static_cast<double*>(sys->d_foe_scratch.p);
+    f.triple_ctas = triple_ctas;
+    f.cheb_ctas = std::max(1, std::min(n, 2 * sys->ctx->n_sm));
+    f.status = static_cast<int*>(sys->d_status.p);
+    double* w = static_cast<double*>(sys->d_foe.p);
+    double* Ht = w;
+    double* X = w + nnz;
+    double* Htp = w + 2 * nnz;
+    double* T[3] = {w + 3 * nnz, w + 4 * nnz, w + 5 * nnz};
+    double* Kc = w + 6 * nnz;
+    double* tmp = w + 7 * nnz;
+    double* tr_d = w + 9 * nnz;          // n_pl + 1 traces, then E_BS
+    const double* I = static_cast<const double*>(sys->d_ident.p);
+    const double sigma = 2.0 / (e_max - e_min), tau = 0.5 * (e_min + e_max);
+    CUDA_TRY(foe_prep(f, H, S, sigma, tau, Ht, X, st));
+    CUDA_TRY(foe_triple(f, X, Ht, Htp, st));
+    // the Chebyshev recursion t^{j+1} = 2 H~' t^j - t^{j-1} on every pattern column;
+    // pass 1 keeps the traces (for the search of mu), pass 2 sums K'
+    auto recursion = [&](const std::vector<double>* c) -> lsw_status {
+        const double* prev = I;
+        double* cur = T[0];
+        CUDA_TRY(foe_cheb(f, Htp, I, nullptr, 1.0, cur, st));
+        if (c) CUDA_TRY(foe_axpy_t(f, Kc, cur, (*c)[1], st));
+        else CUDA_TRY(foe_trace(f, cur, tr_d + 1, st));
+        int slot = 1;
+        for (int j = 2; j <= n_pl; ++j) {
+            double* next = T[slot];
+            CUDA_TRY(foe_cheb(f, Htp, cur, prev, 2.0, next, st));
+            if (c) CUDA_TRY(foe_axpy_t(f, Kc, next, (*c)[j], st));
+            else CUDA_TRY(foe_trace(f, next, tr_d + j, st));
+            prev = cur;
+            cur = next;
+            slot = (slot + 1) % 3;
+            if (T[slot] == prev) slot = (slot + 1) % 3;
+        }
+        return LSW_OK;
+    };
+    lsw_status e = recursion(nullptr);
+    if (e != LSW_OK) return e;
+    std::vector<double> tr(n_pl + 1);
+    CUDA_TRY(cudaMemcpyAsync(tr.data() + 1, tr_d + 1, n_pl * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    tr[0] = static_cast<double>(n);
+    // mu by bisection on [e_min, e_max]: Tr K' = c_0/2 Tr T_0 + sum_j c_j Tr T_j, the c_j
+    // those of the polynomial interpolating 1/2 [1 - erf((x - sigma (mu - tau)) / (sigma de))]
+    // at the n_pl + 1 Chebyshev nodes
+    const int Nn = n_pl + 1;
+    std::vector<double> c(Nn), cosj(static_cast<size_t>(Nn) * Nn), xk(Nn);
+    for (int k = 0; k < Nn; ++k) {
+        const double th = M_PI * (k + 0.5) / Nn;
+        xk[k] = std::cos(th);
+        for (int j = 0; j < Nn; ++j) cosj[static_cast<size_t>(j) * Nn + k] = std::cos(j * th);
+    }
+    double lo = e_min, hi = e_max, mu = 0.5 * (lo + hi), trace = 0.0;
+    for (int it = 0; it < max_bisect; ++it) {
+        mu = 0.5 * (lo + hi);
+        const double m0 = sigma * (mu - tau), w0 = sigma * de;
+        std::vector<double> fx(Nn);
+        for (int k = 0; k < Nn; ++k) fx[k] = 0.5 * (1.0 - std::erf((xk[k] - m0) / w0));
+        for (int j = 0; j < Nn; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < Nn; ++k) acc += fx[k] * cosj[static_cast<size_t>(j) * Nn + k];
+            c[j] = 2.0 / Nn * acc;
+        }
+        trace = 0.5 * c[0] * tr[0];
+        for (int j = 1; j < Nn; ++j) trace += c[j] * tr[j];
+        if (std::fabs(trace - n_el) <= tol) break;
+        if (trace < n_el) lo = mu;
+        else hi = mu;
+    }
+    CUDA_TRY(cudaMemsetAsync(Kc, 0, nnz * sizeof(double), st));
+    CUDA_TRY(foe_axpy_t(f, Kc, I, 0.5 * c[0], st));
+    e = recursion(&c);
+    if (e != LSW_OK) return e;
+    CUDA_TRY(foe_transpose(f, Kc, Kp_out, st));        // K' (columns were kept on the CSR rows)
+    CUDA_TRY(foe_triple(f, X, Kp_out, K_out, st));     // K = S^-1/2 K' S^-1/2 on the pattern
+    CUDA_TRY(foe_ebs(f, K_out, Ht, S, sigma, tau, tr_d + n_pl + 1, st));
+    double ebs = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&ebs, tr_d + n_pl + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    (void)tmp;
+    if (mu_out) *mu_out = mu;
+    if (ebs_out) *ebs_out = ebs;
+    if (trace_out) *trace_out = trace;
+    return LSW_OK;
+}
+
 lsw_status lsw_build_density(lsw_system sys, const void* phi, const double* K, double* rho, const int64_t fine_lo[3],
                              const int64_t fine_dims[3]) {
     g_err.clear();
@@ -1712,6 +1858,7 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
                                &sys->d_sfatom, &sys->d_rowp, &sys->d_col, &sys->d_tile_fine,
                                &sys->d_listA, &sys->d_listB, &sys->d_ptiles, &sys->d_patoms, &sys->d_ttab,
                                &sys->d_items, &sys->d_citems, &sys->d_slab_atoms, &sys->d_PA, &sys->d_PQ, &sys->d_mcoef,
+                               &sys->d_tpos, &sys->d_diag, &sys->d_ident, &sys->d_foe, &sys->d_foe_scratch,
                                &sys->d_ws, &sys->d_status,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
                                &sys->d_ep, &sys->d_shift, &sys->d_fn_all, &sys->d_U, &sys->d_dfn,

@@ -16,6 +16,7 @@ constexpr int KIN_HALF = 14;     // kinetic blocks l = -14..14
 constexpr int KIN_TAPS = 2 * KIN_HALF + 1;
 constexpr int FWD_LO = -14;      // combined filters (w * h), (w * g): m = -14..16
 constexpr int FWD_TAPS = 31;
+constexpr int MOVL_P = 5;        // moment overlaps F^p, p = 0..4 (quartic confinement)
 constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [2lo-14, 2hi+16]
 constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
 constexpr int ZCOLS_F64 = 64;    // real-space columns per block of the z stage (FP64)
@@ -28,6 +29,7 @@ struct FilterSet {
     double kin_r[KIN_TAPS];
     double kin[4][KIN_TAPS];     // hh, hg, gh, gg: <X_0|d2|Y_l>
     double fwd[2][FWD_TAPS];     // (w*h)_m, (w*g)_m
+    double movl[5][KIN_TAPS];    // F^p(l) = int x^p phi(x) phi(x - l) dx, p = 0..4
 };
 
 // Derive the whole table (lsw_filters.cpp).  Returns false with a message on failure.
@@ -242,6 +244,30 @@ struct PanelHSLaunch {
     int64_t listA_n, listB_n, nnz, PA_n, PQ_n, n_tiles;
     int n_sf;
 };
+
+// Fermi operator expansion on the pattern (lsw_foe.cu): shared arguments.
+struct FoeLaunch {
+    int n;                       // functions (rows)
+    int64_t nnz;
+    const int64_t* row_ptr;      // pattern CSR (symmetric, with the diagonal)
+    const int32_t* col;
+    const int64_t* tpos;         // position of the transposed entry of each entry
+    const int64_t* diag;         // position of the diagonal entry of each row
+    double* scratch;             // triple_ctas dense rows of n values, zero between uses
+    int triple_ctas, cheb_ctas;
+    int* status;
+};
+cudaError_t configure_foe_kernels(size_t max_smem);
+cudaError_t foe_prep(const FoeLaunch& a, const double* H, const double* S, double sigma, double tau, double* Ht,
+                     double* X, cudaStream_t s);
+cudaError_t foe_triple(const FoeLaunch& a, const double* X, const double* A, double* Y, cudaStream_t s);
+cudaError_t foe_cheb(const FoeLaunch& a, const double* Htp, const double* Tc, const double* Tp, double alpha, double* Tn,
+                     cudaStream_t s);
+cudaError_t foe_trace(const FoeLaunch& a, const double* T, double* out, cudaStream_t s);
+cudaError_t foe_axpy_t(const FoeLaunch& a, double* K, const double* T, double c, cudaStream_t s);
+cudaError_t foe_transpose(const FoeLaunch& a, const double* src, double* dst, cudaStream_t s);
+cudaError_t foe_ebs(const FoeLaunch& a, const double* K, const double* Ht, const double* S, double sigma, double tau,
+                    double* out, cudaStream_t s);
 
 // Fixed device scratch of the allocation-free Hamiltonian entry point (lsw_kernels.cu).
 constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(32) << 20;   // 32 MiB

@@ -25,7 +25,8 @@ LSW_PART_COARSE, LSW_PART_FINE = 0, 1
 LSW_FINE_UNION, LSW_FINE_OWN = 0, 1
 LSW_PAIR_CUTOFF, LSW_PAIR_SUM_OF_RADII = 0, 1
 FILTERS = {"h": 0, "g": 1, "moments": 2, "magic": 3, "kin_r": 4, "kin_hh": 5, "kin_hg": 6,
-           "kin_gh": 7, "kin_gg": 8, "fwd_h": 9, "fwd_g": 10}
+           "kin_gh": 7, "kin_gg": 8, "fwd_h": 9, "fwd_g": 10, "movl_0": 11, "movl_1": 12,
+           "movl_2": 13, "movl_3": 14, "movl_4": 15}
 
 _STATUS = {1: "LSW_ERR_ARG", 2: "LSW_ERR_OOM", 3: "LSW_ERR_CUDA", 4: "LSW_ERR_TIMEOUT",
            5: "LSW_ERR_STATE", 6: "LSW_ERR_UNSUPPORTED", 7: "LSW_ERR_IO"}
@@ -69,6 +70,8 @@ _SIGS = {
     "lsw_apply_hamiltonian_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_combine": (C.c_int, [_P, _P, _P, _P]),
     "lsw_lowdin_taylor": (C.c_int, [_P, _P, _P, _P]),
+    "lsw_foe": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double,
+                          C.c_int32, _P, _P, _DP, _DP, _DP]),
     "lsw_reformat": (C.c_int, [_P, _P, _I32P, _P, _P]),
     "lsw_workspace_bytes": (C.c_int, [_P, _I64P]),
     "lsw_sync": (C.c_int, [_P, C.c_double]),
@@ -199,6 +202,14 @@ def lsw_combine(sys, M, phi_in, phi_out):
 def lsw_lowdin_taylor(sys, S, phi_in, phi_out):
     """phi'_a = L(a) sum_b (3 delta_ab - S_ab) / 2 phi_b (first-order Taylor Loewdin step)."""
     check(lib().lsw_lowdin_taylor(sys, _ptr(S), _ptr(phi_in), _ptr(phi_out)))
+
+
+def lsw_foe(sys, H, S, e_min, e_max, n_el, n_pl, de, Kp, K, tol=1e-10, max_bisect=200):
+    """Fermi operator expansion on the pattern; returns (mu, E_BS, Tr K')."""
+    mu, ebs, tr = C.c_double(), C.c_double(), C.c_double()
+    check(lib().lsw_foe(sys, _ptr(H), _ptr(S), e_min, e_max, n_el, n_pl, de, tol, max_bisect, _ptr(Kp), _ptr(K),
+                        C.byref(mu), C.byref(ebs), C.byref(tr)))
+    return mu.value, ebs.value, tr.value
 
 
 def lsw_apply_hamiltonian_noalloc(sys, phi, hphi, e_kin=None, e_pot=None):

@@ -44,6 +44,13 @@ def test_filters_equal_oracle_table(ctx):
         lo, vals = lsw.lsw_filter_table(ctx, name)
         assert lo == tab[name][0]
         assert np.array_equal(vals, tab[name][1]), name
+    # moment overlaps of the confinement: the library's double-double solve against the
+    # oracle's 50-digit one, each rounded once to FP64
+    for p in range(5):
+        lo, vals = lsw.lsw_filter_table(ctx, "movl_%d" % p)
+        ref = tab["movl_%d" % p]
+        assert lo == ref[0]
+        assert np.max(np.abs(vals - ref[1])) <= 2e-16 * max(1.0, np.max(np.abs(ref[1]))), p
 
 
 def test_forward_filters_are_the_convolution(ctx):
