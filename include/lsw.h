@@ -269,6 +269,46 @@ lsw_status lsw_foe(lsw_system sys, const double* H_dev, const double* S_dev, dou
                    int32_t n_pl, double de, double tol, int32_t max_bisect, double* Kp_dev, double* K_dev,
                    double* mu_out, double* ebs_out, double* trace_out);
 
+/* Quartic confining potential (Sec. "Support function optimization": in the first
+ * iterations each support function alpha sees its own Hamiltonian
+ * H_alpha = H_KS + a_alpha (r - R_alpha)^4, R_alpha its atom's centre):
+ *     hphi_dev += L'(alpha) a_alpha Q_alpha L(alpha) phi_alpha,
+ *     e_conf_dev[alpha] = <phi_alpha | a_alpha Q_alpha | phi_alpha>,
+ * Q_alpha the Galerkin matrix of (r - R_alpha)^4 = sum_d X_d^4 + 2 sum_{d<e} X_d^2 X_e^2 in
+ * the two-level basis: each X_d^m a 1D operator along d between the scaling and wavelet
+ * functions of coarse points i, j (|j - i| <= 14), its entries built from the moment
+ * overlaps F^p of the filter set and the powers of (2 i + k - 2 R_d / h) (the text: "in
+ * the same manner as the kinetic energy").  Call after lsw_apply_hamiltonian on the same
+ * buffers to get H_alpha phi_alpha.  a_dev: n_sf FP64 prefactors (device); phi_dev on L,
+ * hphi_dev on L' (layouts of lsw_system_layout, system precision); e_conf_dev: n_sf FP64
+ * or NULL.  The first call builds the operator tables of every atom (host, then
+ * uploaded; lsw_workspace_bytes) and the batch boxes.  Asynchronous.
+ * Errors: LSW_ERR_ARG (NULL), LSW_ERR_STATE (host-only), LSW_ERR_CUDA. */
+lsw_status lsw_add_confinement(lsw_system sys, const double* a_dev, const void* phi_dev, void* hphi_dev,
+                               double* e_conf_dev);
+
+/* One row of the 1D operator tables of lsw_add_confinement, for cross-checks (host, no
+ * device work): out[l + 14] = <chi^b_i | (x_dim - R_dim)^m | chi^b'_{i+l}>, l = -14..14,
+ * for coarse index i along dimension dim (0..2), m = 2 or 4, b, b' = 0 (scaling) or 1
+ * (wavelet), R the centre of atom `atom`.  Errors: LSW_ERR_ARG. */
+lsw_status lsw_confinement_row(lsw_system sys, int32_t atom, int32_t dim, int32_t m, int32_t b, int32_t bp, int64_t i,
+                               double* out);
+
+/* Preconditioning of the support-function gradient (Sec. "Gradient and preconditioning",
+ * Eq. precond): for every function alpha, `iters` conjugate-gradient iterations from
+ * g_prec = 0 on
+ *     A g_prec = -g,   A = L(alpha) (-1/2 nabla^2 + a_alpha (r - R_alpha)^4 - eps_alpha) L(alpha),
+ * the kinetic part by the Galerkin blocks, the quartic as in lsw_add_confinement.  The
+ * iteration of each function is its own (its own step lengths); it stops changing once
+ * its residual is exactly zero.  g_dev, gprec_dev: compressed on L (system precision),
+ * not overlapping (only members are written); a_dev, eps_dev: n_sf FP64 (eps_alpha < 0
+ * keeps A positive definite); res_dev: iters x n_sf FP64 residual 2-norms after each
+ * iteration (row = iteration), or NULL.  Vectors in the system precision, dot products
+ * in FP64.  Asynchronous.  Errors: LSW_ERR_ARG (NULL, overlap, iters < 1),
+ * LSW_ERR_STATE (host-only), LSW_ERR_CUDA. */
+lsw_status lsw_precondition(lsw_system sys, const double* a_dev, const double* eps_dev, const void* g_dev,
+                            void* gprec_dev, int32_t iters, double* res_dev);
+
 /* Electronic density (Sec. II.A, Eq. density; App. D forms it like the scalar
  * products): rho_j = sum_ab K_ab u_a(j) u_b(j) at every fine point x_j = j h/2 of the
  * grid block [fine_lo, fine_lo + fine_dims), where u_a = M W L phi_a are the real-space
@@ -378,6 +418,9 @@ lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev);
 
 /* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
  * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8),
+ * "hphi_limit" (lsw_apply_hamiltonian computes H phi and the energies of functions
+ * 0 .. value - 1 only, leaving the others' outputs untouched; -1, the default: every
+ * function; a rank of a sharded run numbers its own functions first),
  * "slab_mb" (H/S and combination: panel budget of one slab of tiles, MiB; the panels of
  * consecutive tile-z layers are built and consumed slab by slab, default 8192),
  * "zsplit" (LSW_FP32_BF16X systems only: 2 or 3 bfloat16 parts per FP32 operand of the

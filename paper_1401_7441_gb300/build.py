@@ -1,6 +1,6 @@
 """In-tree build of the sm_103a library ``liblsw.so`` (nvcc + the host compiler).
 
-Five translation units compiled in parallel, one -gencode (sm_103a), static CUDA
+Six translation units compiled in parallel, one -gencode (sm_103a), static CUDA
 runtime, no cmake.  Host code is compiled without floating-point contraction so that
 the locreg membership tests and the filter derivation round exactly as specified.
 """
@@ -29,7 +29,7 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("lsw_kernels.cu", "lsw_panels.cu", "lsw_foe.cu", "lsw_host.cpp", "lsw_filters.cpp")]
+    return [os.path.join(CSRC, f) for f in ("lsw_kernels.cu", "lsw_panels.cu", "lsw_foe.cu", "lsw_confine.cu", "lsw_host.cpp", "lsw_filters.cpp")]
 
 
 def build(verbose: bool = False, force: bool = False) -> str:

@@ -194,6 +194,10 @@ struct lsw_system_s {
     // Fermi operator expansion: transposed positions, diagonal positions, the identity on
     // the pattern, work matrices and the dense row scratch of the triple products
     DeviceBuf d_tpos, d_diag, d_ident, d_foe, d_foe_scratch;
+    // confinement and preconditioning: per-atom tables of the 1D operators X_d^2, X_d^4,
+    // the batch boxes, and the conjugate-gradient vectors and scalars
+    DeviceBuf d_qtab, d_qtab_off, d_cbox, d_cg, d_cgs;
+    int conf_batch = 0;
     std::vector<PanelSlab> slabs;
     DeviceBuf d_shift, d_fn_all;   // reformat: per-atom shifts, records of every function
     // density: real-space store, block records, tile lists (built for one grid)
@@ -207,6 +211,7 @@ struct lsw_system_s {
     int batch_size = 0;
     int tile = 4;
     int64_t slab_mb = PANEL_SLAB_MB;
+    int64_t hphi_limit = -1;         // option "hphi_limit" (-1: every function)
     int use_graph = 1;
     // potential
     const void* V = nullptr;
@@ -474,10 +479,13 @@ lsw_status build_plans(lsw_system_s* s) {
     }
     s->batches.clear();
     int64_t ws_max = 0;
-    for (int64_t f0 = 0; f0 < nf; f0 += s->batch_size) {
+    // option "hphi_limit": H phi only for functions 0 .. limit - 1 (a rank of a sharded
+    // run computes its own functions, which its sub-system numbers first)
+    const int64_t nf_h = s->hphi_limit >= 0 ? std::min<int64_t>(nf, s->hphi_limit) : nf;
+    for (int64_t f0 = 0; f0 < nf_h; f0 += s->batch_size) {
         Batch b;
         b.fn0 = f0;
-        b.nfn = std::min<int64_t>(s->batch_size, nf - f0);
+        b.nfn = std::min<int64_t>(s->batch_size, nf_h - f0);
         HphiLaunch& p = b.proto;
         std::memset(&p, 0, sizeof(p));
         p.prec = s->prec;
@@ -856,7 +864,8 @@ void harvest(lsw_system_s* s, Tracer* tr) {
 
 lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hphi, double* ek, double* ep) {
     cudaStream_t st = s->stream;
-    const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+    int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+    if (s->hphi_limit >= 0) nf = std::min<int64_t>(nf, s->hphi_limit);
     CUDA_TRY(cudaMemsetAsync(ek, 0, nf * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(ep, 0, nf * sizeof(double), st));
     for (const Batch& b : s->batches) {
@@ -1654,6 +1663,236 @@ lsw_status lsw_foe(lsw_system sys, const double* H, const double* S, double e_mi
     return LSW_OK;
 }
 
+// ---------------------------------------------------------------- confinement (Sec. "Support function optimization")
+
+namespace {
+// Tables of the 1D operators (x - R_d)^m, m = 2, 4, between the scaling (b = 0) and
+// wavelet (b = 1) functions of coarse points i, j = i + l (|l| <= 14) along each
+// dimension of every atom's widened box (i over [lo_d - 14, lo_d + n_d + 13]):
+//   <chi^b_i|(x - R)^m|chi^b'_j> = (h/2)^m sum_p C(m,p) sum_k X_k (2i + k - 2c)^(m-p) G^p_Y(l, k),
+//   G^p_Y(l, k) = sum_k' Y_k' F^p(2l + k' - k),   c = R_d / h,  X, Y = h or g by b, b',
+// F^p the moment overlaps of the filter set (the Galerkin matrix of the multiplication
+// operator x^m in the two-level basis, expanded by the refinement equation).
+// G[y][p][l + 14][k] = sum_k' Y_k' F^p(2l + k' - k)
+std::vector<double> conf_G(const FilterSet& F) {
+    const double* XY[2] = {F.h, F.g};
+    std::vector<double> G(2 * MOVL_P * KIN_TAPS * D16, 0.0);
+    for (int y = 0; y < 2; ++y)
+        for (int p = 0; p < MOVL_P; ++p)
+            for (int l = -KIN_HALF; l <= KIN_HALF; ++l)
+                for (int k = 0; k < D16; ++k) {
+                    double acc = 0.0;
+                    for (int kp = 0; kp < D16; ++kp) {
+                        const int idx = 2 * l + (kp + H_LO) - (k + H_LO);
+                        if (idx < -KIN_HALF || idx > KIN_HALF) continue;
+                        acc += XY[y][kp] * F.movl[p][idx + KIN_HALF];
+                    }
+                    G[((y * MOVL_P + p) * KIN_TAPS + (l + KIN_HALF)) * D16 + k] = acc;
+                }
+    return G;
+}
+
+// out[l + 14] = <chi^b_i|(x - R)^m|chi^b'_{i+l}>, l = -14..14, c = R / h
+void conf_row(const FilterSet& F, const std::vector<double>& G, int m, int b, int bp, double gi, double c, double h,
+              double* out) {
+    const double* XY[2] = {F.h, F.g};
+    const double hm = std::pow(h / 2.0, m);
+    for (int l = -KIN_HALF; l <= KIN_HALF; ++l) {
+        double acc = 0.0;
+        double cp = 1.0;   // C(m, p)
+        for (int p = 0; p <= m; ++p) {
+            if (p > 0) cp = cp * (m - p + 1) / p;
+            const double* Gp = &G[((bp * MOVL_P + p) * KIN_TAPS + (l + KIN_HALF)) * D16];
+            double sk = 0.0;
+            for (int k = 0; k < D16; ++k) {
+                const double z = 2.0 * gi + (k + H_LO) - 2.0 * c;
+                double zp = 1.0;
+                for (int r = 0; r < m - p; ++r) zp *= z;
+                sk += XY[b][k] * zp * Gp[k];
+            }
+            acc += cp * sk;
+        }
+        out[l + KIN_HALF] = hm * acc;
+    }
+}
+
+lsw_status build_conf_tables(lsw_system_s* s) {
+    const FilterSet& F = s->ctx->filters;
+    const std::vector<double> G = conf_G(F);
+    const int na = s->n_atoms;
+    std::vector<int64_t> off(na + 1, 0);
+    for (int a = 0; a < na; ++a) {
+        int64_t n = 0;
+        for (int d = 0; d < 3; ++d) n += 2LL * 4 * (s->L[a].n[d] + 2 * KIN_HALF) * KIN_TAPS;
+        off[a + 1] = off[a] + n;
+    }
+    std::vector<double> tab(std::max<int64_t>(off[na], 1), 0.0);
+    const double h = s->h;
+    parallel_for(na, [&](int a) {
+        int64_t base = off[a];
+        for (int d = 0; d < 3; ++d) {
+            const int E = s->L[a].n[d] + 2 * KIN_HALF;
+            const double c = s->pos[3 * a + d] / h;
+            for (int mi = 0; mi < 2; ++mi)
+                for (int b = 0; b < 2; ++b)
+                    for (int bp = 0; bp < 2; ++bp)
+                        for (int i = 0; i < E; ++i)
+                            conf_row(F, G, mi == 0 ? 2 : 4, b, bp, static_cast<double>(s->L[a].lo[d] - KIN_HALF + i), c, h,
+                                     &tab[base + ((static_cast<int64_t>(mi) * 4 + (b * 2 + bp)) * E + i) * KIN_TAPS]);
+            base += 2LL * 4 * E * KIN_TAPS;
+        }
+    });
+    cudaStream_t st = s->stream;
+    CUDA_TRY(s->d_qtab.upload(tab, st));
+    CUDA_TRY(s->d_qtab_off.upload(off, st));
+    return LSW_OK;
+}
+
+// Launch arguments of one batch [f0, f0 + nfn) of the confinement kernels.
+ConfLaunch conf_launch(lsw_system_s* s, int64_t f0, int nfn, const double* acoef, const double* eps, int64_t box_stride) {
+    ConfLaunch c;
+    std::memset(&c, 0, sizeof(c));
+    c.prec = s->prec;
+    c.f0 = f0;
+    c.nfn = nfn;
+    c.sf_atom = static_cast<const int32_t*>(s->d_sfatom.p);
+    c.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
+    c.seg = static_cast<const Seg*>(s->d_seg.p);
+    c.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
+    c.off_L = static_cast<const int64_t*>(s->d_offL.p);
+    c.off_Lp = static_cast<const int64_t*>(s->d_offLp.p);
+    c.qtab = static_cast<const double*>(s->d_qtab.p);
+    c.qtab_off = static_cast<const int64_t*>(s->d_qtab_off.p);
+    c.acoef = acoef;
+    c.eps = eps;
+    for (int b = 0; b < 4; ++b)
+        for (int l = 0; l < KIN_TAPS; ++l) c.kin[b][l] = s->ctx->filters.kin[b][l];
+    c.kin_scale = -1.0 / (2.0 * s->h * s->h);
+    c.box_stride = box_stride;
+    for (int64_t f = f0; f < f0 + nfn; ++f) {
+        const int a = s->sf_atom[f];
+        c.max_rows_L = std::max(c.max_rows_L, s->L[a].n[1] * s->L[a].n[2]);
+        c.max_rows_P = std::max(c.max_rows_P, s->Lp[a].n[1] * s->Lp[a].n[2]);
+        int64_t v = 1;
+        for (int d = 0; d < 3; ++d) v *= s->L[a].n[d] + 2 * KIN_HALF;
+        c.max_vol = std::max(c.max_vol, v);
+    }
+    c.status = static_cast<int*>(s->d_status.p);
+    c.qtab_n = static_cast<int64_t>(s->d_qtab.bytes / sizeof(double));
+    c.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
+    c.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
+    c.vec_n = s->off_L.back();
+    c.dst_n = s->off_Lp.back();
+    c.n_sf = static_cast<int>(s->sf_atom.size());
+    c.n_atoms = s->n_atoms;
+    return c;
+}
+
+// Tables (first call) and batch boxes: three boxes per function of a batch, the batch
+// sized to a budget of 2 GiB.  Returns the box stride (elements) and the batch size.
+lsw_status conf_prepare(lsw_system_s* s, int64_t* box_stride, int* batch) {
+    if (s->d_qtab.bytes == 0) {
+        lsw_status e = build_conf_tables(s);
+        if (e != LSW_OK) return e;
+    }
+    int64_t vmax = 0;
+    for (int a = 0; a < s->n_atoms; ++a) {
+        int64_t v = 1;
+        for (int d = 0; d < 3; ++d) v *= s->L[a].n[d] + 2 * KIN_HALF;
+        vmax = std::max(vmax, v);
+    }
+    *box_stride = align64(8 * vmax);
+    const int64_t nf = static_cast<int64_t>(s->sf_atom.size());
+    const size_t per = 3 * static_cast<size_t>(*box_stride) * s->esize;
+    const int b = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({64, nf, static_cast<int64_t>((size_t(2) << 30) / per)})));
+    if (s->d_cbox.bytes < per * b) {
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        CUDA_TRY(s->d_cbox.alloc(per * b));
+    }
+    *batch = b;
+    return LSW_OK;
+}
+}  // namespace
+
+lsw_status lsw_confinement_row(lsw_system sys, int32_t atom, int32_t dim, int32_t m, int32_t b, int32_t bp, int64_t i,
+                               double* out) {
+    g_err.clear();
+    if (!sys || !out) return fail(LSW_ERR_ARG, "lsw_confinement_row: NULL argument");
+    if (atom < 0 || atom >= sys->n_atoms || dim < 0 || dim > 2 || (m != 2 && m != 4) || b < 0 || b > 1 || bp < 0 || bp > 1)
+        return fail(LSW_ERR_ARG, "lsw_confinement_row: argument out of range");
+    const std::vector<double> G = conf_G(sys->ctx->filters);
+    conf_row(sys->ctx->filters, G, m, b, bp, static_cast<double>(i), sys->pos[3 * atom + dim] / sys->h, sys->h, out);
+    return LSW_OK;
+}
+
+lsw_status lsw_add_confinement(lsw_system sys, const double* a_dev, const void* phi, void* hphi, double* e_conf) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !a_dev || !phi || !hphi) return fail(LSW_ERR_ARG, "lsw_add_confinement: NULL buffer");
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    int64_t stride = 0;
+    int batch = 0;
+    lsw_status e = conf_prepare(sys, &stride, &batch);
+    if (e != LSW_OK) return e;
+    const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
+    unsigned char* box = static_cast<unsigned char*>(sys->d_cbox.p);
+    const size_t bb = static_cast<size_t>(batch) * stride * sys->esize;
+    for (int64_t f0 = 0; f0 < nf; f0 += batch) {
+        const int nb = static_cast<int>(std::min<int64_t>(batch, nf - f0));
+        ConfLaunch c = conf_launch(sys, f0, nb, a_dev, nullptr, stride);
+        CUDA_TRY(conf_apply(c, phi, box, box + bb, box + 2 * bb, hphi, 1, 1, false, e_conf, sys->stream));
+    }
+    return LSW_OK;
+}
+
+lsw_status lsw_precondition(lsw_system sys, const double* a_dev, const double* eps_dev, const void* g, void* gprec,
+                            int32_t iters, double* res) {
+    g_err.clear();
+    if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
+    if (!sys || !a_dev || !eps_dev || !g || !gprec) return fail(LSW_ERR_ARG, "lsw_precondition: NULL buffer");
+    if (g == gprec) return fail(LSW_ERR_ARG, "lsw_precondition: g and g_prec must not overlap");
+    if (iters < 1) return fail(LSW_ERR_ARG, "lsw_precondition: iters %d", iters);
+    CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    int64_t stride = 0;
+    int batch = 0;
+    lsw_status e = conf_prepare(sys, &stride, &batch);
+    if (e != LSW_OK) return e;
+    const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
+    const int64_t nv = sys->off_L.back();
+    const size_t vb = static_cast<size_t>(std::max<int64_t>(nv, 1)) * sys->esize;
+    if (sys->d_cg.bytes < 3 * vb || sys->d_cgs.bytes < 4 * nf * sizeof(double)) {
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        CUDA_TRY(sys->d_cg.alloc(3 * vb));
+        CUDA_TRY(sys->d_cgs.alloc(static_cast<size_t>(4 * std::max<int64_t>(nf, 1)) * sizeof(double)));
+    }
+    unsigned char* V = static_cast<unsigned char*>(sys->d_cg.p);
+    void* r = V;
+    void* p = V + vb;
+    void* Ap = V + 2 * vb;
+    double* sc = static_cast<double*>(sys->d_cgs.p);
+    double* rr = sc;
+    double* rr_new = sc + nf;
+    double* pAp = sc + 2 * nf;
+    unsigned char* box = static_cast<unsigned char*>(sys->d_cbox.p);
+    const size_t bb = static_cast<size_t>(batch) * stride * sys->esize;
+    cudaStream_t st = sys->stream;
+    for (int64_t f0 = 0; f0 < nf; f0 += batch) {
+        const int nb = static_cast<int>(std::min<int64_t>(batch, nf - f0));
+        ConfLaunch c = conf_launch(sys, f0, nb, a_dev, eps_dev, stride);
+        CUDA_TRY(conf_cg_init(c, g, gprec, r, p, st));
+        CUDA_TRY(conf_dot(c, r, r, rr, st));
+        for (int it = 0; it < iters; ++it) {
+            // Ap = P_L (T + Q - eps) P_L p
+            CUDA_TRY(conf_apply(c, p, box, box + bb, box + 2 * bb, Ap, 0, 0, true, nullptr, st));
+            CUDA_TRY(conf_dot(c, p, Ap, pAp, st));
+            CUDA_TRY(conf_cg_step1(c, rr, pAp, p, Ap, gprec, r, st));
+            CUDA_TRY(conf_dot(c, r, r, rr_new, st));
+            CUDA_TRY(conf_cg_step2(c, rr, rr_new, r, p, res ? res + static_cast<int64_t>(it) * nf : nullptr, st));
+        }
+    }
+    return LSW_OK;
+}
+
 lsw_status lsw_build_density(lsw_system sys, const void* phi, const double* K, double* rho, const int64_t fine_lo[3],
                              const int64_t fine_dims[3]) {
     g_err.clear();
@@ -1859,6 +2098,7 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
                                &sys->d_listA, &sys->d_listB, &sys->d_ptiles, &sys->d_patoms, &sys->d_ttab,
                                &sys->d_items, &sys->d_citems, &sys->d_slab_atoms, &sys->d_PA, &sys->d_PQ, &sys->d_mcoef,
                                &sys->d_tpos, &sys->d_diag, &sys->d_ident, &sys->d_foe, &sys->d_foe_scratch,
+                               &sys->d_qtab, &sys->d_qtab_off, &sys->d_cbox, &sys->d_cg, &sys->d_cgs,
                                &sys->d_ws, &sys->d_status,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
                                &sys->d_ep, &sys->d_shift, &sys->d_fn_all, &sys->d_U, &sys->d_dfn,
@@ -1984,6 +2224,14 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
         drop_graphs(sys);
         sys->batch_size = static_cast<int>(value);
+        return build_plans(sys);
+    }
+    if (std::strcmp(name, "hphi_limit") == 0) {
+        if (value < -1 || value > static_cast<int64_t>(sys->sf_atom.size()))
+            return fail(LSW_ERR_ARG, "lsw_set_option: hphi_limit %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        sys->hphi_limit = value;
         return build_plans(sys);
     }
     if (std::strcmp(name, "graph") == 0) {

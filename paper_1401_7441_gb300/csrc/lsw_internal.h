@@ -269,6 +269,40 @@ cudaError_t foe_transpose(const FoeLaunch& a, const double* src, double* dst, cu
 cudaError_t foe_ebs(const FoeLaunch& a, const double* K, const double* Ht, const double* S, double sigma, double tau,
                     double* out, cudaStream_t s);
 
+// Quartic confinement and preconditioning (lsw_confine.cu): one batch of functions
+// f0 .. f0 + nfn - 1, each on its dense box E = L box widened by 14 (8 types).
+struct ConfLaunch {
+    int prec;
+    int64_t f0;
+    int nfn;
+    const int32_t* sf_atom;
+    const AtomRec* atoms;
+    const Seg* seg;
+    const int32_t* rowptr;
+    const int64_t* off_L;
+    const int64_t* off_Lp;
+    const double* qtab;          // per atom: [dim][m = 2, 4][b b'][i over E][l + 14] of X_d^m
+    const int64_t* qtab_off;     // first table entry of each atom (n_atoms + 1)
+    const double* acoef;         // a_f, the confinement prefactor of each function
+    const double* eps;           // eps_f of the preconditioning equation (NULL otherwise)
+    double kin[4][KIN_TAPS];     // kinetic blocks hh, hg, gh, gg
+    double kin_scale;            // -1 / (2 h^2)
+    int64_t box_stride;          // elements of one function's box (8 types)
+    int max_rows_L, max_rows_P;  // largest ny * nz of L and of L' boxes in the batch
+    int64_t max_vol;             // largest E volume in the batch
+    int* status;
+    int64_t qtab_n, seg_n, rowptr_n, vec_n, dst_n;
+    int n_sf, n_atoms;
+};
+cudaError_t conf_apply(const ConfLaunch& a, const void* vin, void* box_in, void* box_out, void* box_tmp, void* dst,
+                       int region, int accumulate, bool precond, double* energy, cudaStream_t s);
+cudaError_t conf_cg_init(const ConfLaunch& a, const void* g, void* x, void* r, void* p, cudaStream_t s);
+cudaError_t conf_dot(const ConfLaunch& a, const void* x, const void* y, double* out, cudaStream_t s);
+cudaError_t conf_cg_step1(const ConfLaunch& a, const double* rr, const double* pAp, const void* p, const void* Ap, void* x,
+                          void* r, cudaStream_t s);
+cudaError_t conf_cg_step2(const ConfLaunch& a, double* rr, const double* rr_new, const void* r, void* p, double* res,
+                          cudaStream_t s);
+
 // Fixed device scratch of the allocation-free Hamiltonian entry point (lsw_kernels.cu).
 constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(32) << 20;   // 32 MiB
 constexpr int NOALLOC_MAX_DEVICES = 64;

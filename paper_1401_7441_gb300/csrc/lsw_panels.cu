@@ -87,10 +87,10 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
         sgc_n = a.seg_n - segc;
         sgf_n = a.seg_n - segf;
     }
-    const T* src = static_cast<const T*>(side ? a.hphi : a.phi);
+    const T* __restrict__ src = static_cast<const T*>(side ? a.hphi : a.phi);
     const int64_t src_n = side ? a.hphi_n : a.phi_n;
     const int64_t* offs = side ? a.off_Lp : a.off_L;
-    T* dst = static_cast<T*>(side ? a.PQ : a.PA);
+    T* __restrict__ dst = static_cast<T*>(side ? a.PQ : a.PA);
     const int64_t dst_n = side ? a.PQ_n : a.PA_n;
     (void)dst;
     (void)src_n;
@@ -149,10 +149,17 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
                         ST(out, o + rel, a.out_n, LD(static_cast<const T*>(a.PQ), base + static_cast<int64_t>(j) * kp + k, a.PQ_n));
                     }
             } else {
-                for (int j = 0; j < pa.nsf; ++j) {
-                    const int64_t o = LD(offs, pa.f0 + j, a.n_sf + 1);
-                    const T v = rel >= 0 ? LD(src, o + rel, src_n) : T(0);
-                    ST(dst, base + static_cast<int64_t>(j) * kp + k, dst_n, v);
+                // the atom's functions four at a time: every load issued before the stores
+                for (int j0 = 0; j0 < pa.nsf; j0 += 4) {
+                    T v[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        v[j] = T(0);
+                        if (rel >= 0 && j0 + j < pa.nsf) v[j] = LD(src, LD(offs, pa.f0 + j0 + j, a.n_sf + 1) + rel, src_n);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (j0 + j < pa.nsf) ST(dst, base + static_cast<int64_t>(j0 + j) * kp + k, dst_n, v[j]);
                 }
             }
         }
@@ -258,24 +265,58 @@ __global__ void __launch_bounds__(256) k_panel_hs(PanelHSLaunch a) {
         __syncthreads();
         if (k0 + PH_KC < kp) fetch(k0 + PH_KC);         // next chunk in flight during the products
         const int kn = min(PH_KC, kp - k0);
-        for (int k = 0; k < kn; ++k) {
-            T av[4], cv[8];
+#ifndef LSW_CHECKED
+        if constexpr (sizeof(T) == 4) {
+            // 16-byte shared loads (the 4 rows and 2 x 4 columns of this thread) and packed
+            // two-lane FMAs (each lane one FMA rounded to nearest: the same bits as below)
+            for (int k = 0; k < kn; ++k) {
+                const float4 a4 = *reinterpret_cast<const float4*>(sA + k * PH_LDA + 4 * ti);
+                const float4 c4 = *reinterpret_cast<const float4*>(sC + k * PH_LDC + 4 * tj);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+                if (wide) {
+                    const float4 d4 = *reinterpret_cast<const float4*>(sC + k * PH_LDC + 64 + 4 * tj);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = LD(sA, k * PH_LDA + 4 * ti + i, SA_N);
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 ai = make_float2(av[i], av[i]);
+                        float2 r0 = __ffma2_rn(ai, make_float2(c4.x, c4.y), make_float2(acc[i][0], acc[i][1]));
+                        float2 r1 = __ffma2_rn(ai, make_float2(c4.z, c4.w), make_float2(acc[i][2], acc[i][3]));
+                        float2 r2 = __ffma2_rn(ai, make_float2(d4.x, d4.y), make_float2(acc[i][4], acc[i][5]));
+                        float2 r3 = __ffma2_rn(ai, make_float2(d4.z, d4.w), make_float2(acc[i][6], acc[i][7]));
+                        acc[i][0] = r0.x, acc[i][1] = r0.y, acc[i][2] = r1.x, acc[i][3] = r1.y;
+                        acc[i][4] = r2.x, acc[i][5] = r2.y, acc[i][6] = r3.x, acc[i][7] = r3.y;
+                    }
+                } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) cv[j] = LD(sC, k * PH_LDC + 4 * tj + j, SC_N);
-            if (wide) {
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 ai = make_float2(av[i], av[i]);
+                        float2 r0 = __ffma2_rn(ai, make_float2(c4.x, c4.y), make_float2(acc[i][0], acc[i][1]));
+                        float2 r1 = __ffma2_rn(ai, make_float2(c4.z, c4.w), make_float2(acc[i][2], acc[i][3]));
+                        acc[i][0] = r0.x, acc[i][1] = r0.y, acc[i][2] = r1.x, acc[i][3] = r1.y;
+                    }
+                }
+            }
+        } else
+#endif
+        {
+            for (int k = 0; k < kn; ++k) {
+                T av[4], cv[8];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) cv[4 + j] = LD(sC, k * PH_LDC + 64 + 4 * tj + j, SC_N);
+                for (int i = 0; i < 4; ++i) av[i] = LD(sA, k * PH_LDA + 4 * ti + i, SA_N);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) cv[j] = LD(sC, k * PH_LDC + 4 * tj + j, SC_N);
+                if (wide) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
-            } else {
+                    for (int j = 0; j < 4; ++j) cv[4 + j] = LD(sC, k * PH_LDC + 64 + 4 * tj + j, SC_N);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
+                }
             }
         }
         __syncthreads();

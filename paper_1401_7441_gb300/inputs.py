@@ -337,11 +337,14 @@ def phi_values(wl: Workload, f: int, atom: int, g_coarse, g_fine, xp=np, device=
     return v / xp.sqrt(xp.sum(v * v))
 
 
-def fill_phi(wl: Workload, phi, off_L, sf_atom, coarse_g, fine_g, chunk_coefs=1 << 25):
+def fill_phi(wl: Workload, phi, off_L, sf_atom, coarse_g, fine_g, chunk_coefs=1 << 25, fn_ids=None):
     """Write every support function's compressed coefficients into the torch tensor
     ``phi`` (layout ``off_L``) in a few large vectorized passes, with the same values
     as ``phi_values`` for each function.  ``coarse_g[a]`` / ``fine_g[a]`` are the grid
-    indices of atom a's coarse and fine members (layout order)."""
+    indices of atom a's coarse and fine members (layout order).  ``fn_ids`` (optional):
+    the workload's function number of each entry (a sub-system's functions keep the
+    content of their function in the whole system; ``sf_atom`` then holds the whole
+    system's atoms)."""
     import torch
     dev = phi.device
     N = wl.N
@@ -392,7 +395,8 @@ def fill_phi(wl: Workload, phi, off_L, sf_atom, coarse_g, fine_g, chunk_coefs=1 
         gidx = torch.where(is_c, torch.repeat_interleave(oc_a, cnt) + j, torch.repeat_interleave(of_a, cnt) + j)
         g = torch.where(is_c, GC[torch.clamp(gidx, max=max(0, GC.numel() - 1))],
                         GF[torch.clamp(gidx, max=max(0, GF.numel() - 1))] if GF.numel() else torch.zeros_like(gidx))
-        z = counter_normal(wl.seed, fid, t, g, xp=torch)
+        fg_ = fid if fn_ids is None else torch.as_tensor(np.asarray(fn_ids, np.int64), device=dev)[fid]
+        z = counter_normal(wl.seed, fg_, t, g, xp=torch)
         c = pos[atom_r]
         x = (g % N[0]).to(torch.float64) * h - c[:, 0]
         y = ((g // N[0]) % N[1]).to(torch.float64) * h - c[:, 1]

@@ -70,6 +70,9 @@ _SIGS = {
     "lsw_apply_hamiltonian_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "lsw_combine": (C.c_int, [_P, _P, _P, _P]),
     "lsw_lowdin_taylor": (C.c_int, [_P, _P, _P, _P]),
+    "lsw_add_confinement": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lsw_confinement_row": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64, _DP]),
+    "lsw_precondition": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, _P]),
     "lsw_foe": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double,
                           C.c_int32, _P, _P, _DP, _DP, _DP]),
     "lsw_reformat": (C.c_int, [_P, _P, _I32P, _P, _P]),
@@ -210,6 +213,23 @@ def lsw_foe(sys, H, S, e_min, e_max, n_el, n_pl, de, Kp, K, tol=1e-10, max_bisec
     check(lib().lsw_foe(sys, _ptr(H), _ptr(S), e_min, e_max, n_el, n_pl, de, tol, max_bisect, _ptr(Kp), _ptr(K),
                         C.byref(mu), C.byref(ebs), C.byref(tr)))
     return mu.value, ebs.value, tr.value
+
+
+def lsw_add_confinement(sys, a, phi, hphi, e_conf=None):
+    """hphi += L' a Q L phi (quartic confinement of each function's atom); e_conf = <phi|aQ|phi>."""
+    check(lib().lsw_add_confinement(sys, _ptr(a), _ptr(phi), _ptr(hphi), _ptr(e_conf)))
+
+
+def lsw_confinement_row(sys, atom, dim, m, b, bp, i):
+    """Entries <chi^b_i|(x_dim - R_dim)^m|chi^b'_{i+l}>, l = -14..14 (host)."""
+    out = np.zeros(29)
+    check(lib().lsw_confinement_row(sys, atom, dim, m, b, bp, int(i), out.ctypes.data_as(_DP)))
+    return out
+
+
+def lsw_precondition(sys, a, eps, g, gprec, iters, res=None):
+    """CG on L (-1/2 nabla^2 + a (r - R)^4 - eps) L gprec = -g, ``iters`` iterations per function."""
+    check(lib().lsw_precondition(sys, _ptr(a), _ptr(eps), _ptr(g), _ptr(gprec), int(iters), _ptr(res)))
 
 
 def lsw_apply_hamiltonian_noalloc(sys, phi, hphi, e_kin=None, e_pot=None):

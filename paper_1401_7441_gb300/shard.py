@@ -88,15 +88,18 @@ def exchange(buffers, offsets, plan, group=None):
             p += e - s
 
 
-def subsystem(wl, owner, rank, sf_atom, row_ptr, col):
+def subsystem(wl, owner, rank, sf_atom, row_ptr, col, own_first=False):
     """The atoms a rank hands to the library for its share of a sharded run.
 
     Its own atoms, the atoms of the functions its rows reach (the halo), and ghost atoms
     (no support functions) whose fine spheres can reach the L' region of an own atom, so
     that the fine region -- the union of every atom's fine sphere -- is the same as the
     whole system's wherever an own function lives.  The grid, the potential's wells and
-    every radius are the whole system's.  Returns (workload, global atom of each
-    sub-system atom, global function of each sub-system function)."""
+    every radius are the whole system's.  With ``own_first`` the own atoms come first (so
+    the own functions are the sub-system's first functions, the ones the library's
+    "hphi_limit" option selects), then the others, each group in global order.  Returns
+    (workload, global atom of each sub-system atom, global function of each sub-system
+    function)."""
     import copy
     pos = np.asarray(wl.pos, np.float64)
     owner = np.asarray(owner, np.int64)
@@ -113,6 +116,9 @@ def subsystem(wl, owner, rank, sf_atom, row_ptr, col):
     d2 = np.sum((pos[None, :, :] - pos[own_atoms][:, None, :]) ** 2, axis=2)
     ghosts = set(np.nonzero(np.any(d2 <= (reach[:, None]) ** 2, axis=0))[0].tolist())
     keep = sorted(set(own_atoms.tolist()) | halo_atoms | ghosts)
+    if own_first:
+        own_set = set(own_atoms.tolist())
+        keep = sorted(own_set) + [a for a in keep if a not in own_set]
     with_fns = set(own_atoms.tolist()) | halo_atoms
     nsf = np.asarray(wl.nsf, np.int64)
     sub_nsf = np.array([nsf[a] if a in with_fns else 0 for a in keep], np.int64)
@@ -126,6 +132,36 @@ def subsystem(wl, owner, rank, sf_atom, row_ptr, col):
     w.r_fine = np.asarray(wl.r_fine)[keep]
     w.nsf = sub_nsf
     return w, np.asarray(keep, np.int64), fn_map.astype(np.int64)
+
+
+def exchange_local(buffers, offsets, g2l, plan, group=None):
+    """The halo exchange of ``exchange`` between ranks whose buffers use their own
+    sub-system layouts: ``offsets`` (per buffer, n_local + 1) and ``g2l`` (dict: global
+    function -> local function) of this rank.  Function f occupies the same number of
+    elements on every rank that holds it (its keys are the same), so each range is sent
+    from the owner's layout and written at the receiver's."""
+    import torch
+    import torch.distributed as dist
+    send, recv = plan
+    reqs, inbox = [], []
+    for r, fs in recv.items():
+        for bi, (buf, off) in enumerate(zip(buffers, offsets)):
+            rg = [(int(off[g2l[f]]), int(off[g2l[f] + 1])) for f in fs]
+            t = torch.empty(sum(e - b for b, e in rg), dtype=buf.dtype, device=buf.device)
+            reqs.append(dist.irecv(t, src=r, group=group, tag=bi))
+            inbox.append((buf, rg, t))
+    for r, fs in send.items():
+        for bi, (buf, off) in enumerate(zip(buffers, offsets)):
+            rg = [(int(off[g2l[f]]), int(off[g2l[f] + 1])) for f in fs]
+            t = torch.cat([buf[b:e] for b, e in rg]) if rg else buf[:0].clone()
+            reqs.append(dist.isend(t.contiguous(), dst=r, group=group, tag=bi))
+    for q in reqs:
+        q.wait()
+    for buf, rg, t in inbox:
+        p = 0
+        for b, e in rg:
+            buf[b:e] = t[p:p + (e - b)]
+            p += e - b
 
 
 def cell_weights(blocks_lo, blocks_hi, dims, symmetric=True):

@@ -163,3 +163,26 @@ def test_checkpoint_description_roundtrip(ctx, tmp_path):
     with pytest.raises(lsw.LswError) as e:
         lsw.lsw_load(ctx, str(tmp_path / "missing.lsw"))
     assert e.value.status == lsw.LSW_ERR_IO
+
+
+def test_confinement_rows_equal_oracle_blocks(ctx):
+    # the library's 1D operator entries of (x - R)^m (m = 2, 4) between scaling and
+    # wavelet functions, from its own moment overlaps, against the oracle's blocks
+    from oracle import confinement as Q
+    wl = I.scaled("atoms64", 4, seed=3)
+    S = host_system(wl, ctx)
+    ft = F.load()
+    cols = np.arange(-4, 60)
+    for atom in range(2):
+        for dim in range(3):
+            c = wl.pos[atom][dim] / wl.h
+            for m in (2, 4):
+                for b in (0, 1):
+                    for bp in (0, 1):
+                        idx = np.arange(10, 40, 3)
+                        ref = Q.quartic_block_1d(m, b, bp, idx, cols, c, wl.h, ft)
+                        for ii, i in enumerate(idx):
+                            row = lsw.lsw_confinement_row(S.sys, atom, dim, m, b, bp, int(i))
+                            r2 = ref[ii, np.searchsorted(cols, i + np.arange(-14, 15))]
+                            assert np.max(np.abs(row - r2)) <= 1e-13 * np.max(np.abs(r2)), (atom, dim, m, b, bp, i)
+    S.close()

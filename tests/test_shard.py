@@ -253,3 +253,67 @@ def test_cell_partition_balances_the_density_work_of_a_workload():
     finally:
         S.close()
         lsw.lsw_ctx_destroy(ctx)
+
+
+def _worker_local(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1401_7441_gb300 import inputs as I_
+    from paper_1401_7441_gb300 import lsw as L_
+    from paper_1401_7441_gb300 import shard as SH
+    from tests.lib_support import host_system as hs
+    from tests.lib_support import keys_to_g
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
+    try:
+        wl = I_.scaled("atoms64", 10, seed=6)
+        ctx = L_.lsw_ctx_create(L_.LSW_HOST_ONLY)
+        W = hs(wl, ctx)
+        owner = SH.partition_atoms(wl.pos, wl.nsf, world)
+        plan = SH.halo_plan(W.row_ptr, W.col, W.sf_atom, owner, rank)
+        w, amap, fmap = SH.subsystem(wl, owner, rank, W.sf_atom, W.row_ptr, W.col, own_first=True)
+        R = hs(w, ctx)
+        n_own = int(np.sum(owner[W.sf_atom] == rank))
+        g2l = {int(g): k for k, g in enumerate(fmap)}
+        phi = torch.full((R.total_L,), float("nan"), dtype=torch.float64)
+        for k in range(n_own):                                 # own functions only
+            a = int(R.sf_atom[k])
+            v = I_.phi_values(wl, int(fmap[k]), int(amap[a]), keys_to_g(R.keys(a, 0, 0)), keys_to_g(R.keys(a, 0, 1)))
+            phi[R.off_L[k]:R.off_L[k] + len(v)] = torch.from_numpy(v)
+        SH.exchange_local([phi], [R.off_L], g2l, plan)
+        bad = 0
+        for k in range(n_own, R.n_sf):                         # the halo arrived at this rank's offsets
+            a = int(R.sf_atom[k])
+            v = I_.phi_values(wl, int(fmap[k]), int(amap[a]), keys_to_g(R.keys(a, 0, 0)), keys_to_g(R.keys(a, 0, 1)))
+            if not np.array_equal(phi[R.off_L[k]:R.off_L[k] + len(v)].numpy(), v):
+                bad += 1
+        q.put(("ok", rank, bad, R.n_sf - n_own))
+        R.close()
+        W.close()
+        L_.lsw_ctx_destroy(ctx)
+    except Exception as e:
+        q.put(("error", rank, repr(e), 0))
+        raise
+    finally:
+        dist.destroy_process_group()
+
+
+def test_exchange_between_subsystem_layouts_gloo():
+    # the exchange of the sharded benchmark: each rank holds its own sub-system layout
+    # (own functions first); halo functions arrive from their owners at the local offsets
+    import torch.multiprocessing as mp
+    ensure_built()
+    ctx = mp.get_context("spawn")
+    qu = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_local, args=(r, 2, port, qu)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [qu.get(timeout=600) for _ in range(2)]
+    for p in procs:
+        p.join(120)
+    assert all(r[0] == "ok" for r in res), res
+    assert all(p.exitcode == 0 for p in procs)
+    for _, rank, bad, n_halo in res:
+        assert n_halo > 0 and bad == 0, (rank, bad, n_halo)
