@@ -92,9 +92,10 @@ def subsystem(wl, owner, rank, sf_atom, row_ptr, col, own_first=False):
     """The atoms a rank hands to the library for its share of a sharded run.
 
     Its own atoms, the atoms of the functions its rows reach (the halo), and ghost atoms
-    (no support functions) whose fine spheres can reach the L' region of an own atom, so
-    that the fine region -- the union of every atom's fine sphere -- is the same as the
-    whole system's wherever an own function lives.  The grid, the potential's wells and
+    (no support functions) whose fine spheres can reach the L' region of an own or halo
+    atom, so that the fine region -- the union of every atom's fine sphere -- is the same
+    as the whole system's wherever a function of the sub-system lives (its keys, layout
+    and results are the whole system's).  The grid, the potential's wells and
     every radius are the whole system's.  With ``own_first`` the own atoms come first (so
     the own functions are the sub-system's first functions, the ones the library's
     "hphi_limit" option selects), then the others, each group in global order.  Returns
@@ -110,10 +111,13 @@ def subsystem(wl, owner, rank, sf_atom, row_ptr, col, own_first=False):
     halo_atoms = set()
     for a in np.nonzero(owner[sf_atom] == rank)[0]:
         halo_atoms.update(int(sf_atom[b]) for b in col[row_ptr[a]:row_ptr[a + 1]])
-    # L' radius plus the largest fine radius, with a grid diagonal of slack: an extra ghost
-    # only repeats fine points the whole system has anyway
-    reach = np.asarray(wl.r_loc)[own_atoms] + wl.lprime_margin * wl.h + np.max(wl.r_fine) + 2.0 * wl.h
-    d2 = np.sum((pos[None, :, :] - pos[own_atoms][:, None, :]) ** 2, axis=2)
+    # L' radius plus the largest fine radius, with a grid diagonal of slack, around every
+    # atom with functions here (own and halo): the regions of the halo functions are then
+    # the whole system's too, so their phi and H phi have the owner's layout; an extra
+    # ghost only repeats fine points the whole system has anyway
+    fn_atoms = np.array(sorted(set(own_atoms.tolist()) | halo_atoms), np.int64)
+    reach = np.asarray(wl.r_loc)[fn_atoms] + wl.lprime_margin * wl.h + np.max(wl.r_fine) + 2.0 * wl.h
+    d2 = np.sum((pos[None, :, :] - pos[fn_atoms][:, None, :]) ** 2, axis=2)
     ghosts = set(np.nonzero(np.any(d2 <= (reach[:, None]) ** 2, axis=0))[0].tolist())
     keep = sorted(set(own_atoms.tolist()) | halo_atoms | ghosts)
     if own_first:

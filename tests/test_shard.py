@@ -161,9 +161,9 @@ def test_sharded_rows_equal_single_process_gloo():
 @pytest.mark.parametrize("name,world", [("atoms64", 2), ("atoms64", 3), ("atoms1200_small", 2),
                                         ("atoms64_cutoff8", 2)])
 def test_subsystem_reproduces_the_owned_functions(name, world):
-    # through the library (host-only): in each rank's sub-system every own function has
-    # the same L and L' keys and offsets as in the whole system, and its pattern row maps
-    # onto the whole system's row.  With an 8 bohr pair cutoff the halo alone misses atoms
+    # through the library (host-only): in each rank's sub-system every own and halo
+    # function has the same L and L' keys and lengths as in the whole system, and every
+    # own function's pattern row maps onto the whole system's row.  With an 8 bohr pair cutoff the halo alone misses atoms
     # whose fine spheres reach L' (R + 8h + r_f = 11.6 bohr): the ghost atoms keep those
     # fine points (without them 82 fine key sets of own functions differ)
     ensure_built()
@@ -183,15 +183,18 @@ def test_subsystem_reproduces_the_owned_functions(name, world):
                 assert T.n_sf == len(fmap)
                 for fs in range(T.n_sf):
                     f = int(fmap[fs])
-                    if fown[f] != r:
-                        continue
-                    covered.add(f)
                     a, asub = int(S.sf_atom[f]), int(T.sf_atom[fs])
                     assert amap[asub] == a
+                    # own and halo functions alike: the whole system's regions and lengths
+                    # (the halo's phi and H phi arrive in the owner's layout)
                     for region in (lsw.LSW_REGION_L, lsw.LSW_REGION_LP):
                         for part in (lsw.LSW_PART_COARSE, lsw.LSW_PART_FINE):
                             assert np.array_equal(S.keys(a, region, part), T.keys(asub, region, part)), (f, region, part)
                     assert S.off_L[f + 1] - S.off_L[f] == T.off_L[fs + 1] - T.off_L[fs]
+                    assert S.off_Lp[f + 1] - S.off_Lp[f] == T.off_Lp[fs + 1] - T.off_Lp[fs]
+                    if fown[f] != r:
+                        continue
+                    covered.add(f)
                     row = fmap[T.col[T.row_ptr[fs]:T.row_ptr[fs + 1]]]
                     assert np.array_equal(np.sort(row), S.col[S.row_ptr[f]:S.row_ptr[f + 1]])
             finally:
