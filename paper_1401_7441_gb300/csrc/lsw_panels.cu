@@ -27,7 +27,7 @@ namespace lsw {
 
 // ---------------------------------------------------------------- pack
 
-constexpr int PK_THREADS = 256;
+constexpr int PK_THREADS = 512;   // 16 warps: many tiles' loads in flight per CTA
 
 template <class T, bool Unpack>
 __global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(256) k_panel_hs(PanelHSLaunch a) {
         if constexpr (sizeof(T) == 4) {
             // 16-byte shared loads (the 4 rows and 2 x 4 columns of this thread) and packed
             // two-lane FMAs (each lane one FMA rounded to nearest: the same bits as below)
+#pragma unroll 4
             for (int k = 0; k < kn; ++k) {
                 const float4 a4 = *reinterpret_cast<const float4*>(sA + k * PH_LDA + 4 * ti);
                 const float4 c4 = *reinterpret_cast<const float4*>(sC + k * PH_LDC + 4 * tj);
