@@ -418,6 +418,9 @@ lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev);
 
 /* Tuning knob by name: "batch" (functions per HPhi batch), "graph" (0/1, capture the
  * enqueued work in a CUDA graph), "tile" (H/S tile edge, coarse points, 2..8),
+ * "hs_tc" (FP32 and split-bfloat16 systems: 1, the default, runs the per-tile H/S products
+ * as split-bfloat16 tensor-core products, 3 parts per FP32 value and 6 products, FP32
+ * accumulation in tensor memory; 0 runs them on the FMA units),
  * "hphi_limit" (lsw_apply_hamiltonian computes H phi and the energies of functions
  * 0 .. value - 1 only, leaving the others' outputs untouched; -1, the default: every
  * function; a rank of a sharded run numbers its own functions first),

@@ -1,5 +1,6 @@
-"""Autotuner for the library's launch shapes: functions per H phi batch ("batch") and
-the H/S tile edge ("tile").
+"""Autotuner for the library's launch shapes: functions per H phi batch ("batch"), the
+plane kernels of split-bfloat16 systems on the FMA units or the tensor cores ("xy_tc"),
+and the H/S tile edge ("tile").
 
 Each candidate is set through lsw_set_option, warmed once, then timed with CUDA events
 on the system's stream; the fastest is kept.  Everything runs in the library's kernels;
@@ -10,8 +11,8 @@ from __future__ import annotations
 
 from . import lsw
 
-BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512)
-TILE_CANDIDATES = (3, 4, 5, 6, 8)
+BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512, 1024, 2048)
+TILE_CANDIDATES = (3, 4, 5, 6, 7, 8)
 
 
 def _time(fn, stream, reps):
@@ -48,6 +49,17 @@ def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDID
         if best_b is None or ms < report["batch"][best_b]:
             best_b = b
     lsw.lsw_set_option(system.sys, "batch", best_b)
+    best_x = 0
+    if system.precision == lsw.LSW_FP32_BF16X:
+        report["xy_tc"] = {0: report["batch"][best_b]}
+        try:
+            lsw.lsw_set_option(system.sys, "xy_tc", 1)
+            report["xy_tc"][1] = _time(lambda: lsw.lsw_apply_hamiltonian(system.sys, phi, hphi, e_kin, e_pot),
+                                       stream, reps)
+            best_x = 1 if report["xy_tc"][1] < report["xy_tc"][0] else 0
+        except lsw.LswError:              # locregs too large for the tensor-core plane tiles
+            pass
+        lsw.lsw_set_option(system.sys, "xy_tc", best_x)
     lsw.lsw_apply_hamiltonian(system.sys, phi, hphi, e_kin, e_pot)
     for t in tiles:
         lsw.lsw_set_option(system.sys, "tile", t)
@@ -56,5 +68,5 @@ def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDID
         if best_t is None or ms < report["tile"][best_t]:
             best_t = t
     lsw.lsw_set_option(system.sys, "tile", best_t)
-    report["chosen"] = {"batch": best_b, "tile": best_t}
+    report["chosen"] = {"batch": best_b, "tile": best_t, "xy_tc": best_x}
     return report

@@ -35,7 +35,7 @@ def sources():
 def build(verbose: bool = False, force: bool = False) -> str:
     """Compile (if stale) and return the path of liblsw.so."""
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, "lsw_internal.h"), os.path.join(CSRC, "lsw_device.h"), os.path.join(ROOT, "include", "lsw.h"),
+    deps = srcs + [os.path.join(CSRC, "lsw_internal.h"), os.path.join(CSRC, "lsw_device.h"), os.path.join(CSRC, "lsw_tc.h"), os.path.join(ROOT, "include", "lsw.h"),
                    os.path.abspath(__file__)]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -212,6 +212,7 @@ struct lsw_system_s {
     int tile = 4;
     int64_t slab_mb = PANEL_SLAB_MB;
     int64_t hphi_limit = -1;         // option "hphi_limit" (-1: every function)
+    int hs_tc = 1;                   // option "hs_tc": FP32 H/S products on the tensor cores
     int use_graph = 1;
     // potential
     const void* V = nullptr;
@@ -962,6 +963,7 @@ PanelHSLaunch product_launch(lsw_system_s* s, Tracer* tr, const PanelSlab& sl, b
     p.PQ_n = static_cast<int64_t>(s->d_PQ.bytes / s->esize);
     p.n_tiles = static_cast<int64_t>(s->d_ptiles.bytes / sizeof(PanelTile));
     p.n_sf = static_cast<int>(s->sf_atom.size());
+    p.tc = (s->prec != LSW_FP64 && s->hs_tc && !combine) ? 1 : 0;
     return p;
 }
 
@@ -2225,6 +2227,13 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         drop_graphs(sys);
         sys->batch_size = static_cast<int>(value);
         return build_plans(sys);
+    }
+    if (std::strcmp(name, "hs_tc") == 0) {
+        if (value != 0 && value != 1) return fail(LSW_ERR_ARG, "lsw_set_option: hs_tc %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        sys->hs_tc = static_cast<int>(value);
+        return LSW_OK;
     }
     if (std::strcmp(name, "hphi_limit") == 0) {
         if (value < -1 || value > static_cast<int64_t>(sys->sf_atom.size()))

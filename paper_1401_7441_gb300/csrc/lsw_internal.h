@@ -240,6 +240,7 @@ struct PanelHSLaunch {
     double* H;
     double* S;
     const double* M;             // combination: coefficients on the pattern
+    int tc;                      // 1: FP32 products on the tensor cores (split bfloat16)
     int* status;
     int64_t listA_n, listB_n, nnz, PA_n, PQ_n, n_tiles;
     int n_sf;

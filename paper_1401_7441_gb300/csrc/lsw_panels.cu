@@ -22,6 +22,7 @@
 
 #include "lsw_device.h"
 #include "lsw_internal.h"
+#include "lsw_tc.h"
 
 namespace lsw {
 
@@ -381,6 +382,198 @@ __global__ void __launch_bounds__(256) k_panel_hs(PanelHSLaunch a) {
     }
 }
 
+// ---------------------------------------------------------------- products on the tensor cores
+
+// k_panel_hs for FP32 panels on the tensor cores: per work item (tile, up to 64 A rows,
+// up to 128 columns of [A; Q]) the product D[c][a] = sum_k C[c][k] A[a][k] (C the [A; Q]
+// rows, A the item's A rows) runs as tcgen05.mma kind::f16 with M = 128 (the C rows), N
+// = the A rows rounded up to 16, K = 16 per instruction, from split-bfloat16 operands:
+// each FP32 panel value is split into 3 bfloat16 parts (each part the rounding of what
+// the previous ones leave) and the 6 products of parts whose orders add up to at most 2
+// are accumulated in FP32 in tensor memory (relative error of a product about 2^-24, the
+// level of FP32 rounding).  The panel rows are K-major, the layout the instruction reads:
+// thread t converts (row, 8 panel entries) units straight into the canonical core-matrix
+// layout.  Two operand buffers alternate, so the conversion of one chunk of 32 entries
+// overlaps the products of the previous one.  Waits on MMA completion are bounded (about
+// 1 s) and end in a status bit.  The epilogue reads D from tensor memory (thread (warp w,
+// lane l): row c = 32 (w mod 4) + l, columns half w / 4) and adds each pattern entry as
+// in k_panel_hs.
+constexpr int PT_M = 128, PT_N = 64, PT_KC = 32, PT_NS = 3;
+constexpr int PT_APART = PT_M * PT_KC * 2;                 // bytes of one bfloat16 part of the C operand
+constexpr int PT_BPART = PT_N * PT_KC * 2;                 // ... of the A operand
+constexpr int PT_STAGE = PT_NS * (PT_APART + PT_BPART);    // one buffer
+constexpr int PT_SMEM = tc::HEAD + 2 * PT_STAGE;
+
+__global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 21;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PanelItem it = LD(a.items, blockIdx.x, a.nitems);
+    const PanelTile tl = LD(a.tiles, it.tile, a.n_tiles);
+    const int kp = tl.kp;
+    const int nN = (it.na + 15) & ~15;                      // MMA N (A rows, padded)
+    const float* PA = static_cast<const float*>(a.PA);
+    const float* PQ = static_cast<const float*>(a.PQ);
+    const uint32_t mb0 = tc::saddr(smem_raw), mb1 = tc::saddr(smem_raw + 8);
+    if (warp == 0) tc::tmem_alloc(tc::saddr(smem_raw + 16), PT_N);
+    if (tid == 32) {
+        tc::mbar_init(mb0);
+        tc::mbar_init(mb1);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem_raw + 16);
+    unsigned char* stage[2] = {smem_raw + tc::HEAD, smem_raw + tc::HEAD + PT_STAGE};
+    const int64_t room = PT_SMEM;
+    const uint32_t id = tc::idesc(PT_M, nN);
+    const int nch = (kp + PT_KC - 1) / PT_KC;
+    bool ok = true;
+    uint32_t phase[2] = {0, 0};
+    for (int ch = 0; ch < nch && ok; ++ch) {
+        const int s = ch & 1;
+        if (ch >= 2) {   // the products that read this buffer (chunk ch - 2) are done
+            ok = tc::mbar_wait(s ? mb1 : mb0, phase[s]);
+            phase[s] ^= 1;
+            if (!__syncthreads_and(ok)) break;
+            tc::fence_after();
+        }
+        unsigned char* sA = stage[s];                        // C rows: M operand
+        unsigned char* sB = stage[s] + PT_NS * PT_APART;     // A rows: N operand
+        const int k0 = ch * PT_KC;
+        // 128 C rows x 4 groups of 8 entries, then 64 A rows x 4 groups
+        for (int u = tid; u < (PT_M + PT_N) * (PT_KC / 8); u += blockDim.x) {
+            const bool isC = u < PT_M * (PT_KC / 8);
+            const int uu = isC ? u : u - PT_M * (PT_KC / 8);
+            const int row = uu >> 2, g = uu & 3;
+            const int k = k0 + 8 * g;
+            float x[8];
+            bool have = k < kp;
+            const float* src = nullptr;
+            int64_t off = 0, n = 0;
+            if (isC) {
+                const int cc = it.c0 + row;
+                have = have && row < it.nc;
+                if (cc < tl.nA) src = PA, off = tl.pA + static_cast<int64_t>(cc) * kp, n = a.PA_n;
+                else src = PQ, off = tl.pQ + static_cast<int64_t>(cc - tl.nA) * kp, n = a.PQ_n;
+            } else {
+                have = have && row < it.na;
+                src = PA, off = tl.pA + static_cast<int64_t>(it.a0 + row) * kp, n = a.PA_n;
+            }
+            if (have) {
+                Quad<float> q0, q1;
+                ld4(q0, src, off + k, n, ST_, KID);
+                if (k + 4 < kp) ld4(q1, src, off + k + 4, n, ST_, KID);
+                else q1.zero();
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[e] = q0[e], x[4 + e] = q1[e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = 0.f;
+            }
+            if (isC) tc::put8<PT_NS>(sA, PT_APART, tc::core_off(row, 8 * g, PT_KC), x, ST_, room - (sA - smem_raw));
+            else tc::put8<PT_NS>(sB, PT_BPART, tc::core_off(row, 8 * g, PT_KC), x, ST_, room - (sB - smem_raw));
+        }
+        tc::fence_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            for (int kk = 0; kk < PT_KC / 16; ++kk)
+#pragma unroll
+                for (int t = 0; t < tc::Terms<PT_NS>::n; ++t)
+                    tc::mma(tmem, tc::sdesc(tc::saddr(sA + tc::Terms<PT_NS>::b(t) * PT_APART + kk * 256), PT_KC),
+                            tc::sdesc(tc::saddr(sB + tc::Terms<PT_NS>::a(t) * PT_BPART + kk * 256), PT_KC), id,
+                            ch > 0 || kk > 0 || t > 0);
+            tc::commit(s ? mb1 : mb0);
+        }
+    }
+    // the last products (and the one before, on the other buffer)
+    if (ok && nch >= 1) {
+        const int s = (nch - 1) & 1;
+        ok = tc::mbar_wait(s ? mb1 : mb0, phase[s]);
+        phase[s] ^= 1;
+        if (ok && nch >= 2) {
+            ok = tc::mbar_wait(s ? mb0 : mb1, phase[s ^ 1]);
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(a.status, ST_WAIT_TIMEOUT);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (warp == 0) tc::tmem_free(tmem, PT_N);
+        return;
+    }
+    tc::fence_after();
+    // pattern positions: the CSR rows of this item's A functions in the (now free) operand
+    // buffers, rows that do not fit searched in global memory
+    __shared__ int rofs[64 + 1];
+    __shared__ int rlen[64];
+    __shared__ long long rbase[64];
+    int* rcols = reinterpret_cast<int*>(smem_raw + tc::HEAD);
+    const int rcap = 2 * PT_STAGE / static_cast<int>(sizeof(int));
+    if (tid < it.na) {
+        const int fa = LD(a.listA, tl.listA + it.a0 + tid, a.listA_n);
+        const int64_t r0 = LD(a.row_ptr, fa, a.n_sf + 1), r1 = LD(a.row_ptr, fa + 1, a.n_sf + 1);
+        rbase[tid] = r0;
+        rlen[tid] = static_cast<int>(r1 - r0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int o = 0;
+        for (int i = 0; i < it.na; ++i) {
+            rofs[i] = o;
+            if (o + rlen[i] <= rcap) o += rlen[i];
+            else rofs[i] = -1;
+        }
+    }
+    __syncthreads();
+    for (int i = warp; i < it.na; i += blockDim.x >> 5) {
+        if (rofs[i] < 0) continue;
+        for (int k = lane; k < rlen[i]; k += 32) ST(rcols, rofs[i] + k, rcap, LD(a.col, rbase[i] + k, a.nnz));
+    }
+    __syncthreads();
+    const int c = 32 * (warp & 3) + lane;                   // C row of this thread (tensor-memory lane)
+    const int cg = it.c0 + c;
+    const bool c_ok = c < it.nc;
+    const bool isS = cg < tl.nA;
+    const int fb = c_ok ? (isS ? LD(a.listA, tl.listA + cg, a.listA_n) : LD(a.listB, tl.listB + (cg - tl.nA), a.listB_n))
+                        : -1;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    for (int j0 = (warp >> 2) * (PT_N / 2); j0 < (warp >> 2) * (PT_N / 2) + PT_N / 2; j0 += 8) {
+        if (j0 >= nN) break;                                 // warp-uniform
+        float v[8];
+        tc::tmem_ld8(tlane + j0, v);
+        if (!c_ok) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int r = j0 + e;
+            if (r >= it.na || v[e] == 0.f) continue;
+            const int64_t r0 = rbase[r];
+            const int ro = rofs[r];
+            int lo = 0, hi = rlen[r] - 1;
+            int64_t pos = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int cm = ro >= 0 ? LD(rcols, ro + mid, rcap) : LD(a.col, r0 + mid, a.nnz);
+                if (cm == fb) {
+                    pos = r0 + mid;
+                    break;
+                }
+                if (cm < fb) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (pos >= 0) atomicAdd((isS ? a.S : a.H) + pos, static_cast<double>(v[e]));
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_free(tmem, PT_N);
+}
+
 // ---------------------------------------------------------------- sparse combination
 
 // (M Phi)_a = P_L(a) sum_b M_ab phi_b (Sec. "Orthogonalization", Eq. gradient): per work
@@ -509,7 +702,8 @@ cudaError_t configure_panel_kernels(size_t max_smem) {
                         reinterpret_cast<const void*>(k_panel_hs<double>),
                         reinterpret_cast<const void*>(k_panel_hs<float>),
                         reinterpret_cast<const void*>(k_panel_combine<double>),
-                        reinterpret_cast<const void*>(k_panel_combine<float>)};
+                        reinterpret_cast<const void*>(k_panel_combine<float>),
+                        reinterpret_cast<const void*>(k_panel_hs_tc)};
     for (const void* k : ks) {
         cudaFuncAttributes fa;
         if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return e;
@@ -566,6 +760,10 @@ cudaError_t enqueue_lowdin_coeffs(const int64_t* row_ptr, const int32_t* col, co
 cudaError_t enqueue_panel_hs(const PanelHSLaunch& a, cudaStream_t s) {
     if (a.nitems == 0) return cudaSuccess;
     const size_t smem = panel_hs_smem(a.prec);
+    if (a.prec != 0 && a.tc) {
+        TRACED(a.tr, TK_HS, s, (k_panel_hs_tc<<<static_cast<unsigned>(a.nitems), 256, PT_SMEM, s>>>(a)));
+        return cudaGetLastError();
+    }
     if (a.prec == 0)
         TRACED(a.tr, TK_HS, s, (k_panel_hs<double><<<static_cast<unsigned>(a.nitems), 256, smem, s>>>(a)));
     else

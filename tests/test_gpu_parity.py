@@ -361,3 +361,28 @@ def test_fp64_largest_locregs_plane_kernel_without_staging():
     first = np.concatenate([[0], np.cumsum(wl.nsf)])
     fs = sorted({int(first[big[0]]), int(first[big[-1]]), 0})
     _full_size_sampled(wl, lsw.LSW_FP64, {"batch": 8}, fs, fs[:1], 1e-12)
+
+
+@pytest.mark.parametrize("prec", [lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
+def test_hs_tensor_core_products_against_fma_and_oracle(prec):
+    # the per-tile H/S products on the tensor cores (split bfloat16, 3 parts, 6 products)
+    # and on the FMA units: both within the tolerance of the oracle, and close to each
+    # other (FP32 rounding of the per-tile sums), for tile edges 4 and 6
+    wl = I.scaled("atoms64", 8, seed=5)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    n = len(geo.sf_atom)
+    ref = oracle_hphi(wl, geo, range(n), V)
+    for tile in (4, 6):
+        g_tc = gpu_run(wl, phi_fn(wl), prec, options={"tile": tile, "hs_tc": 1})
+        g_fma = gpu_run(wl, phi_fn(wl), prec, options={"tile": tile, "hs_tc": 0})
+        check_rows(wl, geo, g_tc, ref, range(n), 1e-5)
+        check_rows(wl, geo, g_fma, ref, range(n), 1e-5)
+        sd = np.sqrt(np.abs(g_fma["S"][g_fma["row_ptr"][:-1] + np.array(
+            [np.searchsorted(g_fma["col"][g_fma["row_ptr"][i]:g_fma["row_ptr"][i + 1]], i) for i in range(n)])]))
+        rows = np.repeat(np.arange(n), np.diff(g_fma["row_ptr"]))
+        scale = sd[rows] * sd[g_fma["col"]]
+        assert np.max(np.abs(g_tc["S"] - g_fma["S"]) / scale) <= 1e-6, tile
+        hn = np.array([np.linalg.norm(g_fma["hphi"][g_fma["off_Lp"][f]:g_fma["off_Lp"][f + 1]][
+            ~np.isnan(g_fma["hphi"][g_fma["off_Lp"][f]:g_fma["off_Lp"][f + 1]])]) for f in range(n)])
+        assert np.max(np.abs(g_tc["H"] - g_fma["H"]) / (sd[rows] * hn[g_fma["col"]])) <= 1e-6, tile
