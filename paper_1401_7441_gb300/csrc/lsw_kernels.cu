@@ -1261,12 +1261,34 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     }
     if (yhi_ >= 0) {
       if constexpr (NS == 0) {
-        // ---- y pass: columns x', blocks of NB rows b within [ylo, yhi]
+        // ---- y pass: blocks of NB rows b within [ylo, yhi], and per block only the columns
+        //      x' the x pass reads: for a member row b its blocks k = rx0/NB .. rx1/NB read
+        //      x' in [2 (k NB + dx), 2 (k NB + NB - 1 + dx) + 30]
         const int nbb = (yhi_ - ylo_ + NB) / NB;
+        __shared__ int cq0[64], cq1[64], pq[65];
+        if (threadIdx.x < nbb) {
+            const int q = threadIdx.x;
+            int c0 = X, c1 = -1;
+            for (int b = ylo_ + q * NB; b < min(ylo_ + (q + 1) * NB, yhi_ + 1); ++b) {
+                if (rx0[b] < 0) continue;
+                c0 = min(c0, 2 * ((rx0[b] / NB) * NB + dx));
+                c1 = max(c1, 2 * ((rx1[b] / NB) * NB + NB - 1 + dx) + 30);
+            }
+            cq0[q] = max(c0, 0);
+            cq1[q] = min(c1, X - 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            pq[0] = 0;
+            for (int q = 0; q < nbb; ++q) pq[q + 1] = pq[q] + max(0, cq1[q] - cq0[q] + 1);
+        }
+        __syncthreads();
         {
-            const FastDiv fd_X(X);
-            for (int tk = threadIdx.x; tk < X * nbb; tk += blockDim.x) {
-                const int q = fd_X.div(tk), xo = tk - q * X, b0 = ylo_ + q * NB;
+            const int ntk = pq[nbb];
+            for (int tk = threadIdx.x; tk < ntk; tk += blockDim.x) {
+                int q = 0;
+                while (tk >= pq[q + 1]) ++q;
+                const int xo = cq0[q] + (tk - pq[q]), b0 = ylo_ + q * NB;
                 T w[2 * NB + 29], s[NB], d[NB];
                 swin(w, pl, xo, X, 2 * (b0 + dy), Y, smem_n, st);
                 bwd_block<T, NB>(w, s, d);
@@ -1385,24 +1407,32 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             __syncthreads();
             if (threadIdx.x == 0) ntask = 0;
             __syncthreads();
-            // ---- kinetic y arm: (bx, column x'' in [xlo, xhi], block of rows in [ylo, yhi])
-            const int nbyk = (yhi_ - ylo_ + BB) / BB;
+            // ---- kinetic y arm: (bx, column x'' in [xlo, xhi], block of rows): per column only
+            //      the rows whose member range contains it (the rows the compressed write reads)
             const int ncols = xhi - xlo + 1;
             for (int c = threadIdx.x; c < 2 * ncols; c += blockDim.x) {
                 const int bx = c >= ncols, xb = xlo + (c - bx * ncols);
                 const int x = xb + dx;
                 if (x < 0 || x >= nx) continue;
                 if (!colf[bx][x & 127] && !colf[bx + 2][x & 127]) continue;
-                const int base = atomicAdd(&ntask, nbyk);
-                for (int k = 0; k < nbyk; ++k)
-                    if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | k;
+                int yc0 = -1, yc1 = -2;
+                for (int b = ylo_; b <= yhi_; ++b)
+                    if (rx0[b] >= 0 && rx0[b] <= xb && xb <= rx1[b]) {
+                        if (yc0 < 0) yc0 = b;
+                        yc1 = b;
+                    }
+                if (yc0 < 0) continue;
+                const int nk = (yc1 - yc0 + BB) / BB;
+                const int base = atomicAdd(&ntask, nk);
+                for (int k = 0; k < nk; ++k)
+                    if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | (yc0 + k * BB);
             }
             __syncthreads();
             nt = min(ntask, BWD_MAX_TASKS);
             if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
             for (int it = threadIdx.x; it < nt; it += blockDim.x) {
                 const int code = task[it];
-                const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = ylo_ + (code & 4095) * BB;
+                const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = code & 4095;
                 const int x = xb + dx;
                 T k0[KW], k1[KW], o0[BB], o1[BB];
                 swin(k0, Dp, bx * ny * RS + x, RS, b0 + dy - KIN_HALF, ny, dp_n, st);

@@ -390,19 +390,26 @@ __global__ void __launch_bounds__(256) k_panel_hs(PanelHSLaunch a) {
 // = the A rows rounded up to 16, K = 16 per instruction, from split-bfloat16 operands:
 // each FP32 panel value is split into 3 bfloat16 parts (each part the rounding of what
 // the previous ones leave) and the 6 products of parts whose orders add up to at most 2
-// are accumulated in FP32 in tensor memory (relative error of a product about 2^-24, the
-// level of FP32 rounding).  The panel rows are K-major, the layout the instruction reads:
-// thread t converts (row, 8 panel entries) units straight into the canonical core-matrix
-// layout.  Two operand buffers alternate, so the conversion of one chunk of 32 entries
-// overlaps the products of the previous one.  Waits on MMA completion are bounded (about
-// 1 s) and end in a status bit.  The epilogue reads D from tensor memory (thread (warp w,
-// lane l): row c = 32 (w mod 4) + l, columns half w / 4) and adds each pattern entry as
+// are accumulated in FP32 in tensor memory (relative error of a product about 2^-24).
+// The tensor cores' FP32 accumulation rounds each addition (measured: about 3e-6 of a
+// sum of 300 terms when every product goes into one accumulator, biased low), so the
+// leading product (part 0 x part 0) of each chunk of 32 panel entries goes into an
+// accumulator of its own, read into registers after the chunk (2 additions per chunk in
+// tensor memory, the chunks summed in FP32 registers), while the 5 correction products,
+// 2^-8 smaller, share one accumulator over the whole panel row.  The panel rows are
+// K-major, the layout the instruction reads: thread t converts (row, 8 panel entries)
+// units straight into the canonical core-matrix layout.  Two operand buffers (and two
+// leading-product accumulators) alternate, so the conversion of one chunk overlaps the
+// products of the previous one.  Waits on MMA completion are bounded (about 1 s) and end
+// in a status bit.  The epilogue holds, per thread, the sums of its C row c = 32 (w mod
+// 4) + l (warp w, lane l) over half w / 4 of the A rows, and adds each pattern entry as
 // in k_panel_hs.
 constexpr int PT_M = 128, PT_N = 64, PT_KC = 32, PT_NS = 3;
 constexpr int PT_APART = PT_M * PT_KC * 2;                 // bytes of one bfloat16 part of the C operand
 constexpr int PT_BPART = PT_N * PT_KC * 2;                 // ... of the A operand
 constexpr int PT_STAGE = PT_NS * (PT_APART + PT_BPART);    // one buffer
 constexpr int PT_SMEM = tc::HEAD + 2 * PT_STAGE;
+constexpr int PT_TCOLS = 256;                              // tensor memory: lead[2] at 0, 64; corrections at 128
 
 __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
     const float* PA = static_cast<const float*>(a.PA);
     const float* PQ = static_cast<const float*>(a.PQ);
     const uint32_t mb0 = tc::saddr(smem_raw), mb1 = tc::saddr(smem_raw + 8);
-    if (warp == 0) tc::tmem_alloc(tc::saddr(smem_raw + 16), PT_N);
+    if (warp == 0) tc::tmem_alloc(tc::saddr(smem_raw + 16), PT_TCOLS);
     if (tid == 32) {
         tc::mbar_init(mb0);
         tc::mbar_init(mb1);
@@ -429,15 +436,33 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
     const int64_t room = PT_SMEM;
     const uint32_t id = tc::idesc(PT_M, nN);
     const int nch = (kp + PT_KC - 1) / PT_KC;
+    // this thread's tensor-memory lane and columns of the accumulators
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    const int jbase = (warp >> 2) * (PT_N / 2);
+    const bool jlive = jbase < nN;                          // warp-uniform
+    float sum[PT_N / 2];
+#pragma unroll
+    for (int j = 0; j < PT_N / 2; ++j) sum[j] = 0.f;
+    auto read_lead = [&](int sbuf) {                        // sum += leading-product chunk in lead[sbuf]
+        if (!jlive) return;
+#pragma unroll
+        for (int g = 0; g < PT_N / 16; ++g) {
+            float v[8];
+            tc::tmem_ld8(tlane + sbuf * PT_N + jbase + 8 * g, v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sum[8 * g + e] += v[e];
+        }
+    };
     bool ok = true;
     uint32_t phase[2] = {0, 0};
     for (int ch = 0; ch < nch && ok; ++ch) {
         const int s = ch & 1;
-        if (ch >= 2) {   // the products that read this buffer (chunk ch - 2) are done
+        if (ch >= 2) {   // the products of chunk ch - 2 (this buffer, this lead accumulator) are done
             ok = tc::mbar_wait(s ? mb1 : mb0, phase[s]);
             phase[s] ^= 1;
             if (!__syncthreads_and(ok)) break;
             tc::fence_after();
+            read_lead(s);
         }
         unsigned char* sA = stage[s];                        // C rows: M operand
         unsigned char* sB = stage[s] + PT_NS * PT_APART;     // A rows: N operand
@@ -482,20 +507,26 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
         if (tid == 0) {
             for (int kk = 0; kk < PT_KC / 16; ++kk)
 #pragma unroll
-                for (int t = 0; t < tc::Terms<PT_NS>::n; ++t)
-                    tc::mma(tmem, tc::sdesc(tc::saddr(sA + tc::Terms<PT_NS>::b(t) * PT_APART + kk * 256), PT_KC),
-                            tc::sdesc(tc::saddr(sB + tc::Terms<PT_NS>::a(t) * PT_BPART + kk * 256), PT_KC), id,
-                            ch > 0 || kk > 0 || t > 0);
+                for (int t = 0; t < tc::Terms<PT_NS>::n; ++t) {
+                    const int pa_ = tc::Terms<PT_NS>::b(t), pb_ = tc::Terms<PT_NS>::a(t);
+                    const bool lead = pa_ == 0 && pb_ == 0;
+                    const uint32_t d = tmem + (lead ? static_cast<uint32_t>(s * PT_N) : 2u * PT_N);
+                    tc::mma(d, tc::sdesc(tc::saddr(sA + pa_ * PT_APART + kk * 256), PT_KC),
+                            tc::sdesc(tc::saddr(sB + pb_ * PT_BPART + kk * 256), PT_KC), id,
+                            lead ? kk > 0 : (ch > 0 || kk > 0 || t > 1));
+                }
             tc::commit(s ? mb1 : mb0);
         }
     }
-    // the last products (and the one before, on the other buffer)
-    if (ok && nch >= 1) {
-        const int s = (nch - 1) & 1;
-        ok = tc::mbar_wait(s ? mb1 : mb0, phase[s]);
-        phase[s] ^= 1;
-        if (ok && nch >= 2) {
-            ok = tc::mbar_wait(s ? mb0 : mb1, phase[s ^ 1]);
+    // the last two chunks' products
+    if (ok) {
+        for (int ch = (nch >= 2 ? nch - 2 : 0); ch < nch && ok; ++ch) {
+            const int s = ch & 1;
+            ok = tc::mbar_wait(s ? mb1 : mb0, phase[s]);
+            phase[s] ^= 1;
+            if (!__syncthreads_and(ok)) break;
+            tc::fence_after();
+            read_lead(s);
         }
     }
     if (!__syncthreads_and(ok)) {
@@ -503,10 +534,19 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        if (warp == 0) tc::tmem_free(tmem, PT_N);
+        if (warp == 0) tc::tmem_free(tmem, PT_TCOLS);
         return;
     }
-    tc::fence_after();
+    // the correction products
+    if (jlive) {
+#pragma unroll
+        for (int g = 0; g < PT_N / 16; ++g) {
+            float v[8];
+            tc::tmem_ld8(tlane + 2 * PT_N + jbase + 8 * g, v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sum[8 * g + e] += v[e];
+        }
+    }
     // pattern positions: the CSR rows of this item's A functions in the (now free) operand
     // buffers, rows that do not fit searched in global memory
     __shared__ int rofs[64 + 1];
@@ -537,20 +577,13 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
     __syncthreads();
     const int c = 32 * (warp & 3) + lane;                   // C row of this thread (tensor-memory lane)
     const int cg = it.c0 + c;
-    const bool c_ok = c < it.nc;
-    const bool isS = cg < tl.nA;
-    const int fb = c_ok ? (isS ? LD(a.listA, tl.listA + cg, a.listA_n) : LD(a.listB, tl.listB + (cg - tl.nA), a.listB_n))
-                        : -1;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
-    for (int j0 = (warp >> 2) * (PT_N / 2); j0 < (warp >> 2) * (PT_N / 2) + PT_N / 2; j0 += 8) {
-        if (j0 >= nN) break;                                 // warp-uniform
-        float v[8];
-        tc::tmem_ld8(tlane + j0, v);
-        if (!c_ok) continue;
+    if (jlive && c < it.nc) {
+        const bool isS = cg < tl.nA;
+        const int fb = isS ? LD(a.listA, tl.listA + cg, a.listA_n) : LD(a.listB, tl.listB + (cg - tl.nA), a.listB_n);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int r = j0 + e;
-            if (r >= it.na || v[e] == 0.f) continue;
+        for (int e = 0; e < PT_N / 2; ++e) {
+            const int r = jbase + e;
+            if (r >= it.na || sum[e] == 0.f) continue;
             const int64_t r0 = rbase[r];
             const int ro = rofs[r];
             int lo = 0, hi = rlen[r] - 1;
@@ -565,13 +598,13 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
                 if (cm < fb) lo = mid + 1;
                 else hi = mid - 1;
             }
-            if (pos >= 0) atomicAdd((isS ? a.S : a.H) + pos, static_cast<double>(v[e]));
+            if (pos >= 0) atomicAdd((isS ? a.S : a.H) + pos, static_cast<double>(sum[e]));
         }
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_free(tmem, PT_N);
+    if (warp == 0) tc::tmem_free(tmem, PT_TCOLS);
 }
 
 // ---------------------------------------------------------------- sparse combination
