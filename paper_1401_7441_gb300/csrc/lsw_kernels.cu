@@ -1407,32 +1407,24 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             __syncthreads();
             if (threadIdx.x == 0) ntask = 0;
             __syncthreads();
-            // ---- kinetic y arm: (bx, column x'' in [xlo, xhi], block of rows): per column only
-            //      the rows whose member range contains it (the rows the compressed write reads)
+            // ---- kinetic y arm: (bx, column x'' in [xlo, xhi], block of rows in [ylo, yhi])
+            const int nbyk = (yhi_ - ylo_ + BB) / BB;
             const int ncols = xhi - xlo + 1;
             for (int c = threadIdx.x; c < 2 * ncols; c += blockDim.x) {
                 const int bx = c >= ncols, xb = xlo + (c - bx * ncols);
                 const int x = xb + dx;
                 if (x < 0 || x >= nx) continue;
                 if (!colf[bx][x & 127] && !colf[bx + 2][x & 127]) continue;
-                int yc0 = -1, yc1 = -2;
-                for (int b = ylo_; b <= yhi_; ++b)
-                    if (rx0[b] >= 0 && rx0[b] <= xb && xb <= rx1[b]) {
-                        if (yc0 < 0) yc0 = b;
-                        yc1 = b;
-                    }
-                if (yc0 < 0) continue;
-                const int nk = (yc1 - yc0 + BB) / BB;
-                const int base = atomicAdd(&ntask, nk);
-                for (int k = 0; k < nk; ++k)
-                    if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | (yc0 + k * BB);
+                const int base = atomicAdd(&ntask, nbyk);
+                for (int k = 0; k < nbyk; ++k)
+                    if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | k;
             }
             __syncthreads();
             nt = min(ntask, BWD_MAX_TASKS);
             if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
             for (int it = threadIdx.x; it < nt; it += blockDim.x) {
                 const int code = task[it];
-                const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = code & 4095;
+                const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = ylo_ + (code & 4095) * BB;
                 const int x = xb + dx;
                 T k0[KW], k1[KW], o0[BB], o1[BB];
                 swin(k0, Dp, bx * ny * RS + x, RS, b0 + dy - KIN_HALF, ny, dp_n, st);

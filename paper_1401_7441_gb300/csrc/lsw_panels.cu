@@ -410,6 +410,7 @@ constexpr int PT_BPART = PT_N * PT_KC * 2;                 // ... of the A opera
 constexpr int PT_STAGE = PT_NS * (PT_APART + PT_BPART);    // one buffer
 constexpr int PT_SMEM = tc::HEAD + 2 * PT_STAGE;
 constexpr int PT_TCOLS = 256;                              // tensor memory: lead[2] at 0, 64; corrections at 128
+constexpr int PT_U = (PT_M + PT_N) * (PT_KC / 8) / 256;    // operand units per thread and chunk
 
 __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
@@ -453,6 +454,41 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
             for (int e = 0; e < 8; ++e) sum[8 * g + e] += v[e];
         }
     };
+    // operand units of a chunk: 128 C rows x 4 groups of 8 entries, then 64 A rows x 4
+    // groups; thread t takes units t + 256 m, m < PT_U
+    Quad<float> pre[PT_U][2];
+    auto fetch = [&](int chn) {
+        const int k0 = chn * PT_KC;
+#pragma unroll
+        for (int m = 0; m < PT_U; ++m) {
+            const int u = tid + m * 256;
+            const bool isC = u < PT_M * (PT_KC / 8);
+            const int uu = isC ? u : u - PT_M * (PT_KC / 8);
+            const int row = uu >> 2, g = uu & 3;
+            const int k = k0 + 8 * g;
+            bool have = k < kp;
+            const float* src;
+            int64_t off, n;
+            if (isC) {
+                const int cc = it.c0 + row;
+                have = have && row < it.nc;
+                const bool inA = cc < tl.nA;
+                src = inA ? PA : PQ;
+                off = inA ? tl.pA + static_cast<int64_t>(cc) * kp : tl.pQ + static_cast<int64_t>(cc - tl.nA) * kp;
+                n = inA ? a.PA_n : a.PQ_n;
+            } else {
+                have = have && row < it.na;
+                src = PA;
+                off = tl.pA + static_cast<int64_t>(it.a0 + row) * kp;
+                n = a.PA_n;
+            }
+            if (have) ld4(pre[m][0], src, off + k, n, ST_, KID);
+            else pre[m][0].zero();
+            if (have && k + 4 < kp) ld4(pre[m][1], src, off + k + 4, n, ST_, KID);
+            else pre[m][1].zero();
+        }
+    };
+    fetch(0);
     bool ok = true;
     uint32_t phase[2] = {0, 0};
     for (int ch = 0; ch < nch && ok; ++ch) {
@@ -466,40 +502,21 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
         }
         unsigned char* sA = stage[s];                        // C rows: M operand
         unsigned char* sB = stage[s] + PT_NS * PT_APART;     // A rows: N operand
-        const int k0 = ch * PT_KC;
-        // 128 C rows x 4 groups of 8 entries, then 64 A rows x 4 groups
-        for (int u = tid; u < (PT_M + PT_N) * (PT_KC / 8); u += blockDim.x) {
+        // this chunk's values are in registers (loaded during the previous chunk): split
+        // and store them, then load the next chunk's (in flight during the products)
+#pragma unroll
+        for (int m = 0; m < PT_U; ++m) {
+            const int u = tid + m * 256;
             const bool isC = u < PT_M * (PT_KC / 8);
             const int uu = isC ? u : u - PT_M * (PT_KC / 8);
             const int row = uu >> 2, g = uu & 3;
-            const int k = k0 + 8 * g;
             float x[8];
-            bool have = k < kp;
-            const float* src = nullptr;
-            int64_t off = 0, n = 0;
-            if (isC) {
-                const int cc = it.c0 + row;
-                have = have && row < it.nc;
-                if (cc < tl.nA) src = PA, off = tl.pA + static_cast<int64_t>(cc) * kp, n = a.PA_n;
-                else src = PQ, off = tl.pQ + static_cast<int64_t>(cc - tl.nA) * kp, n = a.PQ_n;
-            } else {
-                have = have && row < it.na;
-                src = PA, off = tl.pA + static_cast<int64_t>(it.a0 + row) * kp, n = a.PA_n;
-            }
-            if (have) {
-                Quad<float> q0, q1;
-                ld4(q0, src, off + k, n, ST_, KID);
-                if (k + 4 < kp) ld4(q1, src, off + k + 4, n, ST_, KID);
-                else q1.zero();
 #pragma unroll
-                for (int e = 0; e < 4; ++e) x[e] = q0[e], x[4 + e] = q1[e];
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = 0.f;
-            }
+            for (int e = 0; e < 4; ++e) x[e] = pre[m][0][e], x[4 + e] = pre[m][1][e];
             if (isC) tc::put8<PT_NS>(sA, PT_APART, tc::core_off(row, 8 * g, PT_KC), x, ST_, room - (sA - smem_raw));
             else tc::put8<PT_NS>(sB, PT_BPART, tc::core_off(row, 8 * g, PT_KC), x, ST_, room - (sB - smem_raw));
         }
+        if (ch + 1 < nch) fetch(ch + 1);
         tc::fence_smem();
         tc::fence_before();
         __syncthreads();
