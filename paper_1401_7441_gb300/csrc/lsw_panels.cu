@@ -31,7 +31,7 @@ namespace lsw {
 constexpr int PK_THREADS = 512;   // 16 warps: many tiles' loads in flight per CTA
 
 template <class T, bool Unpack>
-__global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
+__global__ void __launch_bounds__(PK_THREADS, 2) k_pack(PackLaunch a) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = Unpack ? 12 : 10;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -96,6 +96,9 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
     (void)dst;
     (void)src_n;
     const int TE = a.tile, T2 = TE * TE, T3 = T2 * TE;
+    int64_t of4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) of4[j] = j < pa.nsf ? LD(offs, pa.f0 + j, a.n_sf + 1) : 0;
     // tile-z layers of the box inside the slab; one warp per tile of the box
     const int z0 = max(tlo[2], a.tz0), z1 = min(tlo[2] + tn[2], a.tz1);
     const int nbox = tn[0] * tn[1] * max(0, z1 - z0);
@@ -108,8 +111,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
         const PanelTile tl = LD(a.tiles, ent.x, a.n_tiles);
         const int kp = tl.kp;
         const int64_t base = (side ? tl.pQ : tl.pA) + static_cast<int64_t>(ent.y) * kp;
-        for (int k = lane; k < kp; k += 32) {
-            // offset of this panel entry inside a compressed function of the atom, -1: 0
+        // offset of panel entry k inside a compressed function of the atom (-1: not a member)
+        auto rel_of = [&](int k) -> int64_t {
             int64_t rel = -1;
             int x = 0, y = 0, z = 0, t = 0;
             bool coarse = k < T3, valid = false;
@@ -142,25 +145,39 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack(PackLaunch a) {
                     }
                 }
             }
-            if constexpr (Unpack) {
+            return rel;
+        };
+        if constexpr (Unpack) {
+            for (int k = lane; k < kp; k += 32) {
                 // combination result: panel row of the A side (in the Q buffer) -> members of L
+                const int64_t rel = rel_of(k);
                 if (rel >= 0)
                     for (int j = 0; j < pa.nsf; ++j) {
                         const int64_t o = LD(offs, pa.f0 + j, a.n_sf + 1);
                         ST(out, o + rel, a.out_n, LD(static_cast<const T*>(a.PQ), base + static_cast<int64_t>(j) * kp + k, a.PQ_n));
                     }
-            } else {
-                // the atom's functions four at a time: every load issued before the stores
+            }
+        } else {
+            // 4 entries per lane and 4 functions at a time: 16 loads in flight before the stores
+            for (int kb = lane; kb < kp; kb += 128) {
+                int64_t rel[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) rel[u] = kb + 32 * u < kp ? rel_of(kb + 32 * u) : -1;
                 for (int j0 = 0; j0 < pa.nsf; j0 += 4) {
-                    T v[4];
+                    T v[4][4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        v[j] = T(0);
-                        if (rel >= 0 && j0 + j < pa.nsf) v[j] = LD(src, LD(offs, pa.f0 + j0 + j, a.n_sf + 1) + rel, src_n);
+                        const int64_t o = j0 + j < pa.nsf ? (j0 + j < 4 ? of4[j] : LD(offs, pa.f0 + j0 + j, a.n_sf + 1)) : 0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            v[u][j] = (rel[u] >= 0 && j0 + j < pa.nsf) ? LD(src, o + rel[u], src_n) : T(0);
                     }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (j0 + j < pa.nsf) ST(dst, base + static_cast<int64_t>(j0 + j) * kp + k, dst_n, v[j]);
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (kb + 32 * u < kp && j0 + j < pa.nsf)
+                                ST(dst, base + static_cast<int64_t>(j0 + j) * kp + kb + 32 * u, dst_n, v[u][j]);
                 }
             }
         }
