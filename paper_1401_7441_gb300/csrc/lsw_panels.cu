@@ -472,16 +472,25 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
         }
     };
     // operand units of a chunk: 128 C rows x 4 groups of 8 entries, then 64 A rows x 4
-    // groups; thread t takes units t + 256 m, m < PT_U
+    // groups; thread t takes units t + 256 m, m < PT_U.  Unit uu is row (uu & 7) + 8 (uu >>
+    // 5) and group (uu >> 3) & 3, so the 8 threads of a 16-byte store phase write the 8
+    // rows of one core matrix: 128 contiguous bytes, every bank once (with the 4 groups of
+    // a row on consecutive threads, the phase's rows fell 128 bytes apart, on 4 banks)
     Quad<float> pre[PT_U][2];
+    auto unit = [&](int m, bool& isC, int& row, int& g) {
+        const int u = tid + m * 256;
+        isC = u < PT_M * (PT_KC / 8);
+        const int uu = isC ? u : u - PT_M * (PT_KC / 8);
+        row = (uu & 7) + 8 * (uu >> 5);
+        g = (uu >> 3) & 3;
+    };
     auto fetch = [&](int chn) {
         const int k0 = chn * PT_KC;
 #pragma unroll
         for (int m = 0; m < PT_U; ++m) {
-            const int u = tid + m * 256;
-            const bool isC = u < PT_M * (PT_KC / 8);
-            const int uu = isC ? u : u - PT_M * (PT_KC / 8);
-            const int row = uu >> 2, g = uu & 3;
+            bool isC;
+            int row, g;
+            unit(m, isC, row, g);
             const int k = k0 + 8 * g;
             bool have = k < kp;
             const float* src;
@@ -523,10 +532,9 @@ __global__ void __launch_bounds__(256, 2) k_panel_hs_tc(PanelHSLaunch a) {
         // and store them, then load the next chunk's (in flight during the products)
 #pragma unroll
         for (int m = 0; m < PT_U; ++m) {
-            const int u = tid + m * 256;
-            const bool isC = u < PT_M * (PT_KC / 8);
-            const int uu = isC ? u : u - PT_M * (PT_KC / 8);
-            const int row = uu >> 2, g = uu & 3;
+            bool isC;
+            int row, g;
+            unit(m, isC, row, g);
             float x[8];
 #pragma unroll
             for (int e = 0; e < 4; ++e) x[e] = pre[m][0][e], x[4 + e] = pre[m][1][e];
