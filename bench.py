@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--tile", type=int, default=0)
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--set", action="append", default=[], metavar="NAME=VALUE",
+                   help="library option (lsw_set_option), applied after the autotuner; repeatable")
     p.add_argument("--record-traffic", default=None, metavar="CSV",
                    help="write profiles/roofline_traffic.json from an ncu launch list (dram bytes) of a run with "
                         "the given --workload/--precision/--batch, then exit")
@@ -629,6 +631,11 @@ def gpu_main(args):
     if not args.no_autotune and not args.batch and not args.tile:
         from paper_1401_7441_gb300 import autotune
         tune = autotune.autotune(S, phi, hphi, Hm, Sm, ek, ep, stream)
+    set_opts = {}
+    for kv in args.set:
+        k, v = kv.split("=", 1)
+        lsw.lsw_set_option(S.sys, k, int(v))
+        set_opts[k] = int(v)
 
     for _ in range(args.warmup):
         if args.sync_each:
@@ -794,7 +801,8 @@ def gpu_main(args):
                 "parallelism": ("sharded: x slabs, halo exchange of phi and H phi by NCCL send/recv" if sharded
                                 else "replicas" if world > 1 else "single"),
                 "pattern_nnz": nnz,
-                "tuning": {"options": (tune or {}).get("chosen", {"batch": args.batch or None, "tile": args.tile or None}),
+                "tuning": {"options": {**(tune or {}).get("chosen", {"batch": args.batch or None,
+                                                                       "tile": args.tile or None}), **set_opts},
                            "autotune_ms": {k: v for k, v in (tune or {}).items() if k != "chosen"}},
                 "kernels": per_kernel, "kernel_share": kshare, "work_count": wnote,
                 "dense_box_tflop_per_step": {k: v / 1e12 for k, v in dense.items()},

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 from . import lsw
 
-BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512, 1024, 2048)
+BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512, 1024, 2048, 4096)
 TILE_CANDIDATES = (3, 4, 5, 6, 7, 8)
 
 

@@ -187,6 +187,7 @@ struct lsw_system_s {
     std::vector<int32_t> col;
     // device state
     DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
+    DeviceBuf d_plane_items, d_queue;   // plane items of the persistent kernels, their queue counters
     DeviceBuf d_tile_fine, d_listA, d_listB, d_ws, d_status, d_escratch;
     // H/S in the transposed layout: used tiles, per-atom tile tables, product items, the
     // atoms of each slab and the panel buffers of one slab (reused slab after slab)
@@ -213,6 +214,8 @@ struct lsw_system_s {
     int64_t slab_mb = PANEL_SLAB_MB;
     int64_t hphi_limit = -1;         // option "hphi_limit" (-1: every function)
     int hs_tc = 1;                   // option "hs_tc": FP32 H/S products on the tensor cores
+    int persistent = 1;              // option "persistent": FMA plane kernels over item queues
+    int fwd_list = 1;                // option "fwd_list": forward x pass over member blocks only
     int use_graph = 1;
     // potential
     const void* V = nullptr;
@@ -480,6 +483,8 @@ lsw_status build_plans(lsw_system_s* s) {
     }
     s->batches.clear();
     int64_t ws_max = 0;
+    std::vector<int32_t> items;          // plane items of every batch
+    std::vector<int64_t> item_off;       // per batch: first item, -1 without items
     // option "hphi_limit": H phi only for functions 0 .. limit - 1 (a rank of a sharded
     // run computes its own functions, which its sub-system numbers first)
     const int64_t nf_h = s->hphi_limit >= 0 ? std::min<int64_t>(nf, s->hphi_limit) : nf;
@@ -492,6 +497,7 @@ lsw_status build_plans(lsw_system_s* s) {
         p.prec = s->prec;
         p.nfn = static_cast<int>(b.nfn);
         p.zcols = zcols;
+        p.fwd_list = s->fwd_list;
         size_t smem_bwd_plain = 0;
         int64_t o = 0;
         for (int64_t f = f0; f < f0 + b.nfn; ++f) {
@@ -550,17 +556,57 @@ lsw_status build_plans(lsw_system_s* s) {
         if (!p.gstage) p.smem_bwd = smem_bwd_plain;
         p.zsplit = s->zsplit;
         p.xy_tc = s->zsplit ? s->xy_tc : 0;
-        if (p.smem_fwd > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem ||
-            p.smem_ztc > s->ctx->max_smem || p.smem_kin > s->ctx->max_smem || p.smem_bwd_tc + BWD_STATIC_SMEM > s->ctx->max_smem ||
+        if (p.smem_fwd + FWD_STATIC_SMEM > s->ctx->max_smem || p.smem_z > s->ctx->max_smem || p.smem_bwd + BWD_STATIC_SMEM > s->ctx->max_smem ||
+            p.smem_ztc > s->ctx->max_smem || p.smem_kin > s->ctx->max_smem || p.smem_bwd_tc + BWD_TC_STATIC_SMEM > s->ctx->max_smem ||
             p.smem_fwd_tc > s->ctx->max_smem)
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles (%zu/%zu/%zu/%zu > %zu bytes)",
                         p.smem_fwd, p.smem_z, p.smem_bwd, p.smem_ztc, s->ctx->max_smem);
+        // persistent FMA plane kernels: the batch's (function, plane, z type) items, largest
+        // planes first (stable in function and plane order), and as many CTAs as fit
+        if (s->persistent && !(p.zsplit && p.xy_tc) && p.max_nzp < 1024 && p.max_nz < 1024) {
+            auto add = [&](int which) {
+                std::vector<std::pair<int64_t, int32_t>> it;
+                for (int64_t f = f0; f < f0 + b.nfn; ++f) {
+                    const FnRec& r = recs[f];
+                    const int64_t X = 2 * r.n[0] + 29, Y = 2 * r.n[1] + 29;
+                    const int planes = which == 0 ? r.n[2] : r.np[2];
+                    const int64_t cost = which == 0 ? X * Y : X * Y + static_cast<int64_t>(r.np[0]) * r.np[1];
+                    for (int z = 0; z < planes; ++z)
+                        for (int bz = 0; bz < 2; ++bz)
+                            it.emplace_back(-cost, static_cast<int32_t>(((f - f0) << 11) | (z << 1) | bz));
+                }
+                std::stable_sort(it.begin(), it.end(),
+                                 [](const auto& u, const auto& v) { return u.first < v.first; });
+                for (const auto& q : it) items.push_back(q.second);
+                return static_cast<int>(it.size());
+            };
+            int bf = 0, bb = 0;
+            CUDA_TRY(plane_kernel_blocks(p.prec, p.smem_fwd, p.smem_bwd, &bf, &bb));
+            item_off.push_back(static_cast<int64_t>(items.size()));
+            p.n_items_fwd = add(0);
+            p.n_items_bwd = add(1);
+            p.grid_fwd = std::max(1, std::min(p.n_items_fwd, std::max(1, bf) * s->ctx->n_sm));
+            p.grid_bwd = std::max(1, std::min(p.n_items_bwd, std::max(1, bb) * s->ctx->n_sm));
+        } else {
+            item_off.push_back(-1);
+        }
         s->batches.push_back(b);
     }
     s->ws_elems = ws_max;
     cudaStream_t st = s->stream;
     CUDA_TRY(s->d_fn.upload(recs, st));
     for (auto& b : s->batches) b.proto.fn = static_cast<const FnRec*>(s->d_fn.p) + b.fn0;
+    if (!items.empty()) {
+        CUDA_TRY(s->d_plane_items.upload(items, st));
+        if (!s->d_queue.p) CUDA_TRY(s->d_queue.alloc(4 * sizeof(int)));
+    }
+    for (size_t i = 0; i < s->batches.size(); ++i) {
+        HphiLaunch& p = s->batches[i].proto;
+        if (item_off[i] < 0) continue;
+        p.items_fwd = static_cast<const int32_t*>(s->d_plane_items.p) + item_off[i];
+        p.items_bwd = p.items_fwd + p.n_items_fwd;
+        p.queue = static_cast<int*>(s->d_queue.p);
+    }
     CUDA_TRY(s->d_ws.alloc(static_cast<size_t>(ws_max) * s->esize));
     return LSW_OK;
 }
@@ -894,6 +940,7 @@ lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hph
         p.seg_n = static_cast<int64_t>(s->d_seg.bytes / sizeof(Seg));
         p.rowptr_n = static_cast<int64_t>(s->d_rowptr.bytes / sizeof(int32_t));
         p.n_atoms = s->n_atoms;
+        if (p.queue) CUDA_TRY(cudaMemsetAsync(p.queue, 0, 2 * sizeof(int), st));
         CUDA_TRY(enqueue_hphi_batch(p, st));
     }
     return LSW_OK;
@@ -1210,8 +1257,8 @@ bool noalloc_finish(const lsw_system_s* s, HphiLaunch* p, size_t smem_bwd_plain)
     const size_t mx = s->ctx->max_smem;
     p->gstage = p->smem_bwd + BWD_STATIC_SMEM <= mx ? 1 : 0;
     if (!p->gstage) p->smem_bwd = smem_bwd_plain;
-    return !(p->smem_fwd > mx || p->smem_z > mx || p->smem_bwd + BWD_STATIC_SMEM > mx || p->smem_ztc > mx ||
-             p->smem_kin > mx || p->smem_bwd_tc + BWD_STATIC_SMEM > mx || p->smem_fwd_tc > mx);
+    return !(p->smem_fwd + FWD_STATIC_SMEM > mx || p->smem_z > mx || p->smem_bwd + BWD_STATIC_SMEM > mx || p->smem_ztc > mx ||
+             p->smem_kin > mx || p->smem_bwd_tc + BWD_TC_STATIC_SMEM > mx || p->smem_fwd_tc > mx);
 }
 }  // namespace
 
@@ -2101,7 +2148,7 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
                                &sys->d_items, &sys->d_citems, &sys->d_slab_atoms, &sys->d_PA, &sys->d_PQ, &sys->d_mcoef,
                                &sys->d_tpos, &sys->d_diag, &sys->d_ident, &sys->d_foe, &sys->d_foe_scratch,
                                &sys->d_qtab, &sys->d_qtab_off, &sys->d_cbox, &sys->d_cg, &sys->d_cgs,
-                               &sys->d_ws, &sys->d_status,
+                               &sys->d_ws, &sys->d_status, &sys->d_plane_items, &sys->d_queue,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
                                &sys->d_ep, &sys->d_shift, &sys->d_fn_all, &sys->d_U, &sys->d_dfn,
                                &sys->d_tptr, &sys->d_tfn};
@@ -2241,6 +2288,20 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
         drop_graphs(sys);
         sys->hphi_limit = value;
+        return build_plans(sys);
+    }
+    if (std::strcmp(name, "fwd_list") == 0) {
+        if (value != 0 && value != 1) return fail(LSW_ERR_ARG, "lsw_set_option: fwd_list %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        sys->fwd_list = static_cast<int>(value);
+        return build_plans(sys);
+    }
+    if (std::strcmp(name, "persistent") == 0) {
+        if (value != 0 && value != 1) return fail(LSW_ERR_ARG, "lsw_set_option: persistent %lld", static_cast<long long>(value));
+        CUDA_TRY(cudaStreamSynchronize(sys->stream));
+        drop_graphs(sys);
+        sys->persistent = static_cast<int>(value);
         return build_plans(sys);
     }
     if (std::strcmp(name, "graph") == 0) {

@@ -21,7 +21,9 @@ constexpr int V_REACH = 14;      // real-space box of a coarse block [lo, hi]: [
 constexpr int ALIGN_ELEMS = 64;  // function offsets in the compressed arrays
 constexpr int ZCOLS_F64 = 64;    // real-space columns per block of the z stage (FP64)
 constexpr int ZCOLS_F32 = 128;   // (FP32)
-constexpr size_t BWD_STATIC_SMEM = 13 * 1024 + 512;   // upper bound of k_bwd_xy's static shared memory
+constexpr size_t BWD_STATIC_SMEM = 16 * 1024 + 512;   // upper bound of k_bwd_xy's static shared memory
+constexpr size_t BWD_TC_STATIC_SMEM = 8 * 1024 + 512; // ... of its tensor-core versions (checked at set-up)
+constexpr size_t FWD_STATIC_SMEM = 4 * 1024;          // ... of k_fwd_xy
 
 // Filter tables, FP64 (rounded once from double-double).
 struct FilterSet {
@@ -153,6 +155,17 @@ struct HphiLaunch {
     size_t smem_bwd_tc;          // dynamic shared memory of the tensor-core plane kernel
     size_t smem_fwd_tc;          // dynamic shared memory of the tensor-core forward plane kernel
     size_t smem_kin;             // dynamic shared memory of the kinetic z-arm kernel
+    // persistent FMA plane kernels: the batch's items (function << 11 | plane << 1 | z type),
+    // largest planes first, taken from queue[0] (forward) and queue[1] (backward), which
+    // are zeroed before the batch; grid_* CTAs (as many as fit on the GPU).  NULL items:
+    // one CTA per (2 planes + z type, function) grid slot.
+    const int32_t* items_fwd;
+    const int32_t* items_bwd;
+    int n_items_fwd, n_items_bwd;
+    int grid_fwd, grid_bwd;
+    int* queue;
+    int fwd_list;                // 1: the forward x pass computes only the blocks whose input
+                                 // window meets the row's members (the rest of its plane is 0)
     const AtomRec* atoms;
     const Seg* seg;
     const int32_t* rowptr;
@@ -337,6 +350,8 @@ cudaError_t enqueue_reformat(const ReformatLaunch& a, cudaStream_t s);
 cudaError_t upload_filters(const FilterSet& fs, int device);
 cudaError_t measure_peaks(int n_sm, double* fp32_tflops, double* fp64_tflops, double* copy_gbs);
 cudaError_t configure_kernels(size_t max_smem);
+// Resident CTAs per SM of the FMA plane kernels at these dynamic shared-memory sizes.
+cudaError_t plane_kernel_blocks(int prec, size_t smem_fwd, size_t smem_bwd, int* fwd, int* bwd);
 cudaError_t enqueue_hphi_batch(const HphiLaunch& a, cudaStream_t s);
 cudaError_t enqueue_pack(const PackLaunch& a, cudaStream_t s);     // panels of a slab (lsw_panels.cu)
 cudaError_t enqueue_panel_hs(const PanelHSLaunch& a, cudaStream_t s);   // S, H from the panels

@@ -340,14 +340,13 @@ __device__ __forceinline__ void kin_block<float>(const float (&k0)[KW], const fl
 // ---------------------------------------------------------------- forward x, y
 
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
+__device__ __forceinline__ void fwd_plane(const HphiLaunch& a, int fl, int z, int bz) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 2;
     int* st = a.status;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    const FnRec r = a.fn[blockIdx.y];
-    const int z = blockIdx.x >> 1, bz = blockIdx.x & 1;
+    const FnRec r = a.fn[fl];
     if (z >= r.n[2]) return;
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
     const int X = 2 * nx + 29, Y = 2 * ny + 29;
@@ -368,15 +367,81 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
                 8 * plane);
         }
     }
+    // x pass work list.  Row (by, y) holds the types (bz, by, 0), (bz, by, 1) of D, which are
+    // zero off L's members in the row: the coarse segment where the pair holds type 0
+    // (bz = 0, by = 0), else the fine segments.  Block blk (inputs x = 4 blk - 15 ..
+    // 4 blk + 3) is computed for the rows whose nonzero range meets its window; per (by,
+    // blk) the hull of those rows is listed (block-major, consecutive rows on consecutive
+    // threads), and the rest of mid is zero.
+    const int nbx = (nx + 15 + FB - 1) / FB;
+    __shared__ int16_t ix0[2][256], ix1[2][256];
+    __shared__ int hlo[128], hhi[128], hp[129];
+    const bool listed = a.fwd_list && 2 * nbx <= 128 && ny <= 256;   // else every (row, block)
+    if (listed) {
+        const AtomRec& at = a.atoms[r.atom];
+        for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+            const int64_t crow = at.rowLc + y + static_cast<int64_t>(ny) * z;
+            const int64_t frow = at.rowLf + y + static_cast<int64_t>(ny) * z;
+            const int c0 = LD(a.rowptr, crow, a.rowptr_n), c1 = LD(a.rowptr, crow + 1, a.rowptr_n);
+            const int q0 = LD(a.rowptr, frow, a.rowptr_n), q1 = LD(a.rowptr, frow + 1, a.rowptr_n);
+            const int cx0 = c1 > c0 ? LD(a.seg, at.segLc + c0, a.seg_n).x0 : -1;
+            const int cx1 = c1 > c0 ? LD(a.seg, at.segLc + c1 - 1, a.seg_n).x1 : -1;
+            const int fx0 = q1 > q0 ? LD(a.seg, at.segLf + q0, a.seg_n).x0 : -1;
+            const int fx1 = q1 > q0 ? LD(a.seg, at.segLf + q1 - 1, a.seg_n).x1 : -1;
+            ix0[0][y] = static_cast<int16_t>(bz == 0 ? cx0 : fx0);
+            ix1[0][y] = static_cast<int16_t>(bz == 0 ? cx1 : fx1);
+            ix0[1][y] = static_cast<int16_t>(fx0);
+            ix1[1][y] = static_cast<int16_t>(fx1);
+        }
+        for (int e = threadIdx.x; e < 2 * nbx; e += blockDim.x) {
+            hlo[e] = ny;
+            hhi[e] = -1;
+        }
+        for (int i = threadIdx.x; i < 2 * ny * X; i += blockDim.x) ST(mid, i, mid_n, T(0));
+    }
+    __syncthreads();
+    if (listed) {
+        for (int row = threadIdx.x; row < 2 * ny; row += blockDim.x) {
+            const int by = row >= ny, y = row - by * ny;
+            const int x0 = ix0[by][y];
+            if (x0 < 0) continue;
+            const int k1 = min(nbx - 1, (ix1[by][y] + 15) / FB);
+            for (int k = x0 / FB; k <= k1; ++k) {
+                atomicMin(&hlo[by * nbx + k], y);
+                atomicMax(&hhi[by * nbx + k], y);
+            }
+        }
+    }
     cp_wait();
     __syncthreads();
+    if (listed && threadIdx.x == 0) {
+        hp[0] = 0;
+        for (int e = 0; e < 2 * nbx; ++e) hp[e + 1] = hp[e] + max(0, hhi[e] - hlo[e] + 1);
+    }
+    __syncthreads();
     // x pass: rows (by, y), blocks of 8 outputs along x'
-    const int nbx = (nx + 15 + FB - 1) / FB;
     {
         const FastDiv fd_2ny(2 * ny), fd_ny(ny);
-        for (int task = threadIdx.x; task < 2 * ny * nbx; task += blockDim.x) {
-            const int blk = fd_2ny.div(task), row = task - blk * 2 * ny;
-            const int by = fd_ny.div(row), y = row - by * ny;
+        const int ntk = listed ? hp[2 * nbx] : 2 * ny * nbx;
+        for (int task = threadIdx.x; task < ntk; task += blockDim.x) {
+            int by, y, blk;
+            if (listed) {
+                int lo = 0, hi = 2 * nbx - 1;              // the entry e with hp[e] <= task < hp[e + 1]
+                while (lo < hi) {
+                    const int m = (lo + hi + 1) >> 1;
+                    if (hp[m] <= task) lo = m;
+                    else hi = m - 1;
+                }
+                by = lo >= nbx;
+                blk = lo - by * nbx;
+                y = hlo[lo] + (task - hp[lo]);
+            } else {
+                blk = fd_2ny.div(task);
+                const int rw = task - blk * 2 * ny;
+                by = fd_ny.div(rw);
+                y = rw - by * ny;
+            }
+            const int row = by * ny + y;
             const int p0 = blk * FB;
             const int s0 = ((2 * by) * ny + y) * RS, d0 = s0 + ny * RS;
             T w0[FW], w1[FW], u[2 * FB];
@@ -408,6 +473,36 @@ __global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
             const int yo = 2 * p0 + k;
             if (yo < Y) ST(Bf, static_cast<int64_t>(yo) * X + xo, bf_room, u[k]);
         }
+    }
+}
+
+// Item k of a persistent plane kernel: the next index of the queue counter (one atomic per
+// CTA, broadcast through shared memory), so CTAs take the batch's planes largest first
+// as they free up.  The caller's next barrier orders the read before the next write.
+__device__ __forceinline__ int next_item(int* counter, int* s_item) {
+    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    return *s_item;
+}
+
+// Persistent form (a.items_fwd set): a grid of as many CTAs as fit on the GPU loops over
+// the batch's (function, z plane, z type) items; otherwise one CTA per grid slot
+// (blockIdx.x = 2 z + b_z, blockIdx.y = function).
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd_xy(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 2;
+    if (a.items_fwd) {
+        __shared__ int s_item;
+        for (;;) {
+            const int k = next_item(a.queue, &s_item);
+            if (k >= a.n_items_fwd) break;
+            const int code = LD(a.items_fwd, k, a.n_items_fwd);
+            fwd_plane<T>(a, code >> 11, (code >> 1) & 1023, code & 1);
+            __syncthreads();   // shared memory and s_item are reused by the next item
+        }
+    } else {
+        fwd_plane<T>(a, blockIdx.y, blockIdx.x >> 1, blockIdx.x & 1);
     }
 }
 
@@ -1130,8 +1225,7 @@ __device__ bool bwd_tc_potential(const float* Bb, [[maybe_unused]] int64_t bb_ro
 // with P the plane of Bb; thread (warp w, lane l) owns row j = 32 (w mod 4) + l of both
 // products and quarter w / 4 of each K or N range.
 template <class T, int NS>
-__global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1))
-    k_bwd_xy(HphiLaunch a) {
+__device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, int bz) {
     [[maybe_unused]] int* ST_ = a.status;
     [[maybe_unused]] constexpr int KID = 4;
     int* st = a.status;
@@ -1140,12 +1234,12 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     __shared__ int16_t rx0[256], rx1[256];         // member x range per row (L' plane), -1: none
     __shared__ int roff[256];                      // coefficient offset of the row's coarse segment
     __shared__ int fr0[256], fr1[256];             // fine segment range of the row (L' keys)
-    __shared__ int task[BWD_MAX_TASKS];
-    __shared__ int ntask, ylo, yhi, xlo, xhi;
+    __shared__ int16_t fx0[256], fx1[256];         // hull of the row's fine members, -1: none
+    __shared__ int rq0[128], rq1[128], rqp[129];   // per row block: column range, prefix of widths
+    __shared__ int ntask, ylo, yhi;
     __shared__ unsigned char rowf[4][128], colf[4][128];   // D plane: nonzero per (type, row / column)
     T* sm = reinterpret_cast<T*>(smem_raw);
-    const FnRec r = a.fn[blockIdx.y];
-    const int zb = blockIdx.x >> 1, bz = blockIdx.x & 1;
+    const FnRec r = a.fn[fl];
     if (zb >= r.np[2]) return;
     const AtomRec& at = a.atoms[r.atom];
     const int nx = r.n[0], ny = r.n[1], nz = r.n[2];
@@ -1163,6 +1257,17 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     unsigned char* sFy = smem_raw + tc::HEAD;
     unsigned char* sFx = sFy + NS * FY_PART;
     unsigned char* sXr = sFx + NS * FX_PART;
+    // task lists of the x pass and the kinetic x arm, later the plane's fine segments for
+    // the compressed write: static shared memory in the FMA version; in the tensor-core
+    // version the filter operands' region, dead once the potential part is done
+    // (NS * FY_PART >= 2 * 128 * 16 * 2 bytes = BWD_MAX_TASKS ints; 16-byte aligned)
+    int* task;
+    if constexpr (NS == 0) {
+        __shared__ __align__(16) int task_s[BWD_MAX_TASKS];
+        task = task_s;
+    } else {
+        task = reinterpret_cast<int*>(sFy);
+    }
     T* pl = sm;
     T* Gs = NS ? reinterpret_cast<T*>(sXr) : sm;
     // mid [2][nyp][X], later (when the host found room: a.gstage) the z-arm plane
@@ -1184,8 +1289,6 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     if (threadIdx.x == 0) {
         ylo = nyp;
         yhi = -1;
-        xlo = nxp;
-        xhi = -1;
     }
     for (int i = threadIdx.x; i < 4 * 128; i += blockDim.x) {
         rowf[i >> 7][i & 127] = 0;
@@ -1233,15 +1336,16 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             hi = LD(a.seg, at.segPc + s1 - 1, a.seg_n).x1;
             atomicMin(&ylo, y);
             atomicMax(&yhi, y);
-            atomicMin(&xlo, lo);
-            atomicMax(&xhi, hi);
         }
         rx0[y] = static_cast<int16_t>(lo);
         rx1[y] = static_cast<int16_t>(hi);
         roff[y] = off;
         const int64_t frow = at.rowPf + y + static_cast<int64_t>(nyp) * zb;
-        fr0[y] = LD(a.rowptr, frow, a.rowptr_n);
-        fr1[y] = LD(a.rowptr, frow + 1, a.rowptr_n);
+        const int q0 = LD(a.rowptr, frow, a.rowptr_n), q1 = LD(a.rowptr, frow + 1, a.rowptr_n);
+        fr0[y] = q0;
+        fr1[y] = q1;
+        fx0[y] = static_cast<int16_t>(q1 > q0 ? LD(a.seg, at.segPf + q0, a.seg_n).x0 : -1);
+        fx1[y] = static_cast<int16_t>(q1 > q0 ? LD(a.seg, at.segPf + q1 - 1, a.seg_n).x1 : -1);
     }
     cp_wait_group<1>();   // the Bb plane (group 2 may still be in flight)
     if (threadIdx.x == 0) ntask = 0;
@@ -1251,6 +1355,19 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     const T ks = static_cast<T>(a.kin_scale);
     T ekin_t = 0;
     const int ylo_ = ylo, yhi_ = yhi;
+    // The x range of row b whose outputs of the y-type pair `by` (types 2 by, 2 by + 1 of
+    // this plane) the compressed write reads: the coarse members where the pair holds the
+    // scaling type 0 (bz = 0, by = 0), else the hull of the row's fine members (the wavelet
+    // types are stored on fine members only).  lo < 0: none.
+    auto need = [&](int by, int b, int& lo, int& hi) {
+        if (bz == 0 && by == 0) {
+            lo = rx0[b];
+            hi = rx1[b];
+        } else {
+            lo = fx0[b];
+            hi = fx1[b];
+        }
+    };
     if constexpr (NS > 0) {
         // ---- potential part on the tensor cores -> Gs (every row and column of the plane)
         if (yhi_ >= 0 && !bwd_tc_potential<NS>(reinterpret_cast<const float*>(Bb), bb_room, X, Y, nyp, nxp, dx, dy,
@@ -1262,18 +1379,23 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     if (yhi_ >= 0) {
       if constexpr (NS == 0) {
         // ---- y pass: blocks of NB rows b within [ylo, yhi], and per block only the columns
-        //      x' the x pass reads: for a member row b its blocks k = rx0/NB .. rx1/NB read
-        //      x' in [2 (k NB + dx), 2 (k NB + NB - 1 + dx) + 30]
+        //      x' the x pass reads: for row b and pair by its blocks k = lo/NB .. hi/NB of
+        //      the needed range read x' in [2 (k NB + dx), 2 (k NB + NB - 1 + dx) + 30]
         const int nbb = (yhi_ - ylo_ + NB) / NB;
-        __shared__ int cq0[64], cq1[64], pq[65];
+        int* cq0 = rq0;
+        int* cq1 = rq1;
+        int* pq = rqp;
         if (threadIdx.x < nbb) {
             const int q = threadIdx.x;
             int c0 = X, c1 = -1;
-            for (int b = ylo_ + q * NB; b < min(ylo_ + (q + 1) * NB, yhi_ + 1); ++b) {
-                if (rx0[b] < 0) continue;
-                c0 = min(c0, 2 * ((rx0[b] / NB) * NB + dx));
-                c1 = max(c1, 2 * ((rx1[b] / NB) * NB + NB - 1 + dx) + 30);
-            }
+            for (int b = ylo_ + q * NB; b < min(ylo_ + (q + 1) * NB, yhi_ + 1); ++b)
+                for (int by = 0; by < 2; ++by) {
+                    int lo, hi;
+                    need(by, b, lo, hi);
+                    if (lo < 0) continue;
+                    c0 = min(c0, 2 * ((lo / NB) * NB + dx));
+                    c1 = max(c1, 2 * ((hi / NB) * NB + NB - 1 + dx) + 30);
+                }
             cq0[q] = max(c0, 0);
             cq1[q] = min(c1, X - 1);
         }
@@ -1303,11 +1425,13 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             }
         }
         __syncthreads();   // pl is dead from here on: Gs reuses it
-        // ---- task list: (by, row b, x block of NB) intersecting the row's member range
+        // ---- task list: (by, row b, x block of NB) intersecting the row's needed range
         for (int b = ylo_ + threadIdx.x; b <= yhi_; b += blockDim.x) {
-            if (rx0[b] < 0) continue;
-            const int k0 = rx0[b] / NB, k1 = rx1[b] / NB;
             for (int by = 0; by < 2; ++by) {
+                int lo, hi;
+                need(by, b, lo, hi);
+                if (lo < 0) continue;
+                const int k0 = lo / NB, k1 = hi / NB;
                 const int base = atomicAdd(&ntask, k1 - k0 + 1);
                 for (int k = k0; k <= k1; ++k)
                     if (base + k - k0 < BWD_MAX_TASKS) task[base + k - k0] = (by << 24) | (b << 12) | k;
@@ -1365,13 +1489,17 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
             __syncthreads();
             if (threadIdx.x == 0) ntask = 0;
             __syncthreads();
-            // ---- kinetic x arm: (by, row b, x block of BB) of member rows whose D rows are nonzero
+            // ---- kinetic x arm: (by, row b, x block of BB) over the needed range of rows whose
+            //      D rows are nonzero
             for (int b = ylo_ + threadIdx.x; b <= yhi_; b += blockDim.x) {
                 const int y = b + dy;
-                if (rx0[b] < 0 || y < 0 || y >= ny) continue;
-                const int k0 = rx0[b] / BB, k1 = rx1[b] / BB;
+                if (y < 0 || y >= ny) continue;
                 for (int by = 0; by < 2; ++by) {
                     if (!rowf[2 * by][y & 127] && !rowf[2 * by + 1][y & 127]) continue;
+                    int lo, hi;
+                    need(by, b, lo, hi);
+                    if (lo < 0) continue;
+                    const int k0 = lo / BB, k1 = hi / BB;
                     const int base = atomicAdd(&ntask, k1 - k0 + 1);
                     for (int k = k0; k <= k1; ++k)
                         if (base + k - k0 < BWD_MAX_TASKS) task[base + k - k0] = (by << 24) | (b << 12) | k;
@@ -1404,28 +1532,44 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                     }
                 }
             }
-            __syncthreads();
-            if (threadIdx.x == 0) ntask = 0;
-            __syncthreads();
-            // ---- kinetic y arm: (bx, column x'' in [xlo, xhi], block of rows in [ylo, yhi])
+            __syncthreads();   // the x arm's Gs updates are done
+            // ---- kinetic y arm: per x type bx (the pair of types bx, bx + 2) and block q of BB
+            //      rows, the columns of the hull of the rows' needed ranges (coarse members
+            //      where the pair holds type 0, else fine members); task (bx, q, column),
+            //      consecutive columns on consecutive threads
             const int nbyk = (yhi_ - ylo_ + BB) / BB;
-            const int ncols = xhi - xlo + 1;
-            for (int c = threadIdx.x; c < 2 * ncols; c += blockDim.x) {
-                const int bx = c >= ncols, xb = xlo + (c - bx * ncols);
+            if (threadIdx.x < 2 * nbyk) {
+                const int bx = threadIdx.x >= nbyk, q = threadIdx.x - bx * nbyk;
+                const bool coarse = bz == 0 && bx == 0;
+                int c0 = nxp, c1 = -1;
+                for (int b = ylo_ + q * BB; b < min(ylo_ + (q + 1) * BB, yhi_ + 1); ++b) {
+                    const int lo = coarse ? rx0[b] : fx0[b], hi = coarse ? rx1[b] : fx1[b];
+                    if (lo < 0) continue;
+                    c0 = min(c0, lo);
+                    c1 = max(c1, hi);
+                }
+                rq0[threadIdx.x] = c0;
+                rq1[threadIdx.x] = c1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                rqp[0] = 0;
+                for (int i = 0; i < 2 * nbyk; ++i) rqp[i + 1] = rqp[i] + max(0, rq1[i] - rq0[i] + 1);
+            }
+            __syncthreads();
+            nt = rqp[2 * nbyk];
+            for (int it = threadIdx.x; it < nt; it += blockDim.x) {
+                int lo = 0, hi = 2 * nbyk - 1;              // the entry i with rqp[i] <= it < rqp[i + 1]
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (rqp[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int bx = lo >= nbyk, q = lo - bx * nbyk;
+                const int xb = rq0[lo] + (it - rqp[lo]), b0 = ylo_ + q * BB;
                 const int x = xb + dx;
                 if (x < 0 || x >= nx) continue;
                 if (!colf[bx][x & 127] && !colf[bx + 2][x & 127]) continue;
-                const int base = atomicAdd(&ntask, nbyk);
-                for (int k = 0; k < nbyk; ++k)
-                    if (base + k < BWD_MAX_TASKS) task[base + k] = (bx << 24) | (xb << 12) | k;
-            }
-            __syncthreads();
-            nt = min(ntask, BWD_MAX_TASKS);
-            if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
-            for (int it = threadIdx.x; it < nt; it += blockDim.x) {
-                const int code = task[it];
-                const int bx = code >> 24, xb = (code >> 12) & 4095, b0 = ylo_ + (code & 4095) * BB;
-                const int x = xb + dx;
                 T k0[KW], k1[KW], o0[BB], o1[BB];
                 swin(k0, Dp, bx * ny * RS + x, RS, b0 + dy - KIN_HALF, ny, dp_n, st);
                 swin(k1, Dp, (bx + 2) * ny * RS + x, RS, b0 + dy - KIN_HALF, ny, dp_n, st);
@@ -1450,7 +1594,12 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
     cp_wait();
     __syncthreads();
     // ---- compress: members of this plane -> H phi (plus the z arm left in G by k_kin_z;
-    //      the FMA path reads it from the plane staged in mid)
+    //      the FMA path reads it from the plane staged in mid).  Coarse members (type 0)
+    //      row by row, a warp per row (one segment of up to n_x' members each); fine members
+    //      flattened over the CTA, one member per thread and type: the plane's fine
+    //      segments (many short chords of the fine spheres) are staged in shared memory and
+    //      each member finds its segment by a binary search, so every lane writes and
+    //      consecutive lanes write consecutive H phi elements.
     if (yhi_ >= 0) {
         const T* G = static_cast<const T*>(a.ws) + r.ws_G;
         const unsigned char* gflag = reinterpret_cast<const unsigned char*>(a.gstage ? gfl : gsrc);
@@ -1459,12 +1608,12 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
         T* out = static_cast<T*>(a.hphi) + r.off_hphi;
         const int64_t out_room = a.hphi_n - r.off_hphi;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int b = ylo_ + warp; b <= yhi_; b += (blockDim.x >> 5)) {
-            if (rx0[b] < 0) continue;
-            const int y = b + dy;
-            const bool yin = y >= 0 && y < ny;
-            const int64_t grow = (static_cast<int64_t>(zb) * nyp + b) * nxp;
-            if (bz == 0) {   // scaling part s (type 0) on the coarse members
+        if (bz == 0) {   // scaling part s (type 0) on the coarse members
+            for (int b = ylo_ + warp; b <= yhi_; b += (blockDim.x >> 5)) {
+                if (rx0[b] < 0) continue;
+                const int y = b + dy;
+                const bool yin = y >= 0 && y < ny;
+                const int64_t grow = (static_cast<int64_t>(zb) * nyp + b) * nxp;
                 for (int xb = rx0[b] + lane; xb <= rx1[b]; xb += 32) {
                     const int x = xb + dx;
                     T v = LD(Gs, static_cast<int64_t>(b) * nxp + xb, gs_n);
@@ -1473,23 +1622,51 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
                     ST(out, roff[b] + (xb - rx0[b]), out_room, v);
                 }
             }
-            // wavelet parts on the fine members of this row
-            const int f0 = fr0[b], f1 = fr1[b];
-            for (int q = f0; q < f1; ++q) {
-                const Seg fs = LD(a.seg, at.segPf + q, a.seg_n);
-                for (int xb = fs.x0 + lane; xb <= fs.x1; xb += 32) {
-                    const int x = xb + dx;
-                    const bool zin = yin && x >= 0 && x < nx;
+        }
+        // wavelet parts on the fine members of this plane: segments [q0, q1) hold members
+        // [m0, m1) of each type's block
+        const int q0 = fr0[ylo_], q1 = fr1[yhi_];
+        if (q1 > q0) {
+            constexpr int SEG_CAP = BWD_MAX_TASKS / 4;    // Seg records in the task array
+            int4* sseg = reinterpret_cast<int4*>(task);
+            const int nq = q1 - q0;
+            const bool staged = nq <= SEG_CAP;
+            if (staged)
+                for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+                    const Seg g = LD(a.seg, at.segPf + q0 + i, a.seg_n);
+                    sseg[i] = make_int4(g.x0, g.x1, g.row, g.off);
+                }
+            __syncthreads();
+            auto seg_at = [&](int i) -> int4 {
+                if (staged) return sseg[i];
+                const Seg g = LD(a.seg, at.segPf + q0 + i, a.seg_n);
+                return make_int4(g.x0, g.x1, g.row, g.off);
+            };
+            const int4 sl = seg_at(nq - 1);
+            const int m0 = seg_at(0).w, m1 = sl.w + (sl.y - sl.x + 1);
+            const int64_t zrow = static_cast<int64_t>(nyp) * zb;
+            for (int m = m0 + static_cast<int>(threadIdx.x); m < m1; m += blockDim.x) {
+                int lo = 0, hi = nq - 1;                     // the segment with off <= m
+                while (lo < hi) {
+                    const int mid_ = (lo + hi + 1) >> 1;
+                    if (seg_at(mid_).w <= m) lo = mid_;
+                    else hi = mid_ - 1;
+                }
+                const int4 g = seg_at(lo);
+                const int xb = g.x + (m - g.w);
+                const int b = static_cast<int>(g.z - zrow);
+                const int y = b + dy, x = xb + dx;
+                const bool zin = y >= 0 && y < ny && x >= 0 && x < nx;
+                const int64_t grow = (static_cast<int64_t>(zb) * nyp + b) * nxp;
 #pragma unroll
-                    for (int tb = 0; tb < 4; ++tb) {
-                        const int t = tb + 4 * bz;
-                        if (t == 0) continue;
-                        T v = LD(Gs, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, gs_n);
-                        if (zin && LD(gflag, (t & 3) * pn + y * nx + x, 4LL * pn))
-                            v += gsm ? LD(mid, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, midA)
-                                     : LD(G, t * gplane + grow + xb, 8 * gplane);
-                        ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + fs.off + (xb - fs.x0), out_room, v);
-                    }
+                for (int tb = 0; tb < 4; ++tb) {
+                    const int t = tb + 4 * bz;
+                    if (t == 0) continue;
+                    T v = LD(Gs, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, gs_n);
+                    if (zin && LD(gflag, (t & 3) * pn + y * nx + x, 4LL * pn))
+                        v += gsm ? LD(mid, (static_cast<int64_t>(tb) * nyp + b) * nxp + xb, midA)
+                                 : LD(G, t * gplane + grow + xb, 8 * gplane);
+                    ST(out, at.ncP + static_cast<int64_t>(t - 1) * at.nfP + m, out_room, v);
                 }
             }
         }
@@ -1501,6 +1678,29 @@ __global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW
         __syncthreads();
         tc::fence_after();
         if ((threadIdx.x >> 5) == 0) tc::tmem_free(*reinterpret_cast<volatile uint32_t*>(smem_raw + 8), 128);
+    }
+}
+
+// Persistent form of the FMA version (a.items_bwd set): the batch's (function, z'' plane,
+// z type) items, largest first, from the second queue counter; otherwise (and always for
+// the tensor-core versions) one CTA per grid slot (blockIdx.x = 2 z'' + b_z, blockIdx.y =
+// function).
+template <class T, int NS>
+__global__ void __launch_bounds__(NS ? 512 : 256, NS ? 1 : (sizeof(T) == 4 ? LSW_BWD_MIN_BLOCKS : 1))
+    k_bwd_xy(HphiLaunch a) {
+    [[maybe_unused]] int* ST_ = a.status;
+    [[maybe_unused]] constexpr int KID = 4;
+    if (NS == 0 && a.items_bwd) {
+        __shared__ int s_item;
+        for (;;) {
+            const int k = next_item(a.queue + 1, &s_item);
+            if (k >= a.n_items_bwd) break;
+            const int code = LD(a.items_bwd, k, a.n_items_bwd);
+            bwd_plane<T, NS>(a, code >> 11, (code >> 1) & 1023, code & 1);
+            __syncthreads();   // shared memory and s_item are reused by the next item
+        }
+    } else {
+        bwd_plane<T, NS>(a, blockIdx.y, blockIdx.x >> 1, blockIdx.x & 1);
     }
 }
 
@@ -1896,7 +2096,30 @@ cudaError_t configure_kernels(size_t max_smem) {
     SETMAX((k_bwd_xy<float, 2>)) SETMAX((k_bwd_xy<float, 3>))
     SETMAX(k_z_dens<double>) SETMAX(k_z_dens<float>)
 #undef SETMAX
+    // the plans size the plane kernels' dynamic shared memory against these bounds
+#define STATIC_BOUND(K, B)                                                                     \
+    {                                                                                          \
+        cudaFuncAttributes fa;                                                                 \
+        if ((e = cudaFuncGetAttributes(&fa, K)) != cudaSuccess) return e;                      \
+        if (fa.sharedSizeBytes > (B)) return cudaErrorInvalidConfiguration;                     \
+    }
+    STATIC_BOUND(k_fwd_xy<double>, FWD_STATIC_SMEM) STATIC_BOUND(k_fwd_xy<float>, FWD_STATIC_SMEM)
+    STATIC_BOUND((k_bwd_xy<double, 0>), BWD_STATIC_SMEM) STATIC_BOUND((k_bwd_xy<float, 0>), BWD_STATIC_SMEM)
+    STATIC_BOUND((k_bwd_xy<float, 2>), BWD_TC_STATIC_SMEM) STATIC_BOUND((k_bwd_xy<float, 3>), BWD_TC_STATIC_SMEM)
+#undef STATIC_BOUND
     return cudaSuccess;
+}
+
+cudaError_t plane_kernel_blocks(int prec, size_t smem_fwd, size_t smem_bwd, int* fwd, int* bwd) {
+    cudaError_t e;
+    if (prec == 0) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd, k_fwd_xy<double>, 256, smem_fwd)) != cudaSuccess)
+            return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bwd, k_bwd_xy<double, 0>, 256, smem_bwd);
+    }
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd, k_fwd_xy<float>, 256, smem_fwd)) != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bwd, k_bwd_xy<float, 0>, 256, smem_bwd);
 }
 
 #define TRACED(TR, KIND, S, LAUNCH) \
@@ -1910,15 +2133,17 @@ template <class T>
 static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
     const int nf = a.nfn;
     TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_rowsL + 7) / 8, nf), 256, 0, s>>>(a)));
+    const dim3 gfwd = a.items_fwd ? dim3(a.grid_fwd) : dim3(2 * a.max_nz, nf);
+    const dim3 gbwd = a.items_bwd ? dim3(a.grid_bwd) : dim3(2 * a.max_nzp, nf);
     if constexpr (sizeof(T) == 4) {
         if (a.xy_tc && a.zsplit == 3)
             TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy_tc<3><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd_tc, s>>>(a)));
         else if (a.xy_tc && a.zsplit == 2)
             TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy_tc<2><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd_tc, s>>>(a)));
         else
-            TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
+            TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<gfwd, 256, a.smem_fwd, s>>>(a)));
     } else {
-        TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));
+        TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<gfwd, 256, a.smem_fwd, s>>>(a)));
     }
     if constexpr (sizeof(T) == 4) {
         if (a.zsplit) {
@@ -1942,9 +2167,9 @@ static cudaError_t hphi_batch(const HphiLaunch& a, cudaStream_t s) {
         else if (a.xy_tc && a.zsplit == 2)
             TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<float, 2><<<dim3(2 * a.max_nzp, nf), 512, a.smem_bwd_tc, s>>>(a)));
         else
-            TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<float, 0><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
+            TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<float, 0><<<gbwd, 256, a.smem_bwd, s>>>(a)));
     } else {
-        TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T, 0><<<dim3(2 * a.max_nzp, nf), 256, a.smem_bwd, s>>>(a)));
+        TRACED(a.tr, TK_BWD_XY, s, (k_bwd_xy<T, 0><<<gbwd, 256, a.smem_bwd, s>>>(a)));
     }
     return cudaGetLastError();
 }
@@ -1959,6 +2184,8 @@ template <class T>
 static cudaError_t dens_batch(HphiLaunch a, cudaStream_t s) {
     const int nf = a.nfn;
     constexpr int C = ZCols<T>::C;
+    a.items_fwd = a.items_bwd = nullptr;       // one CTA per grid slot here
+    a.queue = nullptr;
     a.smem_z = sizeof(T) * 2 * static_cast<size_t>(a.max_nz) * C;
     TRACED(a.tr, TK_UNCOMPRESS, s, (k_uncompress<T><<<dim3((a.max_rowsL + 7) / 8, nf), 256, 0, s>>>(a)));
     TRACED(a.tr, TK_FWD_XY, s, (k_fwd_xy<T><<<dim3(2 * a.max_nz, nf), 256, a.smem_fwd, s>>>(a)));

@@ -154,6 +154,40 @@ def test_options_do_not_change_results():
 
 
 @pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
+def test_persistent_plane_kernels_same_bits(prec):
+    # option "persistent" (default 1): the FMA plane kernels loop over the batch's planes,
+    # largest first, from a queue; 0: one CTA per grid slot.  Option "fwd_list" (default
+    # 1): the forward x pass computes only the blocks whose input window meets the row's
+    # members and zeroes the rest (0: every block; an all-zero window gives +0 either way).
+    # H phi is the same bits; uneven radii (5-8 bohr) and several batches (the queue is
+    # reset before each).  Against the oracle as well.
+    wl = I.scaled("atoms1200", 14, seed=21)
+    geo = G.build(desc_of(wl))
+    V = I.potential(wl)
+    n = len(geo.sf_atom)
+    assert len(set(np.round(wl.r_loc, 3))) > 1                 # uneven radii
+    runs = {}
+    for pers in (0, 1):
+        runs[pers] = gpu_run(wl, phi_fn(wl), prec, options={"persistent": pers, "fwd_list": pers, "batch": 5},
+                             repeat=2)
+    a, b = runs[0], runs[1]
+    gap = np.isnan(a["hphi"])
+    assert np.array_equal(np.isnan(b["hphi"]), gap)
+    assert np.array_equal(a["hphi"][~gap], b["hphi"][~gap])
+    # energies: FP64 sums of per-thread partial sums, in FP32 for the FP32 forms; the
+    # kinetic task lists are built with shared-memory atomics, so which thread sums which
+    # products varies from run to run (FP32 rounding of the partial sums)
+    etol = 1e-12 if prec == lsw.LSW_FP64 else 1e-6
+    for k in ("ek", "ep"):
+        assert np.allclose(a[k], b[k], rtol=etol, atol=0), k
+    assert np.max(np.abs(a["S"] - b["S"])) <= 1e-13 * max(1.0, np.max(np.abs(a["S"])))
+    assert np.max(np.abs(a["H"] - b["H"])) <= 1e-12 * np.max(np.abs(a["H"]))
+    first = np.searchsorted(geo.sf_atom, np.arange(6))        # one function of each of six atoms
+    ref = oracle_hphi(wl, geo, [int(f) for f in first if f < n], V)
+    check_functions(wl, geo, b, ref, 1e-12 if prec == lsw.LSW_FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_atoms64_full_size_sampled(prec):
     wl = I.atoms64()
     geo = G.build(desc_of(wl))
