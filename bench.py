@@ -130,7 +130,7 @@ def stored_traffic(kernel, prec, fns_per_launch):
 
 KERNEL_KIND = {"k_uncompress": "uncompress", "k_fwd_xy": "fwd_xy", "k_fwd_xy_tc": "fwd_xy", "k_z": "z_stage",
                "k_z_tc": "z_stage", "k_kin_z": "kinetic", "k_bwd_xy": "bwd_xy", "k_pack": "hs_pack",
-               "k_panel_hs": "hs_tiles"}
+               "k_panel_hs": "hs_tiles", "k_panel_hs_tc": "hs_tiles"}
 
 
 def record_traffic(csv_path, wl, prec, batch, n_slab_launches=1):

@@ -426,10 +426,11 @@ lsw_status lsw_load_phi(lsw_system sys, const char* path, void* phi_dev);
  * function; a rank of a sharded run numbers its own functions first),
  * "slab_mb" (H/S and combination: panel budget of one slab of tiles, MiB; the panels of
  * consecutive tile-z layers are built and consumed slab by slab, default 8192),
- * "persistent" (1, the default: the FMA plane kernels of H phi run as persistent grids,
- * as many CTAs as fit on the GPU, taking the batch's (function, plane) items largest first
- * from a device queue; 0: one CTA per plane slot of a (planes, functions) grid; the
- * results are the same bits), "fwd_list" (1, the default: the forward plane kernel's x
+ * "persistent" (bit 0: the backward FMA plane kernel of H phi, bit 1: the forward one,
+ * runs as a persistent grid, as many CTAs as fit on the GPU, taking the batch's
+ * (function, plane) items largest first from a device queue; a clear bit: one CTA per
+ * plane slot of a (planes, functions) grid; the default 1, the backward kernel only,
+ * measured fastest; the results are the same bits), "fwd_list" (1, the default: the forward plane kernel's x
  * pass computes only the blocks whose input window meets the row's members of L and
  * zeroes the rest; 0: every block; the same bits),
  * "zsplit" (LSW_FP32_BF16X systems only: 2 or 3 bfloat16 parts per FP32 operand of the

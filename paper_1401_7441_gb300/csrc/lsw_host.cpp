@@ -214,7 +214,8 @@ struct lsw_system_s {
     int64_t slab_mb = PANEL_SLAB_MB;
     int64_t hphi_limit = -1;         // option "hphi_limit" (-1: every function)
     int hs_tc = 1;                   // option "hs_tc": FP32 H/S products on the tensor cores
-    int persistent = 1;              // option "persistent": FMA plane kernels over item queues
+    int persistent = 1;              // option "persistent": bit 0 the backward, bit 1 the forward
+                                     // FMA plane kernel over item queues
     int fwd_list = 1;                // option "fwd_list": forward x pass over member blocks only
     int use_graph = 1;
     // potential
@@ -583,8 +584,8 @@ lsw_status build_plans(lsw_system_s* s) {
             int bf = 0, bb = 0;
             CUDA_TRY(plane_kernel_blocks(p.prec, p.smem_fwd, p.smem_bwd, &bf, &bb));
             item_off.push_back(static_cast<int64_t>(items.size()));
-            p.n_items_fwd = add(0);
-            p.n_items_bwd = add(1);
+            p.n_items_fwd = (s->persistent & 2) ? add(0) : 0;
+            p.n_items_bwd = (s->persistent & 1) ? add(1) : 0;
             p.grid_fwd = std::max(1, std::min(p.n_items_fwd, std::max(1, bf) * s->ctx->n_sm));
             p.grid_bwd = std::max(1, std::min(p.n_items_bwd, std::max(1, bb) * s->ctx->n_sm));
         } else {
@@ -603,8 +604,9 @@ lsw_status build_plans(lsw_system_s* s) {
     for (size_t i = 0; i < s->batches.size(); ++i) {
         HphiLaunch& p = s->batches[i].proto;
         if (item_off[i] < 0) continue;
-        p.items_fwd = static_cast<const int32_t*>(s->d_plane_items.p) + item_off[i];
-        p.items_bwd = p.items_fwd + p.n_items_fwd;
+        const int32_t* it = static_cast<const int32_t*>(s->d_plane_items.p) + item_off[i];
+        p.items_fwd = p.n_items_fwd ? it : nullptr;
+        p.items_bwd = p.n_items_bwd ? it + p.n_items_fwd : nullptr;
         p.queue = static_cast<int*>(s->d_queue.p);
     }
     CUDA_TRY(s->d_ws.alloc(static_cast<size_t>(ws_max) * s->esize));
@@ -2298,7 +2300,7 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
         return build_plans(sys);
     }
     if (std::strcmp(name, "persistent") == 0) {
-        if (value != 0 && value != 1) return fail(LSW_ERR_ARG, "lsw_set_option: persistent %lld", static_cast<long long>(value));
+        if (value < 0 || value > 3) return fail(LSW_ERR_ARG, "lsw_set_option: persistent %lld", static_cast<long long>(value));
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
         drop_graphs(sys);
         sys->persistent = static_cast<int>(value);

@@ -155,7 +155,7 @@ def test_options_do_not_change_results():
 
 @pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_persistent_plane_kernels_same_bits(prec):
-    # option "persistent" (default 1): the FMA plane kernels loop over the batch's planes,
+    # option "persistent" (3: both FMA plane kernels) loops over the batch's planes,
     # largest first, from a queue; 0: one CTA per grid slot.  Option "fwd_list" (default
     # 1): the forward x pass computes only the blocks whose input window meets the row's
     # members and zeroes the rest (0: every block; an all-zero window gives +0 either way).
@@ -168,7 +168,7 @@ def test_persistent_plane_kernels_same_bits(prec):
     assert len(set(np.round(wl.r_loc, 3))) > 1                 # uneven radii
     runs = {}
     for pers in (0, 1):
-        runs[pers] = gpu_run(wl, phi_fn(wl), prec, options={"persistent": pers, "fwd_list": pers, "batch": 5},
+        runs[pers] = gpu_run(wl, phi_fn(wl), prec, options={"persistent": 3 * pers, "fwd_list": pers, "batch": 5},
                              repeat=2)
     a, b = runs[0], runs[1]
     gap = np.isnan(a["hphi"])
