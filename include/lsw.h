@@ -359,7 +359,9 @@ lsw_status lsw_reformat(lsw_system dst, lsw_system src, const int32_t* shift, co
  * LSW_ERR_CUDA. */
 lsw_status lsw_measure_peaks(lsw_ctx ctx, double* fp32_tflops, double* fp64_tflops, double* copy_gbs);
 
-/* Device workspace held by the system, bytes. */
+/* Device memory of the system, bytes: what it holds, plus the H/S panel buffers of one
+ * slab, which the first lsw_build_matrices, lsw_combine or lsw_lowdin_taylor allocates
+ * (so a request loop can budget a system before it runs). */
 lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes);
 
 /* Wait for the system's enqueued work for at most timeout_s seconds (polling an

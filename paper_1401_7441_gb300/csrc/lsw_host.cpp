@@ -63,7 +63,13 @@ struct DeviceBuf {
         p = nullptr;
         bytes = b;
         if (b == 0) return cudaSuccess;
-        return cudaMalloc(&p, b);
+        const cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {         // returned to the caller, not left pending for a later check
+            p = nullptr;
+            bytes = 0;
+            (void)cudaGetLastError();
+        }
+        return e;
     }
     template <class T>
     cudaError_t upload(const std::vector<T>& v, cudaStream_t s) {
@@ -188,6 +194,7 @@ struct lsw_system_s {
     // device state
     DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
     DeviceBuf d_plane_items, d_queue;   // plane items of the persistent kernels, their queue counters
+    DeviceBuf d_colz;                   // L' column tables (ColZ) of every atom
     DeviceBuf d_tile_fine, d_listA, d_listB, d_ws, d_status, d_escratch;
     // H/S in the transposed layout: used tiles, per-atom tile tables, product items, the
     // atoms of each slab and the panel buffers of one slab (reused slab after slab)
@@ -212,6 +219,7 @@ struct lsw_system_s {
     int batch_size = 0;
     int tile = 4;
     int64_t slab_mb = PANEL_SLAB_MB;
+    size_t panel_bytes_A = 0, panel_bytes_Q = 0;   // panel buffers of the H/S plan (allocated on first use)
     int64_t hphi_limit = -1;         // option "hphi_limit" (-1: every function)
     int hs_tc = 1;                   // option "hs_tc": FP32 H/S products on the tensor cores
     int persistent = 1;              // option "persistent": bit 0 the backward, bit 1 the forward
@@ -849,8 +857,19 @@ lsw_status build_hs_plan(lsw_system_s* s) {
     CUDA_TRY(s->d_tile_fine.upload(fine, st));
     CUDA_TRY(s->d_listA.upload(fA, st));
     CUDA_TRY(s->d_listB.upload(fB, st));
-    CUDA_TRY(s->d_PA.alloc(std::max<size_t>(maxA, 4) * es));
-    CUDA_TRY(s->d_PQ.alloc(std::max<size_t>(maxQ, 4) * es));
+    // the panel buffers of one slab are allocated by the first call that uses them
+    // (ensure_panels), so a system that is created but not yet run holds none;
+    // lsw_workspace_bytes counts them either way
+    CUDA_TRY(s->d_PA.alloc(0));
+    CUDA_TRY(s->d_PQ.alloc(0));
+    s->panel_bytes_A = std::max<size_t>(maxA, 4) * es;
+    s->panel_bytes_Q = std::max<size_t>(maxQ, 4) * es;
+    return LSW_OK;
+}
+
+lsw_status ensure_panels(lsw_system_s* s) {
+    if (!s->d_PA.p) CUDA_TRY(s->d_PA.alloc(s->panel_bytes_A));
+    if (!s->d_PQ.p) CUDA_TRY(s->d_PQ.alloc(s->panel_bytes_Q));
     return LSW_OK;
 }
 
@@ -877,7 +896,35 @@ lsw_status upload_geometry(lsw_system_s* s) {
         emit_segments(s->N, P, P.c, &seg, &rowptr, &r.segPc, &r.nsegPc, &r.rowPc);
         emit_segments(s->N, P, P.f, &seg, &rowptr, &r.segPf, &r.nsegPf, &r.rowPf);
     }
+    // L' column tables: per (x, y) column the z range of the coarse members and the z hull
+    // of the fine members (the planes the compressed H phi reads there)
+    int64_t ncz = 0;
+    for (int a = 0; a < s->n_atoms; ++a) {
+        recs[a].colz = ncz;
+        ncz += static_cast<int64_t>(s->Lp[a].n[0]) * s->Lp[a].n[1];
+    }
+    std::vector<ColZ> colz(static_cast<size_t>(ncz), ColZ{-1, -1, -1, -1});
+    parallel_for(s->n_atoms, [&](int a) {
+        const LocregHost& P = s->Lp[a];
+        ColZ* t = colz.data() + recs[a].colz;
+        const int64_t N0 = s->N[0], N01 = static_cast<int64_t>(s->N[0]) * s->N[1];
+        auto fold = [&](const std::vector<int64_t>& g, bool fine) {
+            for (int64_t v : g) {
+                const int x = static_cast<int>(v % N0 - P.lo[0]);
+                const int y = static_cast<int>((v / N0) % s->N[1] - P.lo[1]);
+                const int16_t z = static_cast<int16_t>(v / N01 - P.lo[2]);
+                ColZ& e = t[static_cast<int64_t>(y) * P.n[0] + x];
+                int16_t& lo = fine ? e.f0 : e.c0;
+                int16_t& hi = fine ? e.f1 : e.c1;
+                if (lo < 0 || z < lo) lo = z;
+                if (z > hi) hi = z;
+            }
+        };
+        fold(P.c.g, false);
+        fold(P.f.g, true);
+    });
     cudaStream_t st = s->stream;
+    CUDA_TRY(s->d_colz.upload(colz, st));
     CUDA_TRY(s->d_atoms.upload(recs, st));
     CUDA_TRY(s->d_seg.upload(seg, st));
     CUDA_TRY(s->d_rowptr.upload(rowptr, st));
@@ -923,6 +970,8 @@ lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hph
         p.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
         p.seg = static_cast<const Seg*>(s->d_seg.p);
         p.rowptr = static_cast<const int32_t*>(s->d_rowptr.p);
+        p.colz = static_cast<const ColZ*>(s->d_colz.p);
+        p.colz_n = static_cast<int64_t>(s->d_colz.bytes / sizeof(ColZ));
         p.phi = phi;
         p.hphi = hphi;
         p.e_kin = ek;
@@ -1536,6 +1585,7 @@ lsw_status lsw_apply_hamiltonian(lsw_system sys, const void* phi, void* hphi, do
     if (!ek) ek = e0;
     if (!ep) ep = e0 + nf;
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     GraphKey key{phi, hphi, ek, ep};
     return run_maybe_graph(sys, &sys->graphs_h, key, [&](Tracer* tr) { return enqueue_apply(sys, tr, phi, hphi, ek, ep); });
 }
@@ -1545,6 +1595,8 @@ lsw_status lsw_build_matrices(lsw_system sys, const void* phi, const void* hphi,
     if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys || !phi || !hphi || !H || !S) return fail(LSW_ERR_ARG, "lsw_build_matrices: NULL buffer");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
+    if (lsw_status e = ensure_panels(sys); e != LSW_OK) return e;
     GraphKey key{phi, hphi, H, S};
     return run_maybe_graph(sys, &sys->graphs_m, key, [&](Tracer* tr) { return enqueue_matrices(sys, tr, phi, hphi, H, S); });
 }
@@ -1555,6 +1607,8 @@ lsw_status lsw_combine(lsw_system sys, const double* M, const void* phi_in, void
     if (!sys || !M || !phi_in || !phi_out) return fail(LSW_ERR_ARG, "lsw_combine: NULL buffer");
     if (phi_in == phi_out) return fail(LSW_ERR_ARG, "lsw_combine: input and output must not overlap");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
+    if (lsw_status e = ensure_panels(sys); e != LSW_OK) return e;
     return enqueue_combine(sys, nullptr, M, phi_in, phi_out);
 }
 
@@ -1564,6 +1618,8 @@ lsw_status lsw_lowdin_taylor(lsw_system sys, const double* S, const void* phi_in
     if (!sys || !S || !phi_in || !phi_out) return fail(LSW_ERR_ARG, "lsw_lowdin_taylor: NULL buffer");
     if (phi_in == phi_out) return fail(LSW_ERR_ARG, "lsw_lowdin_taylor: input and output must not overlap");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
+    if (lsw_status e = ensure_panels(sys); e != LSW_OK) return e;
     const int64_t nnz = static_cast<int64_t>(sys->col.size());
     if (sys->d_mcoef.bytes < static_cast<size_t>(std::max<int64_t>(nnz, 1)) * sizeof(double)) {
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
@@ -1588,6 +1644,7 @@ lsw_status lsw_foe(lsw_system sys, const double* H, const double* S, double e_mi
     if (static_cast<size_t>(n) * sizeof(int) + 1024 > sys->ctx->max_smem)
         return fail(LSW_ERR_UNSUPPORTED, "lsw_foe: %d functions exceed the shared-memory column map", n);
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     cudaStream_t st = sys->stream;
     const int triple_ctas = std::max(1, std::min(n, 4 * sys->ctx->n_sm));
     if (sys->d_tpos.bytes == 0) {
@@ -1881,6 +1938,7 @@ lsw_status lsw_add_confinement(lsw_system sys, const double* a_dev, const void* 
     if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys || !a_dev || !phi || !hphi) return fail(LSW_ERR_ARG, "lsw_add_confinement: NULL buffer");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     int64_t stride = 0;
     int batch = 0;
     lsw_status e = conf_prepare(sys, &stride, &batch);
@@ -1904,6 +1962,7 @@ lsw_status lsw_precondition(lsw_system sys, const double* a_dev, const double* e
     if (g == gprec) return fail(LSW_ERR_ARG, "lsw_precondition: g and g_prec must not overlap");
     if (iters < 1) return fail(LSW_ERR_ARG, "lsw_precondition: iters %d", iters);
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     int64_t stride = 0;
     int batch = 0;
     lsw_status e = conf_prepare(sys, &stride, &batch);
@@ -1958,6 +2017,7 @@ lsw_status lsw_build_density(lsw_system sys, const void* phi, const double* K, d
         if (fine_dims[d] > (1LL << 30)) return fail(LSW_ERR_ARG, "lsw_build_density: dimension %d too large", d);
     }
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     bool same = sys->dens_ready;
     for (int d = 0; d < 3; ++d) same = same && sys->dens_lo[d] == fine_lo[d] && sys->dens_n[d] == fine_dims[d];
     if (!same) {
@@ -2007,6 +2067,7 @@ lsw_status lsw_apply_hamiltonian_noalloc(lsw_system sys, const void* phi, void* 
             return fail(LSW_ERR_UNSUPPORTED, "locreg box too large for the on-chip pass tiles");
     }
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     void* scratch = nullptr;
     CUDA_TRY(noalloc_scratch(sys->ctx->device, &scratch));
     cudaStream_t st = sys->stream;
@@ -2150,12 +2211,14 @@ lsw_status lsw_workspace_bytes(lsw_system sys, int64_t* bytes) {
                                &sys->d_items, &sys->d_citems, &sys->d_slab_atoms, &sys->d_PA, &sys->d_PQ, &sys->d_mcoef,
                                &sys->d_tpos, &sys->d_diag, &sys->d_ident, &sys->d_foe, &sys->d_foe_scratch,
                                &sys->d_qtab, &sys->d_qtab_off, &sys->d_cbox, &sys->d_cg, &sys->d_cgs,
-                               &sys->d_ws, &sys->d_status, &sys->d_plane_items, &sys->d_queue,
+                               &sys->d_ws, &sys->d_status, &sys->d_plane_items, &sys->d_queue, &sys->d_colz,
                                &sys->d_escratch, &sys->d_phi, &sys->d_hphi, &sys->d_H, &sys->d_S, &sys->d_ek,
                                &sys->d_ep, &sys->d_shift, &sys->d_fn_all, &sys->d_U, &sys->d_dfn,
                                &sys->d_tptr, &sys->d_tfn};
     int64_t b = 0;
     for (auto* p : bufs) b += static_cast<int64_t>(p->bytes);
+    if (!sys->d_PA.p) b += static_cast<int64_t>(sys->panel_bytes_A);   // not allocated yet
+    if (!sys->d_PQ.p) b += static_cast<int64_t>(sys->panel_bytes_Q);
     *bytes = b;
     return LSW_OK;
 }
@@ -2165,6 +2228,7 @@ lsw_status lsw_sync(lsw_system sys, double timeout_s) {
     if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys) return fail(LSW_ERR_ARG, "lsw_sync: NULL system");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     CUDA_TRY(cudaEventRecord(sys->done, sys->stream));
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -2194,6 +2258,7 @@ lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host, 
     if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys || !phi_host || !H_host || !S_host) return fail(LSW_ERR_ARG, "lsw_step_host: NULL argument");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     const int64_t nf = static_cast<int64_t>(sys->sf_atom.size());
     const size_t bphi = static_cast<size_t>(sys->off_L.back()) * sys->esize;
     const size_t bhphi = static_cast<size_t>(sys->off_Lp.back()) * sys->esize;
@@ -2227,6 +2292,7 @@ lsw_status lsw_system_set_stream(lsw_system sys, void* stream) {
     if (!sys) return fail(LSW_ERR_ARG, "lsw_system_set_stream: NULL system");
     if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     CUDA_TRY(cudaStreamSynchronize(sys->stream));
     sys->stream = static_cast<cudaStream_t>(stream);
     return LSW_OK;
@@ -2238,6 +2304,7 @@ lsw_status lsw_profile(lsw_system sys, int32_t enable) {
     if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (enable != 0 && enable != 1) return fail(LSW_ERR_ARG, "lsw_profile: enable %d", enable);
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     CUDA_TRY(cudaStreamSynchronize(sys->stream));
     drop_graphs(sys);
     sys->direct_tr.reset();
@@ -2251,6 +2318,7 @@ lsw_status lsw_profile_read(lsw_system sys, int32_t max_kinds, int32_t* n_kinds,
     if (!sys || !n_kinds || !ms || !launches) return fail(LSW_ERR_ARG, "lsw_profile_read: NULL argument");
     if (sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     CUDA_TRY(cudaStreamSynchronize(sys->stream));
     harvest(sys, sys->direct_tr.get());
     for (auto* c : {&sys->graphs_h, &sys->graphs_m})
@@ -2270,6 +2338,7 @@ lsw_status lsw_set_option(lsw_system sys, const char* name, int64_t value) {
     if (sys && sys->ctx->host_only) return fail(LSW_ERR_STATE, "host-only context: no device work");
     if (!sys || !name) return fail(LSW_ERR_ARG, "lsw_set_option: NULL argument");
     CUDA_TRY(cudaSetDevice(sys->ctx->device));
+    (void)cudaGetLastError();   // an earlier call's error is not this call's
     if (std::strcmp(name, "batch") == 0) {
         if (value < 1 || value > 4096) return fail(LSW_ERR_ARG, "lsw_set_option: batch %lld", static_cast<long long>(value));
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
@@ -2433,6 +2502,7 @@ lsw_status lsw_save(lsw_system sys, const void* phi_dev, const char* path) {
     if (phi_dev) {
         buf.resize(static_cast<size_t>(total) * sys->esize);
         CUDA_TRY(cudaSetDevice(sys->ctx->device));
+        (void)cudaGetLastError();   // an earlier call's error is not this call's
         CUDA_TRY(cudaStreamSynchronize(sys->stream));
         CUDA_TRY(cudaMemcpy(buf.data(), phi_dev, buf.size(), cudaMemcpyDeviceToHost));
     }

@@ -51,6 +51,13 @@ struct AtomRec {
     int32_t nsegLc, nsegLf, nsegPc, nsegPf;
     int64_t segLc, segLf, segPc, segPf;  // first index in the global Seg array
     int64_t rowLc, rowLf, rowPc, rowPf;  // first index of the per-row CSR (n_rows + 1)
+    int64_t colz;                // first entry of the L' column table (n_x' n_y' ColZ)
+};
+
+// Per (x, y) column of an L' box (entry y n_x' + x): the z range of its coarse members and
+// the z hull of its fine members, L' box coordinates; -1, -1: none.
+struct ColZ {
+    int16_t c0, c1, f0, f1;
 };
 
 // One support function's real-space block in the density store (Eq. density): the
@@ -169,6 +176,8 @@ struct HphiLaunch {
     const AtomRec* atoms;
     const Seg* seg;
     const int32_t* rowptr;
+    const ColZ* colz;            // L' column tables (NULL: the kinetic z arm computes every plane)
+    int64_t colz_n;
     const void* phi;
     void* hphi;
     double* e_kin;

@@ -1061,7 +1061,16 @@ __global__ void __launch_bounds__(128) k_kin_z(HphiLaunch a) {
             const int64_t pnp = static_cast<int64_t>(nxp) * nyp;
             const int64_t gcol = static_cast<int64_t>(yb) * nxp + xb;
             const T ks = static_cast<T>(a.kin_scale);
-            for (int b0 = 0; b0 < nzp; b0 += BB) {
+            // the planes of this column the compressed H phi reads: the coarse members' z
+            // range where the pair holds type 0 (tb = 0), else the fine members' z hull (the
+            // D values of the pair are zero off those, so E_kin loses no term)
+            int zlo = 0, zhi = nzp - 1;
+            if (a.colz) {
+                const ColZ cz = LD(a.colz, a.atoms[r.atom].colz + gcol, a.colz_n);
+                zlo = tb == 0 ? cz.c0 : cz.f0;
+                zhi = tb == 0 ? cz.c1 : cz.f1;
+            }
+            for (int b0 = zlo < 0 ? nzp : (zlo / BB) * BB; b0 <= zhi; b0 += BB) {
                 T k0[KW], k1[KW], o0[BB], o1[BB];
                 swin(k0, col, t, 128, b0 + dz - KIN_HALF, nz, col_n, st);
                 swin(k1, col, nz * 128 + t, 128, b0 + dz - KIN_HALF, nz, col_n, st);
@@ -1235,8 +1244,9 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
     __shared__ int roff[256];                      // coefficient offset of the row's coarse segment
     __shared__ int fr0[256], fr1[256];             // fine segment range of the row (L' keys)
     __shared__ int16_t fx0[256], fx1[256];         // hull of the row's fine members, -1: none
-    __shared__ int rq0[128], rq1[128], rqp[129];   // per row block: column range, prefix of widths
-    __shared__ int ntask, ylo, yhi;
+    __shared__ int cq0[64], cq1[64], pq[65];       // y pass, per block of NB rows: column range, prefix
+    __shared__ int rq0[128], rq1[128], rqp[129];   // kinetic y arm, per (x type, block of BB rows): the same
+    __shared__ int ntask, ntask2, ylo, yhi;
     __shared__ unsigned char rowf[4][128], colf[4][128];   // D plane: nonzero per (type, row / column)
     T* sm = reinterpret_cast<T*>(smem_raw);
     const FnRec r = a.fn[fl];
@@ -1348,7 +1358,7 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
         fx1[y] = static_cast<int16_t>(q1 > q0 ? LD(a.seg, at.segPf + q1 - 1, a.seg_n).x1 : -1);
     }
     cp_wait_group<1>();   // the Bb plane (group 2 may still be in flight)
-    if (threadIdx.x == 0) ntask = 0;
+    if (threadIdx.x == 0) ntask = ntask2 = 0;
     __syncthreads();
     const int64_t mid_n = 2LL * nyp * X;
     const int64_t gs_n = 4LL * nyp * nxp;
@@ -1368,24 +1378,16 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
             hi = fx1[b];
         }
     };
-    if constexpr (NS > 0) {
-        // ---- potential part on the tensor cores -> Gs (every row and column of the plane)
-        if (yhi_ >= 0 && !bwd_tc_potential<NS>(reinterpret_cast<const float*>(Bb), bb_room, X, Y, nyp, nxp, dx, dy,
-                                                K1, N1, K2, N2, FY_PART, FX_PART, XR, sFy, sFx, sXr,
-                                                reinterpret_cast<float*>(Gs), smem_raw, smem_n * 4, st)) {
-            if (threadIdx.x == 0) atomicOr(st, ST_WAIT_TIMEOUT);
-        }
-    }
+    // ---- column ranges per row block, with their prefix sums, in one phase: the y pass's
+    //      (FMA version; blocks of NB rows: for row b and pair by its blocks k = lo/NB ..
+    //      hi/NB of the needed range read x' in [2 (k NB + dx), 2 (k NB + NB - 1 + dx) + 30])
+    //      and the kinetic y arm's (per x type bx, the pair of types bx, bx + 2, and block
+    //      of BB rows: the hull of the rows' needed ranges, the coarse members where the
+    //      pair holds type 0, else the fine members)
+    const int nbb = (yhi_ - ylo_ + NB) / NB;
+    const int nbyk = (yhi_ - ylo_ + BB) / BB;
     if (yhi_ >= 0) {
-      if constexpr (NS == 0) {
-        // ---- y pass: blocks of NB rows b within [ylo, yhi], and per block only the columns
-        //      x' the x pass reads: for row b and pair by its blocks k = lo/NB .. hi/NB of
-        //      the needed range read x' in [2 (k NB + dx), 2 (k NB + NB - 1 + dx) + 30]
-        const int nbb = (yhi_ - ylo_ + NB) / NB;
-        int* cq0 = rq0;
-        int* cq1 = rq1;
-        int* pq = rqp;
-        if (threadIdx.x < nbb) {
+        if (NS == 0 && static_cast<int>(threadIdx.x) < nbb) {
             const int q = threadIdx.x;
             int c0 = X, c1 = -1;
             for (int b = ylo_ + q * NB; b < min(ylo_ + (q + 1) * NB, yhi_ + 1); ++b)
@@ -1399,12 +1401,43 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
             cq0[q] = max(c0, 0);
             cq1[q] = min(c1, X - 1);
         }
+        const int t2 = static_cast<int>(threadIdx.x) - 128;
+        if (t2 >= 0 && t2 < 2 * nbyk) {
+            const int bx = t2 >= nbyk, q = t2 - bx * nbyk;
+            const bool coarse = bz == 0 && bx == 0;
+            int c0 = nxp, c1 = -1;
+            for (int b = ylo_ + q * BB; b < min(ylo_ + (q + 1) * BB, yhi_ + 1); ++b) {
+                const int lo = coarse ? rx0[b] : fx0[b], hi = coarse ? rx1[b] : fx1[b];
+                if (lo < 0) continue;
+                c0 = min(c0, lo);
+                c1 = max(c1, hi);
+            }
+            rq0[t2] = c0;
+            rq1[t2] = c1;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (NS == 0 && threadIdx.x == 0) {
             pq[0] = 0;
             for (int q = 0; q < nbb; ++q) pq[q + 1] = pq[q] + max(0, cq1[q] - cq0[q] + 1);
         }
+        if (threadIdx.x == 32) {
+            rqp[0] = 0;
+            for (int i = 0; i < 2 * nbyk; ++i) rqp[i + 1] = rqp[i] + max(0, rq1[i] - rq0[i] + 1);
+        }
         __syncthreads();
+    }
+    if constexpr (NS > 0) {
+        // ---- potential part on the tensor cores -> Gs (every row and column of the plane)
+        if (yhi_ >= 0 && !bwd_tc_potential<NS>(reinterpret_cast<const float*>(Bb), bb_room, X, Y, nyp, nxp, dx, dy,
+                                                K1, N1, K2, N2, FY_PART, FX_PART, XR, sFy, sFx, sXr,
+                                                reinterpret_cast<float*>(Gs), smem_raw, smem_n * 4, st)) {
+            if (threadIdx.x == 0) atomicOr(st, ST_WAIT_TIMEOUT);
+        }
+    }
+    if (yhi_ >= 0) {
+      if constexpr (NS == 0) {
+        // ---- y pass: blocks of NB rows b within [ylo, yhi], per block only the columns
+        //      listed above
         {
             const int ntk = pq[nbb];
             for (int tk = threadIdx.x; tk < ntk; tk += blockDim.x) {
@@ -1486,9 +1519,7 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
         }
         if (dplane) {
             int nt;
-            __syncthreads();
-            if (threadIdx.x == 0) ntask = 0;
-            __syncthreads();
+            __syncthreads();   // the D plane's zero flags
             // ---- kinetic x arm: (by, row b, x block of BB) over the needed range of rows whose
             //      D rows are nonzero
             for (int b = ylo_ + threadIdx.x; b <= yhi_; b += blockDim.x) {
@@ -1500,14 +1531,14 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
                     need(by, b, lo, hi);
                     if (lo < 0) continue;
                     const int k0 = lo / BB, k1 = hi / BB;
-                    const int base = atomicAdd(&ntask, k1 - k0 + 1);
+                    const int base = atomicAdd(&ntask2, k1 - k0 + 1);
                     for (int k = k0; k <= k1; ++k)
                         if (base + k - k0 < BWD_MAX_TASKS) task[base + k - k0] = (by << 24) | (b << 12) | k;
                 }
             }
             __syncthreads();
-            nt = min(ntask, BWD_MAX_TASKS);
-            if (ntask > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
+            nt = min(ntask2, BWD_MAX_TASKS);
+            if (ntask2 > BWD_MAX_TASKS && threadIdx.x == 0) atomicOr(a.status, ST_BAD_BOX);
             for (int it = threadIdx.x; it < nt; it += blockDim.x) {
                 const int code = task[it];
                 const int by = code >> 24, b = (code >> 12) & 4095, x0 = (code & 4095) * BB;
@@ -1533,30 +1564,8 @@ __device__ __forceinline__ void bwd_plane(const HphiLaunch& a, int fl, int zb, i
                 }
             }
             __syncthreads();   // the x arm's Gs updates are done
-            // ---- kinetic y arm: per x type bx (the pair of types bx, bx + 2) and block q of BB
-            //      rows, the columns of the hull of the rows' needed ranges (coarse members
-            //      where the pair holds type 0, else fine members); task (bx, q, column),
-            //      consecutive columns on consecutive threads
-            const int nbyk = (yhi_ - ylo_ + BB) / BB;
-            if (threadIdx.x < 2 * nbyk) {
-                const int bx = threadIdx.x >= nbyk, q = threadIdx.x - bx * nbyk;
-                const bool coarse = bz == 0 && bx == 0;
-                int c0 = nxp, c1 = -1;
-                for (int b = ylo_ + q * BB; b < min(ylo_ + (q + 1) * BB, yhi_ + 1); ++b) {
-                    const int lo = coarse ? rx0[b] : fx0[b], hi = coarse ? rx1[b] : fx1[b];
-                    if (lo < 0) continue;
-                    c0 = min(c0, lo);
-                    c1 = max(c1, hi);
-                }
-                rq0[threadIdx.x] = c0;
-                rq1[threadIdx.x] = c1;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                rqp[0] = 0;
-                for (int i = 0; i < 2 * nbyk; ++i) rqp[i + 1] = rqp[i] + max(0, rq1[i] - rq0[i] + 1);
-            }
-            __syncthreads();
+            // ---- kinetic y arm: tasks (x type bx, block q of BB rows, column) over the column
+            //      ranges listed above, consecutive columns on consecutive threads
             nt = rqp[2 * nbyk];
             for (int it = threadIdx.x; it < nt; it += blockDim.x) {
                 int lo = 0, hi = 2 * nbyk - 1;              // the entry i with rqp[i] <= it < rqp[i + 1]

@@ -37,6 +37,8 @@ from . import lsw
 
 DENSITY = 64 / 30.0 ** 3          # atoms per bohr^3 of the 64-atom workload
 RADII = (5.0, 6.0, 7.0, 8.0)
+SLAB_MB = 2048                    # H/S panel budget of a served system (library option "slab_mb")
+CACHE_SLACK = 40e9                # bytes PyTorch may keep cached but unused between requests
 
 
 @dataclass
@@ -170,6 +172,36 @@ class Server:
         self.graphs = graphs
         self.resident: "OrderedDict[int, _Entry]" = OrderedDict()
         self.used = 0
+        self._ready, self._inflight = [], []
+
+    def _retry_oom(self, fn):
+        """fn(), and once more after PyTorch's cached blocks went back to the driver if the
+        library ran out of device memory (a library call that fails for memory fails before
+        it enqueues anything; the cache holds the tensors of finished requests, which the
+        library's own allocations cannot use)."""
+        try:
+            return fn()
+        except lsw.LswError as e:
+            if "out of memory" not in str(e):
+                raise
+            self.torch.cuda.empty_cache()
+            try:
+                return fn()
+            except lsw.LswError as e2:
+                free, total = self.torch.cuda.mem_get_info()
+
+                def held(jobs):
+                    systems = {id(j.system): j.system for j in jobs if getattr(j, "system", None) is not None}
+                    return len(systems), sum(lsw.lsw_workspace_bytes(x.sys) for x in systems.values()) / 1e9
+
+                rs = {id(e.system): e.system for e in self.resident.values()}
+                raise lsw.LswError(e2.status, "%s (device free %.1f of %.1f GB; PyTorch reserved %.1f GB, allocated "
+                                   "%.1f GB; budget used %.1f of %.1f GB; systems prepared %d (%.1f GB), in flight %d "
+                                   "(%.1f GB), resident %d (%.1f GB))"
+                                   % (e2, free / 1e9, total / 1e9, self.torch.cuda.memory_reserved() / 1e9,
+                                      self.torch.cuda.memory_allocated() / 1e9, self.used / 1e9, self.budget / 1e9,
+                                      *held(list(self._ready)), *held(list(self._inflight)), len(rs),
+                                      sum(lsw.lsw_workspace_bytes(x.sys) for x in rs.values()) / 1e9)) from e2
 
     # ---------------------------------------------------------------- host preparation
     def _prepare(self, job: _Job):
@@ -177,8 +209,12 @@ class Server:
         if job.req.kind == "charged" and job.parent is not None:
             job.system = job.parent.system            # same geometry: reuse the system
         else:
-            job.system = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff,
-                                    wl.pair_mode, wl.lprime_margin, 0, self.precision, ctx=self.ctx)
+            job.system = self._retry_oom(lambda: lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf,
+                                                            wl.pair_cutoff, wl.pair_mode, wl.lprime_margin, 0,
+                                                            self.precision, ctx=self.ctx))
+            # H/S panels of at most SLAB_MB per system (allocated when the system first runs,
+            # counted by lsw_workspace_bytes before that)
+            lsw.lsw_set_option(job.system.sys, "slab_mb", SLAB_MB)
             if not self.graphs:
                 lsw.lsw_set_option(job.system.sys, "graph", 0)
         S = job.system
@@ -218,7 +254,7 @@ class Server:
             H = torch.empty(nnz, dtype=torch.float64, device="cuda")
             Sm = torch.empty(nnz, dtype=torch.float64, device="cuda")
             lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
-            lsw.lsw_build_matrices(S.sys, phi, hphi, H, Sm)
+            self._retry_oom(lambda: lsw.lsw_build_matrices(S.sys, phi, hphi, H, Sm))
             out = {k: torch.empty(v.numel(), dtype=torch.float64, pin_memory=True)
                    for k, v in (("H", H), ("S", Sm), ("ek", ek), ("ep", ep))}
             for k, v in (("H", H), ("S", Sm), ("ek", ek), ("ep", ep)):
@@ -245,6 +281,11 @@ class Server:
             self.used += ent.bytes - job.est_bytes
             self.resident[job.req.rid] = ent
         job.bufs = {}
+        # PyTorch caches freed blocks per stream; past CACHE_SLACK of cached, unused bytes
+        # they go back to the driver, where the library's own allocations can use them
+        torch = self.torch
+        if torch.cuda.memory_reserved() - torch.cuda.memory_allocated() > CACHE_SLACK:
+            torch.cuda.empty_cache()
         return res
 
     def _evict(self, need):
@@ -259,6 +300,11 @@ class Server:
             self.used -= ent.bytes
             ent.system.close()
             ent.phi = None
+            # the evicted request's tensors go back to the driver, where the library's own
+            # allocations (workspace, panels) can use them
+            torch = getattr(self, "torch", None)
+            if torch is not None:
+                torch.cuda.empty_cache()
         return self.used + need <= self.budget
 
     def _admit(self, cand, inflight, max_inflight):
@@ -303,6 +349,7 @@ class Server:
         ready: list[_Job] = []
         lock = threading.Lock()
         inflight: list[_Job] = []
+        self._ready, self._inflight = ready, inflight      # for the out-of-memory report
         results: list[Result] = []
         errors: list[BaseException] = []
         max_inflight = max_inflight or len(self.streams)
