@@ -67,3 +67,34 @@ def test_budget_evicts_and_still_serves():
         assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
     finally:
         srv.close()
+
+
+def test_workspace_bytes_count_the_panels_before_the_first_run():
+    # the H/S panel buffers are allocated by the first lsw_build_matrices; the bytes a
+    # request loop budgets for a system (lsw_workspace_bytes) are the same before and after
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_7441_gb300 import inputs as I
+    from tests.lib_support import ensure_built
+    ensure_built()
+    wl = I.scaled("atoms64", 10, seed=3)
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   wl.lprime_margin, 0, lsw.LSW_FP32, device=0, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        before = lsw.lsw_workspace_bytes(S.sys)
+        lsw.lsw_set_option(S.sys, "slab_mb", 64)           # re-planned, still not allocated
+        planned = lsw.lsw_workspace_bytes(S.sys)
+        phi = torch.zeros(S.total_L, device="cuda")
+        V = torch.tensor(I.potential(wl), dtype=torch.float32, device="cuda")
+        lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
+        hphi = torch.zeros(S.total_Lp, device="cuda")
+        H = torch.zeros(len(S.col), dtype=torch.float64, device="cuda")
+        Sm = torch.zeros_like(H)
+        lsw.lsw_apply_hamiltonian(S.sys, phi, hphi)
+        lsw.lsw_build_matrices(S.sys, phi, hphi, H, Sm)
+        lsw.lsw_sync(S.sys, 60.0)
+        assert before > 0 and planned > 0
+        assert lsw.lsw_workspace_bytes(S.sys) == planned
+    finally:
+        S.close()
