@@ -1,6 +1,7 @@
 """Autotuner for the library's launch shapes: functions per H phi batch ("batch"), the
 plane kernels of split-bfloat16 systems on the FMA units or the tensor cores ("xy_tc"),
-and the H/S tile edge ("tile").
+persistent grids for the FMA plane kernels ("persistent": bit 0 backward, bit 1 forward)
+and the forward member block lists ("fwd_list"), and the H/S tile edge ("tile").
 
 Each candidate is set through lsw_set_option, warmed once, then timed with CUDA events
 on the system's stream; the fastest is kept.  Everything runs in the library's kernels;
@@ -13,6 +14,7 @@ from . import lsw
 
 BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512, 1024, 2048, 4096)
 TILE_CANDIDATES = (3, 4, 5, 6, 7, 8)
+PERSISTENT_CANDIDATES = (1, 0, 3, 2)
 
 
 def _time(fn, stream, reps):
@@ -60,6 +62,20 @@ def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDID
         except lsw.LswError:              # locregs too large for the tensor-core plane tiles
             pass
         lsw.lsw_set_option(system.sys, "xy_tc", best_x)
+    hphi_ms = lambda: _time(lambda: lsw.lsw_apply_hamiltonian(system.sys, phi, hphi, e_kin, e_pot), stream, reps)
+    best_p, best_l = 1, 1
+    if not best_x:                      # the FMA plane kernels run: their grid forms and work lists
+        report["persistent"] = {}
+        for pv in PERSISTENT_CANDIDATES:
+            lsw.lsw_set_option(system.sys, "persistent", pv)
+            report["persistent"][pv] = hphi_ms()
+        best_p = min(report["persistent"], key=report["persistent"].get)
+        lsw.lsw_set_option(system.sys, "persistent", best_p)
+        report["fwd_list"] = {1: report["persistent"][best_p]}
+        lsw.lsw_set_option(system.sys, "fwd_list", 0)
+        report["fwd_list"][0] = hphi_ms()
+        best_l = min(report["fwd_list"], key=report["fwd_list"].get)
+        lsw.lsw_set_option(system.sys, "fwd_list", best_l)
     lsw.lsw_apply_hamiltonian(system.sys, phi, hphi, e_kin, e_pot)
     for t in tiles:
         lsw.lsw_set_option(system.sys, "tile", t)
@@ -68,5 +84,5 @@ def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDID
         if best_t is None or ms < report["tile"][best_t]:
             best_t = t
     lsw.lsw_set_option(system.sys, "tile", best_t)
-    report["chosen"] = {"batch": best_b, "tile": best_t, "xy_tc": best_x}
+    report["chosen"] = {"batch": best_b, "tile": best_t, "xy_tc": best_x, "persistent": best_p, "fwd_list": best_l}
     return report

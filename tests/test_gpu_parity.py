@@ -187,6 +187,42 @@ def test_persistent_plane_kernels_same_bits(prec):
     check_functions(wl, geo, b, ref, 1e-12 if prec == lsw.LSW_FP64 else 1e-5)
 
 
+def test_autotuner_choices_keep_the_results():
+    # the autotuner sweeps batch, xy_tc, persistent, fwd_list and tile; whatever it picks,
+    # H phi is the same bits as the default form's, and H/S agree within the reduced
+    # precision's tolerance (another tile edge regroups the FP32 per-tile sums)
+    import torch
+    from paper_1401_7441_gb300 import autotune
+    wl = I.scaled("atoms1200", 10, seed=5)
+    base = gpu_run(wl, phi_fn(wl), lsw.LSW_FP32)
+    S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
+                   wl.lprime_margin, 0, lsw.LSW_FP32, device=0, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        phi = torch.tensor(base["phi"], dtype=torch.float32, device="cuda")
+        V = torch.tensor(I.potential(wl), dtype=torch.float32, device="cuda")
+        lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
+        hphi = torch.full((S.total_Lp,), float("nan"), dtype=torch.float32, device="cuda")
+        ek = torch.zeros(S.n_sf, dtype=torch.float64, device="cuda")
+        ep = torch.zeros_like(ek)
+        H = torch.zeros(len(S.col), dtype=torch.float64, device="cuda")
+        Sm = torch.zeros_like(H)
+        rep = autotune.autotune(S, phi, hphi, H, Sm, ek, ep, torch.cuda.current_stream(),
+                                batches=(4, 16, 64), tiles=(4, 6))
+        assert set(rep["chosen"]) >= {"batch", "tile", "xy_tc", "persistent", "fwd_list"}
+        H.zero_()
+        Sm.zero_()
+        lsw.lsw_apply_hamiltonian(S.sys, phi, hphi, ek, ep)
+        lsw.lsw_build_matrices(S.sys, phi, hphi, H, Sm)
+        lsw.lsw_sync(S.sys, 120.0)
+        got = hphi.double().cpu().numpy()
+        gap = np.isnan(base["hphi"])
+        assert np.array_equal(got[~gap], base["hphi"][~gap])
+        assert np.max(np.abs(Sm.cpu().numpy() - base["S"])) <= 1e-5 * max(1.0, np.max(np.abs(base["S"])))
+        assert np.max(np.abs(H.cpu().numpy() - base["H"])) <= 1e-5 * np.max(np.abs(base["H"]))
+    finally:
+        S.close()
+
+
 @pytest.mark.parametrize("prec", [lsw.LSW_FP64, lsw.LSW_FP32, lsw.LSW_FP32_BF16X])
 def test_atoms64_full_size_sampled(prec):
     wl = I.atoms64()
