@@ -297,18 +297,27 @@ __device__ __forceinline__ void fwd_block<float>(const float (&w0)[FW], const fl
         u[2 * j + 1] = acc.y;
     }
 }
+// The tap loop outside, the NB independent accumulators inside: each accumulator sees the
+// same operations in the same order (same bits), and consecutive instructions belong to
+// different dependency chains.
 template <int NB>
 __device__ __forceinline__ void bwd_block_f2(const float (&w)[2 * NB + 29], float (&s)[NB], float (&d)[NB]) {
+    float2 acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < FWD_TAPS; ++m) {
+        const float2 t = c_fwd2_bwd[m];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const float a = w[2 * j + m];
+            acc[j] = __ffma2_rn(t, make_float2(a, a), acc[j]);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < FWD_TAPS; ++m) {
-            const float a = w[2 * j + m];
-            acc = __ffma2_rn(c_fwd2_bwd[m], make_float2(a, a), acc);
-        }
-        s[j] = acc.x;
-        d[j] = acc.y;
+        s[j] = acc[j].x;
+        d[j] = acc[j].y;
     }
 }
 template <>
@@ -322,17 +331,23 @@ __device__ __forceinline__ void bwd_block<float, 8>(const float (&w)[45], float 
 template <>
 __device__ __forceinline__ void kin_block<float>(const float (&k0)[KW], const float (&k1)[KW], float (&o0)[BB],
                                                  float (&o1)[BB]) {
+    float2 acc[BB];
+#pragma unroll
+    for (int j = 0; j < BB; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = 0; l < KIN_TAPS; ++l) {
+        const float2 t0 = c_kin2[0][l], t1 = c_kin2[1][l];
+#pragma unroll
+        for (int j = 0; j < BB; ++j) {
+            const float a = k0[j + l], b = k1[j + l];
+            acc[j] = __ffma2_rn(t0, make_float2(a, a), acc[j]);
+            acc[j] = __ffma2_rn(t1, make_float2(b, b), acc[j]);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < BB; ++j) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int l = 0; l < KIN_TAPS; ++l) {
-            const float a = k0[j + l], b = k1[j + l];
-            acc = __ffma2_rn(c_kin2[0][l], make_float2(a, a), acc);
-            acc = __ffma2_rn(c_kin2[1][l], make_float2(b, b), acc);
-        }
-        o0[j] = acc.x;
-        o1[j] = acc.y;
+        o0[j] = acc[j].x;
+        o1[j] = acc[j].y;
     }
 }
 #endif
