@@ -1052,7 +1052,7 @@ def _timed_steps(lsw, torch, S, b, stream, steps, flush):
 
 
 def compare_main(args):
-    """North-star comparison on one system: the served form (split-bfloat16 z stage,
+    """Served form against the plain form on one system: the served form (split-bfloat16 z stage,
     FP32 elsewhere, batched, graphs, autotuned) against the plain per-locreg FP64 GPU form
     (FP64, one function per batch, no graphs), both through the library; every H phi
     element and every H/S entry of the served form against the FP64 form, and both

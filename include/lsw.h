@@ -52,7 +52,7 @@ typedef enum {
     LSW_ERR_CUDA = 3,         /* a CUDA runtime call failed                      */
     LSW_ERR_TIMEOUT = 4,      /* lsw_sync: the device did not finish in time     */
     LSW_ERR_STATE = 5,        /* wrong call order (e.g. no potential set)        */
-    LSW_ERR_UNSUPPORTED = 6,  /* valid but outside what this build handles       */
+    LSW_ERR_UNSUPPORTED = 6,  /* valid but outside what the library supports    */
     LSW_ERR_IO = 7            /* lsw_save / lsw_load: file cannot be written/read */
 } lsw_status;
 
