@@ -408,18 +408,21 @@ def _full_size_sampled(wl, prec, options, fs, rows, tol):
 
 
 def test_atoms10k_full_size_sampled_split_bf16():
-    # 28,000 functions at the launch shape the benchmark's autotuner picked on a GB300
-    # (batch 512, tile edge 4); every L' element of the sampled functions checked
+    # 28,000 functions at the launch shape the benchmark's autotuner picks on a GB300
+    # (batch 4096, tile edge 6, the persistent backward plane kernel and the forward
+    # member block lists, both defaults); every L' element of the sampled functions
+    # checked, in the first, a middle and the last batch
     wl = I.atoms10k()
     fs = [0, 1, 2, 3, 4, 5, 6, 7, 13999, 27999]
-    _full_size_sampled(wl, lsw.LSW_FP32_BF16X, {"batch": 512, "tile": 4}, fs, [0, 1, 2], 1e-5)
+    _full_size_sampled(wl, lsw.LSW_FP32_BF16X, {"batch": 4096, "tile": 6}, fs, [0, 1, 2], 1e-5)
 
 
 def test_atoms1200_full_size_sampled_fp32():
-    # 4,096 functions on radii 5-8 bohr (uneven locregs in one batch)
+    # 4,096 functions on radii 5-8 bohr, all in one batch (one launch per stage) at the
+    # benchmark's autotuned tile edge 8
     wl = I.atoms1200()
     fs = list(range(12)) + [2047, 4095]
-    _full_size_sampled(wl, lsw.LSW_FP32, {"batch": 128}, fs, [0, 1, 4], 1e-5)
+    _full_size_sampled(wl, lsw.LSW_FP32, {"batch": 4096, "tile": 8}, fs, [0, 1, 4], 1e-5)
 
 
 def test_fp64_largest_locregs_plane_kernel_without_staging():
