@@ -371,7 +371,11 @@ lsw_status lsw_sync(lsw_system sys, double timeout_s);
 
 /* End-to-end step through host memory: copy phi from host (pinned or pageable),
  * apply H, build H_ab and S_ab, and copy the results back; returns when done.
- * hphi_host, e_kin_host and e_pot_host may be NULL (not copied back). */
+ * hphi_host, e_kin_host and e_pot_host may be NULL (not copied back).  The copies are
+ * pipelined with the H phi batches on two copy streams of the system: batch i's phi
+ * goes up while batch i - 1 runs, and its H phi comes back while later batches run (with
+ * pinned host buffers the copies overlap the kernels; pageable ones are still correct).
+ * The H phi batches of this call are not captured in a CUDA graph; H/S is. */
 lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host,
                          double* H_host, double* S_host, double* e_kin_host,
                          double* e_pot_host);

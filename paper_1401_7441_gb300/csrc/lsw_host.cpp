@@ -195,6 +195,7 @@ struct lsw_system_s {
     DeviceBuf d_atoms, d_seg, d_rowptr, d_fn, d_offL, d_offLp, d_sfatom, d_rowp, d_col;
     DeviceBuf d_plane_items, d_queue;   // plane items of the persistent kernels, their queue counters
     DeviceBuf d_colz;                   // L' column tables (ColZ) of every atom
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;   // lsw_step_host's copy streams
     DeviceBuf d_tile_fine, d_listA, d_listB, d_ws, d_status, d_escratch;
     // H/S in the transposed layout: used tiles, per-atom tile tables, product items, the
     // atoms of each slab and the panel buffers of one slab (reused slab after slab)
@@ -958,13 +959,23 @@ void harvest(lsw_system_s* s, Tracer* tr) {
     tr->pending = false;
 }
 
-lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hphi, double* ek, double* ep) {
+struct NoHook {
+    cudaError_t operator()(size_t) const { return cudaSuccess; }
+};
+
+// The batches of H phi on the system's stream; before(i) and after(i) enqueue what batch
+// i waits for and what waits for it (the host-buffer step's copies).
+template <class Before, class After>
+lsw_status enqueue_apply_hooked(lsw_system_s* s, Tracer* tr, const void* phi, void* hphi, double* ek, double* ep,
+                                Before before, After after) {
     cudaStream_t st = s->stream;
     int64_t nf = static_cast<int64_t>(s->sf_atom.size());
     if (s->hphi_limit >= 0) nf = std::min<int64_t>(nf, s->hphi_limit);
     CUDA_TRY(cudaMemsetAsync(ek, 0, nf * sizeof(double), st));
     CUDA_TRY(cudaMemsetAsync(ep, 0, nf * sizeof(double), st));
-    for (const Batch& b : s->batches) {
+    for (size_t bi = 0; bi < s->batches.size(); ++bi) {
+        const Batch& b = s->batches[bi];
+        CUDA_TRY(before(bi));
         HphiLaunch p = b.proto;
         p.tr = tr;
         p.atoms = static_cast<const AtomRec*>(s->d_atoms.p);
@@ -993,8 +1004,13 @@ lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hph
         p.n_atoms = s->n_atoms;
         if (p.queue) CUDA_TRY(cudaMemsetAsync(p.queue, 0, 2 * sizeof(int), st));
         CUDA_TRY(enqueue_hphi_batch(p, st));
+        CUDA_TRY(after(bi));
     }
     return LSW_OK;
+}
+
+lsw_status enqueue_apply(lsw_system_s* s, Tracer* tr, const void* phi, void* hphi, double* ek, double* ep) {
+    return enqueue_apply_hooked(s, tr, phi, hphi, ek, ep, NoHook{}, NoHook{});
 }
 
 PackLaunch pack_launch(lsw_system_s* s, Tracer* tr, const PanelSlab& sl, const void* phi, const void* hphi, void* out) {
@@ -1513,6 +1529,8 @@ lsw_status lsw_system_destroy(lsw_system sys) {
     if (!sys->ctx->host_only) cudaSetDevice(sys->ctx->device);
     drop_graphs(sys);
     if (sys->done) cudaEventDestroy(sys->done);
+    if (sys->copy_in) cudaStreamDestroy(sys->copy_in);
+    if (sys->copy_out) cudaStreamDestroy(sys->copy_out);
     sys->ctx->live_systems--;
     delete sys;
     return LSW_OK;
@@ -2271,19 +2289,92 @@ lsw_status lsw_step_host(lsw_system sys, const void* phi_host, void* hphi_host, 
         CUDA_TRY(sys->d_ek.alloc(nf * sizeof(double)));
         CUDA_TRY(sys->d_ep.alloc(nf * sizeof(double)));
     }
+    // Pipelined: Phi goes up batch by batch on one copy stream, each H phi batch waiting only
+    // for its own functions; H phi comes back batch by batch on another copy stream while
+    // the later batches run; H and S follow the last batch (they need every function).
+    // The H phi batches are enqueued directly (no graph: their waits are on events of
+    // this call).
+    if (!sys->V) return fail(LSW_ERR_STATE, "lsw_step_host: no potential (lsw_set_potential)");
     cudaStream_t st = sys->stream;
-    CUDA_TRY(cudaMemcpyAsync(sys->d_phi.p, phi_host, bphi, cudaMemcpyHostToDevice, st));
-    lsw_status r = lsw_apply_hamiltonian(sys, sys->d_phi.p, sys->d_hphi.p, static_cast<double*>(sys->d_ek.p),
-                                         static_cast<double*>(sys->d_ep.p));
+    if (!sys->copy_in) CUDA_TRY(cudaStreamCreateWithFlags(&sys->copy_in, cudaStreamNonBlocking));
+    if (!sys->copy_out) CUDA_TRY(cudaStreamCreateWithFlags(&sys->copy_out, cudaStreamNonBlocking));
+    const size_t nb = sys->batches.size();
+    std::vector<cudaEvent_t> ev;
+    struct EvGuard {
+        std::vector<cudaEvent_t>* v;
+        ~EvGuard() {
+            for (cudaEvent_t e : *v) cudaEventDestroy(e);
+        }
+    } guard{&ev};
+    auto event = [&](cudaEvent_t* e) -> cudaError_t {
+        cudaError_t c = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        if (c == cudaSuccess) ev.push_back(*e);
+        return c;
+    };
+    const size_t es = sys->esize;
+    const int64_t* oL = sys->off_L.data();
+    const int64_t* oP = sys->off_Lp.data();
+    cudaEvent_t e_start, e_in_all, e_out_all;
+    CUDA_TRY(event(&e_start));
+    CUDA_TRY(event(&e_in_all));
+    CUDA_TRY(event(&e_out_all));
+    // the copies start after what the system's stream holds (a previous step's readers)
+    CUDA_TRY(cudaEventRecord(e_start, st));
+    CUDA_TRY(cudaStreamWaitEvent(sys->copy_in, e_start, 0));
+    CUDA_TRY(cudaStreamWaitEvent(sys->copy_out, e_start, 0));
+    std::vector<cudaEvent_t> e_in(nb), e_out(nb);
+    int64_t done_in = 0;
+    for (size_t i = 0; i < nb; ++i) {
+        const Batch& b = sys->batches[i];
+        const int64_t a = oL[b.fn0], e = oL[b.fn0 + b.nfn];
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(sys->d_phi.p) + a * es, static_cast<const char*>(phi_host) + a * es,
+                                 static_cast<size_t>(e - a) * es, cudaMemcpyHostToDevice, sys->copy_in));
+        CUDA_TRY(event(&e_in[i]));
+        CUDA_TRY(cudaEventRecord(e_in[i], sys->copy_in));
+        done_in = e;
+    }
+    if (static_cast<size_t>(done_in) * es < bphi)       // functions past "hphi_limit"
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(sys->d_phi.p) + done_in * es,
+                                 static_cast<const char*>(phi_host) + done_in * es, bphi - done_in * es,
+                                 cudaMemcpyHostToDevice, sys->copy_in));
+    CUDA_TRY(cudaEventRecord(e_in_all, sys->copy_in));
+    Tracer* tr = nullptr;
+    if (sys->profiling) {
+        if (!sys->direct_tr) sys->direct_tr.reset(new Tracer());
+        tr = sys->direct_tr.get();
+        if (!tr->pending) tr->used = 0;
+    }
+    int64_t done_out = 0;
+    auto before = [&](size_t i) { return cudaStreamWaitEvent(st, e_in[i], 0); };
+    auto after = [&](size_t i) -> cudaError_t {
+        if (!hphi_host) return cudaSuccess;
+        const Batch& b = sys->batches[i];
+        const int64_t a = oP[b.fn0], e = oP[b.fn0 + b.nfn];
+        cudaError_t c;
+        if ((c = event(&e_out[i])) != cudaSuccess) return c;
+        if ((c = cudaEventRecord(e_out[i], st)) != cudaSuccess) return c;
+        if ((c = cudaStreamWaitEvent(sys->copy_out, e_out[i], 0)) != cudaSuccess) return c;
+        done_out = e;
+        return cudaMemcpyAsync(static_cast<char*>(hphi_host) + a * es, static_cast<const char*>(sys->d_hphi.p) + a * es,
+                               static_cast<size_t>(e - a) * es, cudaMemcpyDeviceToHost, sys->copy_out);
+    };
+    lsw_status r = enqueue_apply_hooked(sys, tr, sys->d_phi.p, sys->d_hphi.p, static_cast<double*>(sys->d_ek.p),
+                                        static_cast<double*>(sys->d_ep.p), before, after);
     if (r != LSW_OK) return r;
+    CUDA_TRY(cudaStreamWaitEvent(st, e_in_all, 0));
     r = lsw_build_matrices(sys, sys->d_phi.p, sys->d_hphi.p, static_cast<double*>(sys->d_H.p),
                            static_cast<double*>(sys->d_S.p));
     if (r != LSW_OK) return r;
     CUDA_TRY(cudaMemcpyAsync(H_host, sys->d_H.p, bnnz, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(S_host, sys->d_S.p, bnnz, cudaMemcpyDeviceToHost, st));
-    if (hphi_host) CUDA_TRY(cudaMemcpyAsync(hphi_host, sys->d_hphi.p, bhphi, cudaMemcpyDeviceToHost, st));
+    if (hphi_host && static_cast<size_t>(done_out) * es < bhphi)
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(hphi_host) + done_out * es,
+                                 static_cast<const char*>(sys->d_hphi.p) + done_out * es, bhphi - done_out * es,
+                                 cudaMemcpyDeviceToHost, st));
     if (ek_host) CUDA_TRY(cudaMemcpyAsync(ek_host, sys->d_ek.p, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (ep_host) CUDA_TRY(cudaMemcpyAsync(ep_host, sys->d_ep.p, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaEventRecord(e_out_all, sys->copy_out));
+    CUDA_TRY(cudaStreamWaitEvent(st, e_out_all, 0));
     return lsw_sync(sys, 600.0);
 }
 

@@ -248,16 +248,22 @@ def test_step_host_equals_device_calls():
     S = lsw.System(wl.N, wl.h, wl.pos, wl.r_loc, wl.r_fine, wl.nsf, wl.pair_cutoff, wl.pair_mode,
                    precision=lsw.LSW_FP64, device=0, stream=torch.cuda.current_stream().cuda_stream)
     try:
+        # several batches: Phi goes up and H phi comes back batch by batch on copy streams
+        lsw.lsw_set_option(S.sys, "batch", 4)
         V = torch.tensor(I.potential(wl), dtype=torch.float64, device="cuda")
         lsw.lsw_set_potential(S.sys, V, wl.V_lo, wl.V_shape)
-        H = np.zeros(len(S.col))
-        Sm = np.zeros(len(S.col))
-        hphi = np.zeros(S.total_Lp)
-        lsw.lsw_step_host(S.sys, dev["phi"], hphi, H, Sm)
         gap = np.isnan(dev["hphi"])                 # alignment gaps: never written
-        assert np.max(np.abs(hphi[~gap] - dev["hphi"][~gap])) <= 1e-13 * np.max(np.abs(dev["hphi"][~gap]))
-        assert np.max(np.abs(H - dev["H"])) <= 1e-12 * np.max(np.abs(dev["H"]))
-        assert np.max(np.abs(Sm - dev["S"])) <= 1e-13
+        for _ in range(2):                          # the second call reuses the copy streams
+            H = np.zeros(len(S.col))
+            Sm = np.zeros(len(S.col))
+            hphi = np.zeros(S.total_Lp)
+            ek = np.zeros(S.n_sf)
+            ep = np.zeros(S.n_sf)
+            lsw.lsw_step_host(S.sys, dev["phi"], hphi, H, Sm, ek, ep)
+            assert np.max(np.abs(hphi[~gap] - dev["hphi"][~gap])) <= 1e-13 * np.max(np.abs(dev["hphi"][~gap]))
+            assert np.max(np.abs(H - dev["H"])) <= 1e-12 * np.max(np.abs(dev["H"]))
+            assert np.max(np.abs(Sm - dev["S"])) <= 1e-13
+            assert np.allclose(ek, dev["ek"], rtol=1e-12, atol=0) and np.allclose(ep, dev["ep"], rtol=1e-12, atol=0)
     finally:
         S.close()
 
