@@ -1,7 +1,9 @@
 """Autotuner for the library's launch shapes: functions per H phi batch ("batch"), the
 plane kernels of split-bfloat16 systems on the FMA units or the tensor cores ("xy_tc"),
 persistent grids for the FMA plane kernels ("persistent": bit 0 backward, bit 1 forward)
-and the forward member block lists ("fwd_list"), and the H/S tile edge ("tile").
+and the forward member block lists ("fwd_list"), the H/S tile edge ("tile") and the H/S
+panel budget per slab ("slab_mb": fewer, larger slabs repack fewer atoms at slab edges
+but hold more device memory).
 
 Each candidate is set through lsw_set_option, warmed once, then timed with CUDA events
 on the system's stream; the fastest is kept.  Everything runs in the library's kernels;
@@ -15,6 +17,7 @@ from . import lsw
 BATCH_CANDIDATES = (16, 32, 64, 128, 256, 512, 1024, 2048, 4096)
 TILE_CANDIDATES = (3, 4, 5, 6, 7, 8)
 PERSISTENT_CANDIDATES = (1, 0, 3, 2)
+SLAB_CANDIDATES = (8192, 65536)
 
 
 def _time(fn, stream, reps):
@@ -32,7 +35,7 @@ def _time(fn, stream, reps):
 
 
 def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDIDATES,
-             tiles=TILE_CANDIDATES, reps=2, budget_bytes=None):
+             tiles=TILE_CANDIDATES, reps=2, budget_bytes=None, slabs=SLAB_CANDIDATES):
     """Pick "batch" and "tile" for ``system`` (an lsw.System); returns a report dict.
 
     ``budget_bytes`` caps the workspace a batch may take (None: no cap)."""
@@ -84,5 +87,17 @@ def autotune(system, phi, hphi, H, S, e_kin, e_pot, stream, batches=BATCH_CANDID
         if best_t is None or ms < report["tile"][best_t]:
             best_t = t
     lsw.lsw_set_option(system.sys, "tile", best_t)
-    report["chosen"] = {"batch": best_b, "tile": best_t, "xy_tc": best_x, "persistent": best_p, "fwd_list": best_l}
+    report["slab_mb"] = {}
+    best_s = None
+    for sm in slabs:
+        lsw.lsw_set_option(system.sys, "slab_mb", sm)
+        if budget_bytes is not None and lsw.lsw_workspace_bytes(system.sys) > budget_bytes:
+            continue
+        report["slab_mb"][sm] = _time(lambda: lsw.lsw_build_matrices(system.sys, phi, hphi, H, S), stream, reps)
+        if best_s is None or report["slab_mb"][sm] < report["slab_mb"][best_s]:
+            best_s = sm
+    best_s = best_s if best_s is not None else min(slabs)
+    lsw.lsw_set_option(system.sys, "slab_mb", best_s)
+    report["chosen"] = {"batch": best_b, "tile": best_t, "xy_tc": best_x, "persistent": best_p, "fwd_list": best_l,
+                        "slab_mb": best_s}
     return report

@@ -15,7 +15,7 @@ class _FakeLib:
     """Options of one fake system; the "time" of a call is a function of them."""
 
     def __init__(self, xy_tc_error=False):
-        self.opts = {"batch": 32, "tile": 4, "xy_tc": 0, "persistent": 1, "fwd_list": 1}
+        self.opts = {"batch": 32, "tile": 4, "xy_tc": 0, "persistent": 1, "fwd_list": 1, "slab_mb": 8192}
         self.xy_tc_error = xy_tc_error
         self.last = None
 
@@ -25,7 +25,7 @@ class _FakeLib:
         self.opts[name] = value
 
     def workspace_bytes(self, sys):
-        return 1000 * self.opts["batch"]
+        return 1000 * self.opts["batch"] + 10 * self.opts["slab_mb"]
 
     def apply(self, *a):
         o = self.opts
@@ -34,7 +34,7 @@ class _FakeLib:
                      + 0.5 * o["fwd_list"])
 
     def build(self, *a):
-        self.last = abs(self.opts["tile"] - 6) + 1.0
+        self.last = abs(self.opts["tile"] - 6) + 1.0 + (0.1 if self.opts["slab_mb"] < 65536 else 0.0)
 
 
 @pytest.fixture
@@ -62,7 +62,7 @@ def _system(prec, n_sf=10000):
 def test_each_knob_keeps_its_fastest_candidate(fake):
     f = fake()
     rep = AT.autotune(_system(lsw.LSW_FP32_BF16X), None, None, None, None, None, None, None)
-    assert rep["chosen"] == {"batch": 512, "tile": 6, "xy_tc": 0, "persistent": 3, "fwd_list": 0}
+    assert rep["chosen"] == {"batch": 512, "tile": 6, "xy_tc": 0, "persistent": 3, "fwd_list": 0, "slab_mb": 65536}
     assert {k: f.opts[k] for k in rep["chosen"]} == rep["chosen"]          # left on the choice
     assert set(rep["batch"]) == set(AT.BATCH_CANDIDATES)
     assert set(rep["persistent"]) == set(AT.PERSISTENT_CANDIDATES)
@@ -72,8 +72,9 @@ def test_each_knob_keeps_its_fastest_candidate(fake):
 def test_budget_skips_large_batches_and_fp32_skips_the_tensor_core_planes(fake):
     f = fake()
     rep = AT.autotune(_system(lsw.LSW_FP32), None, None, None, None, None, None, None,
-                      budget_bytes=1000 * 256)
+                      budget_bytes=1000 * 256 + 10 * 8192)
     assert max(rep["batch"]) == 256 and rep["chosen"]["batch"] == 256
+    assert list(rep["slab_mb"]) == [8192] and rep["chosen"]["slab_mb"] == 8192    # the larger slab does not fit
     assert "xy_tc" not in rep and rep["chosen"]["xy_tc"] == 0
     assert f.opts["batch"] == 256
 
