@@ -265,20 +265,6 @@ void sphere_bounds(const int32_t* N, double h, const double* c, double R, int* l
     }
 }
 
-void make_keys(const int32_t* N, RegionHost* r) {
-    r->keys.clear();
-    const auto& g = r->g;
-    size_t i = 0;
-    while (i < g.size()) {
-        size_t j = i;
-        while (j + 1 < g.size() && g[j + 1] == g[j] + 1 && (g[j + 1] / N[0]) == (g[i] / N[0])) ++j;
-        r->keys.push_back(g[i]);
-        r->keys.push_back(g[j]);
-        r->keys.push_back(static_cast<int64_t>(i));
-        i = j + 1;
-    }
-}
-
 void build_locreg(lsw_system_s* s, const std::vector<uint8_t>& fine, int a, double R,
                   LocregHost* out) {
     const int32_t* N = s->N;
@@ -289,34 +275,74 @@ void build_locreg(lsw_system_s* s, const std::vector<uint8_t>& fine, int a, doub
     double rf2 = s->r_fine[a] * s->r_fine[a];
     out->c.g.clear();
     out->f.g.clear();
+    out->c.keys.clear();
+    out->f.keys.clear();
+    const double rg = R / s->h + 1.0;                  // sphere radius in grid steps, rounded up
+    out->c.g.reserve(static_cast<size_t>(4.2 * rg * rg * rg) + 64);
     int bl[3] = {N[0], N[1], N[2]}, bh[3] = {-1, -1, -1};
+    const double h = s->h;
     for (int k = lo[2]; k <= hi[2]; ++k) {
-        double z = static_cast<double>(k) * s->h;
+        double z = static_cast<double>(k) * h;
         for (int j = lo[1]; j <= hi[1]; ++j) {
-            double y = static_cast<double>(j) * s->h;
-            for (int i = lo[0]; i <= hi[0]; ++i) {
-                double x = static_cast<double>(i) * s->h;
-                if (!(d2_of(x, y, z, c) <= R2)) continue;
-                int64_t g = i + static_cast<int64_t>(N[0]) * (j + static_cast<int64_t>(N[1]) * k);
+            double y = static_cast<double>(j) * h;
+            // The members of a row are one interval of i: d2 grows with |x - c_x| and every
+            // operation of d2_of is correctly rounded, hence monotone.  The point nearest
+            // c_x decides whether the row has members; the chord estimates the ends, and
+            // the exact test moves each end to the true boundary.
+            auto in = [&](int i) { return d2_of(static_cast<double>(i) * h, y, z, c) <= R2; };
+            const int mc = static_cast<int>(std::floor(c[0] / h));
+            int m = -1;                                // a member next to the minimum of d2, if any
+            for (int t = mc - 1; t <= mc + 1 && m < 0; ++t) {
+                const int tt = std::min(std::max(t, lo[0]), hi[0]);
+                if (in(tt)) m = tt;
+            }
+            if (m < 0) continue;
+            const double dy = y - c[1], dz = z - c[2];
+            const double w = std::sqrt(std::max(0.0, R2 - (dy * dy + dz * dz)));
+            int ia = std::min(m, std::max(lo[0], static_cast<int>(std::ceil((c[0] - w) / h))));
+            int ib = std::max(m, std::min(hi[0], static_cast<int>(std::floor((c[0] + w) / h))));
+            while (ia > lo[0] && in(ia - 1)) --ia;
+            while (!in(ia)) ++ia;                      // stops at m at the latest
+            while (ib < hi[0] && in(ib + 1)) ++ib;
+            while (!in(ib)) --ib;
+            const int64_t g0 = static_cast<int64_t>(N[0]) * (j + static_cast<int64_t>(N[1]) * k);
+            // keys: (first g, last g, offset of the first) per run of consecutive members
+            // within one x row; the coarse members of the row are one run, the fine ones
+            // one run per stretch of the fine region
+            out->c.keys.push_back(g0 + ia);
+            out->c.keys.push_back(g0 + ib);
+            out->c.keys.push_back(static_cast<int64_t>(out->c.g.size()));
+            int64_t run = -1;                          // first g of the open fine run
+            for (int i = ia; i <= ib; ++i) {
+                const int64_t g = g0 + i;
                 out->c.g.push_back(g);
                 bool isf;
                 if (s->fine_mode == LSW_FINE_UNION)
                     isf = fine[g] != 0;
                 else
-                    isf = d2_of(x, y, z, c) <= rf2;
-                if (isf) out->f.g.push_back(g);
-                bl[0] = std::min(bl[0], i), bh[0] = std::max(bh[0], i);
-                bl[1] = std::min(bl[1], j), bh[1] = std::max(bh[1], j);
-                bl[2] = std::min(bl[2], k), bh[2] = std::max(bh[2], k);
+                    isf = d2_of(static_cast<double>(i) * h, y, z, c) <= rf2;
+                if (isf) {
+                    if (run < 0) {
+                        run = g;
+                        out->f.keys.push_back(g);
+                        out->f.keys.push_back(g);
+                        out->f.keys.push_back(static_cast<int64_t>(out->f.g.size()));
+                    }
+                    out->f.keys[out->f.keys.size() - 2] = g;
+                    out->f.g.push_back(g);
+                } else {
+                    run = -1;
+                }
             }
+            bl[0] = std::min(bl[0], ia), bh[0] = std::max(bh[0], ib);
+            bl[1] = std::min(bl[1], j), bh[1] = std::max(bh[1], j);
+            bl[2] = std::min(bl[2], k), bh[2] = std::max(bh[2], k);
         }
     }
     for (int d = 0; d < 3; ++d) {
         out->lo[d] = out->c.g.empty() ? 0 : bl[d];
         out->n[d] = out->c.g.empty() ? 0 : bh[d] - bl[d] + 1;
     }
-    make_keys(N, &out->c);
-    make_keys(N, &out->f);
 }
 
 // box-local segments and per-row CSR of one region part
