@@ -935,20 +935,23 @@ lsw_status upload_geometry(lsw_system_s* s) {
         const LocregHost& P = s->Lp[a];
         ColZ* t = colz.data() + recs[a].colz;
         const int64_t N0 = s->N[0], N01 = static_cast<int64_t>(s->N[0]) * s->N[1];
-        auto fold = [&](const std::vector<int64_t>& g, bool fine) {
-            for (int64_t v : g) {
-                const int x = static_cast<int>(v % N0 - P.lo[0]);
-                const int y = static_cast<int>((v / N0) % s->N[1] - P.lo[1]);
-                const int16_t z = static_cast<int16_t>(v / N01 - P.lo[2]);
-                ColZ& e = t[static_cast<int64_t>(y) * P.n[0] + x];
-                int16_t& lo = fine ? e.f0 : e.c0;
-                int16_t& hi = fine ? e.f1 : e.c1;
-                if (lo < 0 || z < lo) lo = z;
-                if (z > hi) hi = z;
+        auto fold = [&](const RegionHost& r, bool fine) {       // one segment (x run of a row) at a time
+            for (size_t q = 0; q < r.keys.size() / 3; ++q) {
+                const int64_t g0 = r.keys[3 * q], g1 = r.keys[3 * q + 1];
+                const int x0 = static_cast<int>(g0 % N0 - P.lo[0]);
+                const int y = static_cast<int>((g0 / N0) % s->N[1] - P.lo[1]);
+                const int16_t z = static_cast<int16_t>(g0 / N01 - P.lo[2]);
+                ColZ* row = t + static_cast<int64_t>(y) * P.n[0];
+                for (int x = x0; x <= x0 + static_cast<int>(g1 - g0); ++x) {
+                    int16_t& lo = fine ? row[x].f0 : row[x].c0;
+                    int16_t& hi = fine ? row[x].f1 : row[x].c1;
+                    if (lo < 0 || z < lo) lo = z;
+                    if (z > hi) hi = z;
+                }
             }
         };
-        fold(P.c.g, false);
-        fold(P.f.g, true);
+        fold(P.c, false);
+        fold(P.f, true);
     });
     cudaStream_t st = s->stream;
     CUDA_TRY(s->d_colz.upload(colz, st));
